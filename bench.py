@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark of the k-center farthest-point hot path on GB300.
+
+Workload: GON (Section 3.1) with k = 100 followed by the covering radius of
+its centers (kc_radius), on n = 1,000,000 points in d = 10, a mixture of 25
+isotropic Gaussians (sigma 1, means uniform in [-50, 50]^10), FP32, seed 1.
+One step = one kc_gonzalez + one kc_radius call through the C ABI.
+
+Metric: point-center distance evaluations per second (GON: k sweeps of n
+points; radius: n x k), whole job over all ranks.  `value` is device-timed
+with the points resident in HBM (CUDA events around every step, 256 MiB L2
+flush between steps outside the events); `e2e` is the same metric with the
+points in pinned host memory passed to the C ABI, host<->device copies and
+result read-back inside the wall-clock timed region.
+
+Under torchrun (N > 1) every rank solves its own independent instance of the
+workload (seed 1 + 1000 * rank): weak scaling, no collective on the data path.
+
+--impl reference times the CPU oracle (plain C, one thread) on a bounded
+sample of the same workload: the first 5 GON steps plus the radius of those 5
+centers over all n points per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "point-center dist evals/s & % HBM roofline; mixed-prec batched vs FP32 solve ms"
+UNIT = "dist_evals/s"
+N, D, K = 1_000_000, 10, 100
+WORKLOAD = "gon_radius_gau_n1000000_d10_k100"
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic (read + write bytes) per launch of the dominant kernel from an
+# ncu capture, keyed by the SHA-256 of the kernel's source file at capture
+# time; reported only while the source is unchanged.
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload(rank: int):
+    from paper_1604_03228_gb300 import inputs as I
+    seed = 1 + 1000 * rank
+    return I.gauss_mixture(N, D, seed, 25, 1.0, -50.0, 50.0)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.t is not None:
+            self.t.join(timeout=2)
+
+    def summary(self, t0, t1):
+        inside = [r for (t, r) in self.rows if t0 <= t <= t1]
+        window = "timed"
+        if not inside:
+            inside = [r for (_, r) in self.rows]
+            window = "whole run (timed region shorter than one sample)"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(inside), "window": window}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample(pts, k_sample=5):
+    """Oracle on a bounded sample: first k_sample GON steps + their radius."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    g = O.gonzalez(pts, k_sample, mode="f64")
+    O.radius(pts, g.centers, mode="f64")
+    dt = time.perf_counter() - t0
+    evals = pts.shape[0] * k_sample * 2
+    return evals, dt
+
+
+def cpu_baseline(pts):
+    evals, dt = oracle_sample(pts)
+    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first 5 GON steps + radius of those 5 centers, n={N}, d={D}, FP64, "
+                      f"one thread ({dt:.2f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    pts = workload(0)
+    for _ in range(args.warmup):
+        oracle_sample(pts)
+    tot_e, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        e, t = oracle_sample(pts)
+        tot_e += e
+        tot_t += t
+    v = tot_e / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "d": D, "k": K},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "first 5 GON steps + radius of those 5 centers per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1604_03228_gb300 as kc
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    kc.load()
+    pts = workload(rank)
+    x = torch.from_numpy(pts).cuda()
+    s = torch.cuda.current_stream()
+    cen = torch.empty(K, dtype=torch.int64, device="cuda")
+    kout = torch.empty(1, dtype=torch.int32, device="cuda")
+    rad = torch.empty(1, dtype=torch.float64, device="cuda")
+    rrad = torch.empty(1, dtype=torch.float64, device="cuda")
+    ram = torch.empty(1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        kc.kc_gonzalez(x, K, flags=kc.KC_ASYNC, out=(cen, kout, rad))
+        kc.kc_radius(x, cen, flags=kc.KC_ASYNC, out=(rrad, ram))
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    kc.kc_sync(s)
+    assert int(kout.item()) == K
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kc.kc_trace_read()
+    kc.kc_trace_enable(True)
+    launches0 = kc.kc_launch_count()
+    t_wall0 = time.time()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(s)
+        step()
+        ev[i][1].record(s)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    launches = kc.kc_launch_count() - launches0
+    kc.kc_trace_enable(False)
+    trace = kc.kc_trace_read()
+    kc.kc_sync(s)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sampler.stop()
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    evals_step = N * K + N * K
+    value = evals_step * args.steps * world / (total_ms / 1e3)
+
+    # dominant kernel: the persistent GON kernel (one launch per step)
+    gon_ms = [ms for (name, nk, ms) in trace if name == "gonzalez"]
+    gon_avg = statistics.mean(gon_ms)
+    alg_bytes = K * N * (4 * D + 4)
+    achieved = alg_bytes / (gon_avg / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    src = open(os.path.join(ROOT, "paper_1604_03228_gb300", "csrc", "kc_gon.cu"), "rb").read()
+    traffic = NCU_TRAFFIC.get(hashlib.sha256(src).hexdigest())
+    shares = {}
+    for name, nk, ms in trace:
+        shares[name] = shares.get(name, 0.0) + ms
+
+    # end to end: points in pinned host memory through the C ABI each step
+    e2e = None
+    if rank == 0 or world > 1:
+        hp = torch.from_numpy(pts).pin_memory()
+        for _ in range(2):
+            g = kc.kc_gonzalez(hp, K)
+            kc.kc_radius(hp, g.centers)
+        reps = max(3, min(args.steps, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            g = kc.kc_gonzalez(hp, K)
+            r = kc.kc_radius(hp, g.centers)
+            _ = (g.radius, r.radius)
+        t1 = time.perf_counter()
+        e2e_val = evals_step * reps / (t1 - t0)
+        if world > 1:
+            t = torch.tensor([e2e_val * world], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MIN)
+            e2e_val = float(t.item())
+        h2d = 2 * N * D * 4 + K * 8
+        d2h = K * 8 + 4 + 8 + 8 + 8
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(pts)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": N, "d": D, "k": K, "points": "25-Gaussian mixture",
+                           "l2": f"{L2_FLUSH_BYTES >> 20} MiB flush between steps",
+                           "step": "kc_gonzalez + kc_radius", "replicas": world},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic, "kernel": "gon_kernel",
+                             "peak_kind": peak_kind, "avg_ms": gon_avg,
+                             "alg_bytes_per_launch": alg_bytes},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "step_share_ms": {k_: v / args.steps for k_, v in shares.items()}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

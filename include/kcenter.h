@@ -1,0 +1,153 @@
+/*
+ * kcenter.h -- C ABI of the GB300 k-center library.
+ *
+ * The library computes the k-center method of McClintock & Wirth, "Efficient
+ * Parallel Algorithms for k-Center Clustering" (arXiv 1604.03228): pick at
+ * most k of the n input points as centers so that the largest distance from
+ * any point to its nearest center (the covering radius) is small.  Its hot
+ * path is the farthest-point step of Gonzalez's algorithm (Section 3.1): the
+ * distance from every point to the newest center, a running minimum, and a
+ * global argmax with the lowest index winning ties.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Points are row-major n x d (point i's coordinates at pts[i*d .. i*d+d-1]),
+ *    float32 (KC_F32) or int32 (KC_I32) as opts->dtype says.  The distance is
+ *    Euclidean; squared distances are compared and a radius is returned as a
+ *    distance (square root) in double.
+ *  - Every pointer may be host memory (pageable or pinned) or device memory
+ *    of the current CUDA device; the library tells them apart with
+ *    cudaPointerGetAttributes and copies host inputs in and host outputs out
+ *    itself.  The caller owns all memory it passes; the library never frees
+ *    it.  Scratch memory is allocated by the library on first use, cached per
+ *    (device, stream) and released by kc_release().
+ *  - Calls are ordered on opts->stream (a cudaStream_t; NULL = the legacy
+ *    default stream).  Without KC_ASYNC a call waits for its work and returns
+ *    the final status.  With KC_ASYNC (all pointers must then be device
+ *    pointers) a call only enqueues work; errors found on the device are kept
+ *    in a status word that kc_sync() returns.
+ *  - Selection is exact for int32 points (squared distances in 32-bit
+ *    unsigned arithmetic, which the library checks is exact: d * (max - min)^2
+ *    must be below 2^32, else KC_ERR_RANGE).  For float32 points every argmax
+ *    is taken on the canonical FP32 squared distance: for j = 0..d-1,
+ *    t = x_j - c_j rounded to float, acc = fma(t, t, acc) from acc = 0.  The
+ *    returned radius is then recomputed in FP64 (coordinates widened, terms
+ *    summed in coordinate order without fused multiply-add) for the point(s)
+ *    that can reach the maximum, so it equals the plain FP64 covering radius
+ *    of the chosen centers.
+ *  - Ties between equally far points go to the lowest point index.  When
+ *    every point is at distance 0 from the chosen centers, selection stops
+ *    early and *k_out < k ("at most k centers", Section 1.1).
+ *  - n must be in [1, 2^32 - 2]; d >= 1; k >= 1.  Non-finite float
+ *    coordinates give KC_ERR_NONFINITE.  Spin-waits inside persistent kernels
+ *    give up after a time budget and return KC_ERR_TIMEOUT; nothing traps.
+ *  - Every failure is a status code; kc_last_error() describes the last one
+ *    on the calling thread.  No function aborts the process.
+ */
+#ifndef KCENTER_H
+#define KCENTER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KC_OK = 0,
+    KC_ERR_ARG = 1,        /* invalid argument (sizes, indices, flags) */
+    KC_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+    KC_ERR_OOM = 3,        /* device scratch allocation failed */
+    KC_ERR_TIMEOUT = 4,    /* a device spin-wait ran out of its time budget */
+    KC_ERR_RANGE = 5,      /* int32 squared distances would not fit 32 bits */
+    KC_ERR_NONFINITE = 6   /* a float coordinate is NaN or infinite */
+} kc_status;
+
+typedef enum { KC_F32 = 0, KC_I32 = 1 } kc_dtype;
+
+/* Flags for kc_opts.flags. */
+#define KC_ASYNC 1u        /* enqueue only; see kc_sync() */
+
+typedef struct {
+    int32_t dtype;          /* kc_dtype of the points */
+    uint32_t flags;         /* KC_ASYNC or 0 */
+    uint64_t seed;          /* EIM sampling seed */
+    double phi;             /* EIM Select parameter (Section 4.2); <= 0 means 6 */
+    void *stream;           /* cudaStream_t, NULL = legacy default stream */
+    int64_t timeout_ms;     /* device spin-wait budget; <= 0 means 2000 ms */
+} kc_opts;
+
+/*
+ * kc_gonzalez -- GON, Section 3.1 (the factor-2 greedy of Gonzalez): start
+ * from point `first`, then repeatedly add the point farthest from the centers
+ * chosen so far, until k centers exist.  Cost O(k n) distance evaluations
+ * (Section 5.1).
+ *   pts      [n*d] points (see conventions); read only.
+ *   first    index of the first center, 0 <= first < n.
+ *   centers  [k] int64 out: chosen point indices in selection order; entries
+ *            past *k_out are left untouched.
+ *   k_out    int32 out: number of centers chosen (k, or fewer on early stop).
+ *   radius   double out: covering radius of the chosen centers over all points.
+ * Errors: KC_ERR_ARG for bad sizes or `first`; KC_ERR_RANGE, KC_ERR_NONFINITE,
+ * KC_ERR_TIMEOUT, KC_ERR_OOM, KC_ERR_CUDA as above.  Outputs are undefined on
+ * error.
+ */
+kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t first,
+                      int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts);
+
+/*
+ * kc_radius -- covering radius of a given center set, the "solution value"
+ * reported throughout Section 7 (the objective of Section 1.1, read as the
+ * largest distance from a point to its nearest center):
+ * max over x of min over c of d(x, c).
+ *   centers       [kc] int64 indices into the points, each in [0, n).
+ *   radius        double out: the covering radius.
+ *   argmax_point  int64 out (may be NULL): the farthest point, lowest index on
+ *                 ties.
+ * Errors: KC_ERR_ARG if kc < 1 or an index is out of range; others as above.
+ */
+kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *centers, int32_t kc,
+                    double *radius, int64_t *argmax_point, const kc_opts *opts);
+
+/*
+ * kc_sync -- wait for all work enqueued on `stream` and return (and clear)
+ * the device status word of that stream's scratch: KC_OK, or the first error
+ * a kernel recorded since the last kc_sync / synchronous call.
+ */
+kc_status kc_sync(void *stream);
+
+/* kc_last_error -- text describing the last failure on this thread. */
+const char *kc_last_error(void);
+
+/* kc_release -- free all cached device scratch of every device and stream.
+ * No call may be in flight. */
+void kc_release(void);
+
+/* kc_version -- library version string. */
+const char *kc_version(void);
+
+/*
+ * Tracing (no counterpart in the paper; the paper reports wall-clock time per
+ * simulated MapReduce round, Section 7.1).  While tracing is on, each launch
+ * step of every call is bracketed by CUDA events recorded on the call's
+ * stream.  kc_trace_read waits for the traced work, copies up to `cap`
+ * records into `out` (oldest first), clears the list and returns the number
+ * of records that were pending.  kc_launch_count returns how many CUDA
+ * kernels the library has launched in this process.
+ */
+typedef struct {
+    char name[24];      /* launch step, e.g. "pack", "gonzalez", "radius" */
+    int32_t kernels;    /* kernels launched by this step */
+    float ms;           /* elapsed device time between the events */
+} kc_trace_rec;
+
+void kc_trace_enable(int32_t on);
+int32_t kc_trace_read(kc_trace_rec *out, int32_t cap);
+int64_t kc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KCENTER_H */

@@ -1,0 +1,10 @@
+"""GB300-native k-center farthest-point path (McClintock & Wirth, arXiv 1604.03228).
+
+The CUDA library (``csrc/``, C ABI in ``include/kcenter.h``) does the work;
+``binding`` marshals arguments to it.  ``inputs`` draws seeded synthetic
+point sets shaped like the paper's workloads.
+"""
+from .binding import (KC_ASYNC, KC_ERR_ARG, KC_ERR_CUDA, KC_ERR_NONFINITE, KC_ERR_OOM,  # noqa: F401
+                      KC_ERR_RANGE, KC_ERR_TIMEOUT, KC_F32, KC_I32, KC_OK, GonResult, KCError,
+                      RadiusResult, kc_gonzalez, kc_launch_count, kc_radius, kc_release, kc_sync,
+                      kc_trace_enable, kc_trace_read, kc_version, library_path, load)

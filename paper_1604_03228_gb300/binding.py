@@ -1,0 +1,262 @@
+"""Thin Python binding of the C ABI in include/kcenter.h (ctypes).
+
+Each ``kc_*`` function here has the name of the C entry point it calls and
+only marshals arguments: it turns torch tensors (CUDA or CPU) or numpy arrays
+into pointers and sizes, allocates the output buffers next to the input, and
+raises ``KCError`` on a non-zero status.  Every step of the computation runs
+in the CUDA library; there is no CPU fallback.  If the library is missing or
+fails to build, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+KC_OK, KC_ERR_ARG, KC_ERR_CUDA, KC_ERR_OOM, KC_ERR_TIMEOUT, KC_ERR_RANGE, KC_ERR_NONFINITE = range(7)
+KC_F32, KC_I32 = 0, 1
+KC_ASYNC = 1
+STATUS_NAMES = {0: "KC_OK", 1: "KC_ERR_ARG", 2: "KC_ERR_CUDA", 3: "KC_ERR_OOM", 4: "KC_ERR_TIMEOUT",
+                5: "KC_ERR_RANGE", 6: "KC_ERR_NONFINITE"}
+
+
+class KCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kc_opts(ct.Structure):
+    _fields_ = [("dtype", ct.c_int32), ("flags", ct.c_uint32), ("seed", ct.c_uint64),
+                ("phi", ct.c_double), ("stream", ct.c_void_p), ("timeout_ms", ct.c_int64)]
+
+
+_LIB = None
+
+
+def load(path: str | None = None):
+    """Build (if stale) and load libkcenter.so; raises if that fails."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library missing: {path}")
+    L = ct.CDLL(path)
+    vp, i64, i32, dbl = ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_double
+    popts = ct.POINTER(kc_opts)
+    L.kc_gonzalez.restype = ct.c_int
+    L.kc_gonzalez.argtypes = [vp, i64, i32, i32, i64, vp, vp, vp, popts]
+    L.kc_radius.restype = ct.c_int
+    L.kc_radius.argtypes = [vp, i64, i32, vp, i32, vp, vp, popts]
+    L.kc_sync.restype = ct.c_int
+    L.kc_sync.argtypes = [vp]
+    L.kc_last_error.restype = ct.c_char_p
+    L.kc_release.restype = None
+    L.kc_version.restype = ct.c_char_p
+    L.kc_trace_enable.restype = None
+    L.kc_trace_enable.argtypes = [i32]
+    L.kc_trace_read.restype = i32
+    L.kc_trace_read.argtypes = [ct.POINTER(kc_trace_rec), i32]
+    L.kc_launch_count.restype = i64
+    _LIB = L
+    return L
+
+
+class kc_trace_rec(ct.Structure):
+    _fields_ = [("name", ct.c_char * 24), ("kernels", ct.c_int32), ("ms", ct.c_float)]
+
+
+def kc_trace_enable(on: bool = True) -> None:
+    load().kc_trace_enable(1 if on else 0)
+
+
+def kc_trace_read(cap: int = 65536):
+    """[(step name, kernels, device ms)] recorded since the last read."""
+    L = load()
+    buf = (kc_trace_rec * cap)()
+    cnt = L.kc_trace_read(buf, cap)
+    return [(buf[i].name.decode(), int(buf[i].kernels), float(buf[i].ms)) for i in range(min(cnt, cap))]
+
+
+def kc_launch_count() -> int:
+    return int(load().kc_launch_count())
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+# ----------------------------------------------------------------- helpers
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(x) -> bool:
+    try:
+        import torch
+    except ImportError:
+        return False
+    return isinstance(x, torch.Tensor)
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if _is_torch(x):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _points(points):
+    """(contiguous points, n, d, dtype code) for a 2-D float32/int32 array."""
+    if _is_torch(points):
+        torch = _torch()
+        if points.dim() != 2:
+            raise ValueError("points must be 2-D (n, d)")
+        if points.dtype not in (torch.float32, torch.int32):
+            raise TypeError("points must be float32 or int32")
+        p = points.contiguous()
+        code = KC_F32 if p.dtype == torch.float32 else KC_I32
+    else:
+        p = np.ascontiguousarray(points)
+        if p.ndim != 2:
+            raise ValueError("points must be 2-D (n, d)")
+        if p.dtype == np.float32:
+            code = KC_F32
+        elif p.dtype == np.int32:
+            code = KC_I32
+        else:
+            raise TypeError("points must be float32 or int32")
+    return p, int(p.shape[0]), int(p.shape[1]), code
+
+
+def _empty_like_place(ref, n, dtype_np, pin=False):
+    """Output buffer on the same device as `ref` (torch) or a numpy array."""
+    if _is_torch(ref):
+        torch = _torch()
+        tdt = {np.int64: torch.int64, np.int32: torch.int32, np.float64: torch.float64}[dtype_np]
+        if ref.is_cuda:
+            return torch.empty(n, dtype=tdt, device=ref.device)
+        return torch.empty(n, dtype=tdt, pin_memory=pin)
+    return np.empty(n, dtype=dtype_np)
+
+
+def _stream_handle(ref, stream):
+    if stream is not None:
+        return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    if _is_torch(ref) and ref.is_cuda:
+        return int(_torch().cuda.current_stream(ref.device).cuda_stream)
+    return None
+
+
+def _opts(code, ref, stream, flags, timeout_ms, seed=0, phi=6.0):
+    o = kc_opts()
+    o.dtype = code
+    o.flags = flags
+    o.seed = seed
+    o.phi = phi
+    o.stream = _stream_handle(ref, stream)
+    o.timeout_ms = timeout_ms
+    return o
+
+
+def _check(L, st):
+    if st != KC_OK:
+        raise KCError(st, L.kc_last_error().decode(errors="replace"))
+
+
+def _item(x):
+    if _is_torch(x):
+        return x[0].item()
+    return x[0].item()
+
+
+@dataclass
+class GonResult:
+    centers: object        # int64 [k_out] (tensor or ndarray, same place as the input)
+    k_out: int
+    radius: float
+
+
+@dataclass
+class RadiusResult:
+    radius: float
+    argmax: int
+
+
+# --------------------------------------------------------------- entry points
+
+def kc_gonzalez(points, k: int, first: int = 0, *, stream=None, flags: int = 0,
+                timeout_ms: int = 0, out=None):
+    """GON (Section 3.1) through the C ABI.  With flags=KC_ASYNC returns the
+    raw device outputs (centers[k], k_out[1], radius[1]) without waiting."""
+    L = load()
+    p, n, d, code = _points(points)
+    if out is None:
+        centers = _empty_like_place(p, k, np.int64)
+        k_out = _empty_like_place(p, 1, np.int32)
+        radius = _empty_like_place(p, 1, np.float64)
+    else:
+        centers, k_out, radius = out
+    o = _opts(code, p, stream, flags, timeout_ms)
+    st = L.kc_gonzalez(_ptr(p), n, d, k, first, _ptr(centers), _ptr(k_out), _ptr(radius), ct.byref(o))
+    _check(L, st)
+    if flags & KC_ASYNC:
+        return centers, k_out, radius
+    kk = int(_item(k_out))
+    return GonResult(centers[:kk], kk, float(_item(radius)))
+
+
+def kc_radius(points, centers, *, stream=None, flags: int = 0, timeout_ms: int = 0, out=None):
+    """Covering radius of a center set through the C ABI."""
+    L = load()
+    p, n, d, code = _points(points)
+    if _is_torch(centers):
+        c = centers.to(_torch().int64).contiguous()
+    else:
+        c = np.ascontiguousarray(centers, dtype=np.int64)
+    kc = int(c.shape[0])
+    if out is None:
+        radius = _empty_like_place(p, 1, np.float64)
+        argmax = _empty_like_place(p, 1, np.int64)
+    else:
+        radius, argmax = out
+    o = _opts(code, p, stream, flags, timeout_ms)
+    st = L.kc_radius(_ptr(p), n, d, _ptr(c), kc, _ptr(radius), _ptr(argmax), ct.byref(o))
+    _check(L, st)
+    if flags & KC_ASYNC:
+        return radius, argmax
+    return RadiusResult(float(_item(radius)), int(_item(argmax)))
+
+
+def kc_sync(stream=None) -> int:
+    """Wait for `stream` and return (and clear) its device status."""
+    L = load()
+    h = None
+    if stream is not None:
+        h = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    else:
+        try:
+            torch = _torch()
+            if torch.cuda.is_available():
+                h = int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+    st = L.kc_sync(h)
+    _check(L, st)
+    return st
+
+
+def kc_release() -> None:
+    load().kc_release()
+
+
+def kc_version() -> str:
+    return load().kc_version().decode()

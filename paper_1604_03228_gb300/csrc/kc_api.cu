@@ -1,0 +1,567 @@
+// kc_api.cu -- the C ABI (include/kcenter.h): argument checks, host/device
+// pointer handling, cached device scratch, and the launch sequence of each
+// entry point.  All arithmetic of the method runs in the kernels.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <atomic>
+#include <utility>
+#include <vector>
+
+#include "kc_internal.cuh"
+
+namespace kc {
+int gon_warps_per_cta();
+}
+
+using namespace kc;
+
+namespace {
+
+thread_local std::string g_err;
+
+// ------------------------------------------------------------ tracing
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_trace_on{0};
+thread_local int t_kernels = 0;
+
+struct TraceRec {
+    char name[24];
+    int kernels;
+    cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+std::vector<TraceRec> g_trace;
+std::vector<cudaEvent_t> g_evpool;
+
+cudaEvent_t ev_get() {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    if (!g_evpool.empty()) {
+        cudaEvent_t e = g_evpool.back();
+        g_evpool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one launch step with events on the call's stream while tracing.
+struct TraceStep {
+    bool on;
+    TraceRec r{};
+    cudaStream_t s;
+    int k0 = 0;
+    TraceStep(const char *name, cudaStream_t s_) : on(g_trace_on.load() != 0), s(s_) {
+        if (!on) return;
+        strncpy(r.name, name, sizeof r.name - 1);
+        r.a = ev_get();
+        r.b = ev_get();
+        cudaEventRecord(r.a, s);
+        k0 = t_kernels;
+    }
+    ~TraceStep() {
+        if (!on) return;
+        cudaEventRecord(r.b, s);
+        r.kernels = t_kernels - k0;
+        std::lock_guard<std::mutex> lk(g_tmu);
+        g_trace.push_back(r);
+    }
+};
+
+kc_status fail(kc_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+kc_status cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(KC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(KC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define KC_CUDA(call, what)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, (what));  \
+    } while (0)
+
+// ------------------------------------------------------------ scratch
+// Device scratch is cached per (device, stream): a grow-only arena plus a
+// small persistent status word and a pinned host mirror for read-back.
+struct Arena {
+    char *dev = nullptr;
+    size_t bytes = 0;
+    DevStatus *status = nullptr;   // persistent across calls on this stream
+    DevStatus *host_status = nullptr;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, uintptr_t>, Arena *> g_arenas;
+
+kc_status arena_for(cudaStream_t s, Arena **out) {
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto key = std::make_pair(dev, (uintptr_t)s);
+    auto it = g_arenas.find(key);
+    if (it != g_arenas.end()) {
+        *out = it->second;
+        return KC_OK;
+    }
+    Arena *a = new Arena();
+    cudaError_t e = cudaMalloc(&a->status, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMemset(a->status, 0, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost(&a->host_status, sizeof(DevStatus));
+    if (e != cudaSuccess) {
+        if (a->status) cudaFree(a->status);
+        delete a;
+        return cuda_fail(e, "scratch status allocation");
+    }
+    g_arenas[key] = a;
+    *out = a;
+    return KC_OK;
+}
+
+kc_status arena_reserve(Arena *a, size_t bytes, cudaStream_t s) {
+    if (bytes <= a->bytes) return KC_OK;
+    KC_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (a->dev) cudaFree(a->dev);
+    a->dev = nullptr;
+    a->bytes = 0;
+    const size_t want = bytes + bytes / 8 + (1u << 20);
+    cudaError_t e = cudaMalloc(&a->dev, want);
+    if (e != cudaSuccess) return cuda_fail(e, "scratch allocation");
+    a->bytes = want;
+    return KC_OK;
+}
+
+// Bump allocator over the arena (run once with base == nullptr to size it).
+struct Carve {
+    char *base;
+    size_t off = 0;
+    explicit Carve(char *b) : base(b) {}
+    template <typename T> T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+bool is_device_ptr(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return false;
+}
+
+kc_opts default_opts() {
+    kc_opts o;
+    memset(&o, 0, sizeof o);
+    o.dtype = KC_F32;
+    o.phi = 6.0;
+    return o;
+}
+
+long long timeout_cycles(const kc_opts &o) {
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    if (khz <= 0) khz = 2100000;
+    const long long ms = o.timeout_ms > 0 ? o.timeout_ms : 2000;
+    return ms * (long long)khz;
+}
+
+const char *where_name(int w) {
+    switch (w) {
+        case 1: return "point check";
+        case 2: return "int32 range check";
+        case 3: return "GON step exchange";
+        case 4: return "center index check";
+        default: return "device";
+    }
+}
+
+kc_status status_text(const DevStatus &d) {
+    switch (d.code) {
+        case KC_OK: return KC_OK;
+        case KC_ERR_NONFINITE:
+            return fail(KC_ERR_NONFINITE, "a float coordinate is NaN or infinite");
+        case KC_ERR_RANGE:
+            return fail(KC_ERR_RANGE,
+                        d.where == 1 ? "a float coordinate exceeds 2^54 in magnitude"
+                                     : "int32 coordinates too far apart: d*(max-min)^2 must be < 2^32");
+        case KC_ERR_TIMEOUT:
+            return fail(KC_ERR_TIMEOUT, "device wait timed out in %s (step %lld)", where_name(d.where),
+                        (long long)d.info);
+        case KC_ERR_ARG:
+            return fail(KC_ERR_ARG, "%s failed (item %lld)", where_name(d.where), (long long)d.info);
+        default:
+            return fail((kc_status)d.code, "device error %d in %s", d.code, where_name(d.where));
+    }
+}
+
+// Wait for the stream, read and clear the status word.
+kc_status finish(Arena *a, cudaStream_t s) {
+    KC_CUDA(cudaMemcpyAsync(a->host_status, a->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, s),
+            "status read-back");
+    KC_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    DevStatus d = *a->host_status;
+    if (d.code != 0) {
+        KC_CUDA(cudaMemset(a->status, 0, sizeof(DevStatus)), "status reset");
+        return status_text(d);
+    }
+    return KC_OK;
+}
+
+struct CallCtx {
+    kc_opts o;
+    cudaStream_t s;
+    int dev;
+    bool async;
+    Arena *arena;
+};
+
+kc_status begin(const kc_opts *opts, CallCtx &c) {
+    c.o = opts ? *opts : default_opts();
+    if (c.o.dtype != KC_F32 && c.o.dtype != KC_I32) return fail(KC_ERR_ARG, "dtype must be KC_F32 or KC_I32");
+    if (c.o.flags & ~KC_ASYNC) return fail(KC_ERR_ARG, "unknown flags 0x%x", c.o.flags);
+    c.s = (cudaStream_t)c.o.stream;
+    c.async = (c.o.flags & KC_ASYNC) != 0;
+    KC_CUDA(cudaGetDevice(&c.dev), "cudaGetDevice");
+    return arena_for(c.s, &c.arena);
+}
+
+// Input points: device pointer as is, else copied into `staging`.
+kc_status stage_points(const CallCtx &c, const void *pts, size_t bytes, bool dev_in, void *staging,
+                       const void **out) {
+    if (dev_in) {
+        *out = pts;
+        return KC_OK;
+    }
+    KC_CUDA(cudaMemcpyAsync(staging, pts, bytes, cudaMemcpyHostToDevice, c.s), "copy points to device");
+    *out = staging;
+    return KC_OK;
+}
+
+int choose_gon_grid(int dtype, int d, int64_t n) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int maxg = gon_max_grid(dtype, d);
+    const int W = gon_warps_per_cta();
+    const int64_t nb = nblocks(n);
+    // Aim for about two 128-point blocks per warp; whole waves of SMs.
+    int64_t want = (nb + 2 * W - 1) / (2 * W);
+    int g;
+    if (want >= sms) {
+        int64_t per = (want + sms - 1) / sms;
+        g = (int)(per * sms);
+    } else {
+        g = (int)(want < 1 ? 1 : want);
+    }
+    if (const char *env = getenv("KC_GON_GRID")) {
+        int v = atoi(env);
+        if (v > 0) g = v;
+    }
+    if (g > maxg) g = maxg;
+    return g < 1 ? 1 : g;
+}
+
+}  // namespace
+
+namespace kc {
+void note_launches(int kernels) {
+    g_launches += kernels;
+    t_kernels += kernels;
+}
+}  // namespace kc
+
+extern "C" {
+
+const char *kc_version(void) { return "kcenter-gb300 0.1 (sm_103a)"; }
+
+void kc_trace_enable(int32_t on) { g_trace_on = on ? 1 : 0; }
+
+int64_t kc_launch_count(void) { return g_launches.load(); }
+
+int32_t kc_trace_read(kc_trace_rec *out, int32_t cap) {
+    std::vector<TraceRec> recs;
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        recs.swap(g_trace);
+    }
+    int32_t i = 0;
+    for (auto &r : recs) {
+        float ms = 0.f;
+        cudaEventSynchronize(r.b);
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        if (out && i < cap) {
+            memset(&out[i], 0, sizeof(kc_trace_rec));
+            memcpy(out[i].name, r.name, sizeof out[i].name);
+            out[i].kernels = r.kernels;
+            out[i].ms = ms;
+        }
+        ++i;
+    }
+    std::lock_guard<std::mutex> lk(g_tmu);
+    for (auto &r : recs) {
+        g_evpool.push_back(r.a);
+        g_evpool.push_back(r.b);
+    }
+    return (int32_t)recs.size();
+}
+
+const char *kc_last_error(void) { return g_err.c_str(); }
+
+void kc_release(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_arenas) {
+        cudaSetDevice(kv.first.first);
+        Arena *a = kv.second;
+        if (a->dev) cudaFree(a->dev);
+        if (a->status) cudaFree(a->status);
+        if (a->host_status) cudaFreeHost(a->host_status);
+        delete a;
+    }
+    g_arenas.clear();
+    cudaSetDevice(cur);
+}
+
+kc_status kc_sync(void *stream) {
+    Arena *a = nullptr;
+    kc_status r = arena_for((cudaStream_t)stream, &a);
+    if (r != KC_OK) return r;
+    return finish(a, (cudaStream_t)stream);
+}
+
+kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t first,
+                      int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts) {
+    g_err.clear();
+    if (!pts || !centers || !k_out || !radius) return fail(KC_ERR_ARG, "null pointer argument");
+    if (n < 1 || n > (int64_t)N_MAX) return fail(KC_ERR_ARG, "n=%lld outside [1, 2^32-2]", (long long)n);
+    if (d < 1) return fail(KC_ERR_ARG, "d=%d must be >= 1", d);
+    if (k < 1) return fail(KC_ERR_ARG, "k=%d must be >= 1", k);
+    if (first < 0 || first >= n) return fail(KC_ERR_ARG, "first=%lld outside [0, n)", (long long)first);
+    CallCtx c;
+    kc_status r = begin(opts, c);
+    if (r != KC_OK) return r;
+
+    const bool dev_pts = is_device_ptr(pts, c.dev);
+    const bool dev_cen = is_device_ptr(centers, c.dev);
+    const bool dev_kout = is_device_ptr(k_out, c.dev);
+    const bool dev_rad = is_device_ptr(radius, c.dev);
+    if (c.async && !(dev_pts && dev_cen && dev_kout && dev_rad))
+        return fail(KC_ERR_ARG, "KC_ASYNC needs device pointers for all arguments");
+
+    const int keff = (int)(k < n ? k : n);
+    const int grid = choose_gon_grid(c.o.dtype, d, n);
+    const int64_t nb = nblocks(n);
+    const size_t esz = 4;
+
+    auto layout = [&](Carve &cv, GonArgs &g, RadiusArgs &ra, void **staging, int64_t **cen_dev,
+                      int32_t **kout_dev, double **rad_dev, size_t *zero_bytes) {
+        // zero-initialised region first
+        int32_t *range2 = cv.take<int32_t>(2);
+        unsigned long long *key32 = cv.take<unsigned long long>(1);
+        unsigned long long *max64 = cv.take<unsigned long long>(1);
+        unsigned long long *arg64 = cv.take<unsigned long long>(1);
+        uint64_t *slots = cv.take<uint64_t>((size_t)keff * grid);
+        *zero_bytes = cv.off;
+        *staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
+        void *pk = cv.take<char>((size_t)nb * BLK * d * esz);
+        uint32_t *mind = cv.take<uint32_t>((size_t)nb * BLK);
+        void *cen = cv.take<char>((size_t)keff * d * esz);
+        double *m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
+        *cen_dev = dev_cen ? centers : cv.take<int64_t>(keff);
+        *kout_dev = dev_kout ? k_out : cv.take<int32_t>(1);
+        *rad_dev = dev_rad ? radius : cv.take<double>(1);
+        g.pk = pk;
+        g.dtype = c.o.dtype;
+        g.n = n;
+        g.d = d;
+        g.k = keff;
+        g.first = first;
+        g.mind = mind;
+        g.slots = slots;
+        g.centers = *cen_dev;
+        g.k_out = *kout_dev;
+        g.final_key = (uint64_t *)key32;
+        g.range2 = range2;
+        g.grid = grid;
+        ra.pk = pk;
+        ra.dtype = c.o.dtype;
+        ra.n = n;
+        ra.d = d;
+        ra.centers = *cen_dev;
+        ra.kc_dev = *kout_dev;
+        ra.kc_max = keff;
+        ra.cen = cen;
+        ra.mind = mind;
+        ra.key32 = key32;
+        ra.max64 = max64;
+        ra.arg64 = arg64;
+        ra.m64 = m64;
+        ra.radius_out = *rad_dev;
+        ra.argmax_out = nullptr;
+        ra.have_mind = true;
+    };
+
+    GonArgs g{};
+    RadiusArgs ra{};
+    void *staging;
+    int64_t *cen_dev;
+    int32_t *kout_dev;
+    double *rad_dev;
+    size_t zero_bytes;
+    {
+        Carve sizing(nullptr);
+        layout(sizing, g, ra, &staging, &cen_dev, &kout_dev, &rad_dev, &zero_bytes);
+        r = arena_reserve(c.arena, sizing.off, c.s);
+        if (r != KC_OK) return r;
+    }
+    Carve cv(c.arena->dev);
+    layout(cv, g, ra, &staging, &cen_dev, &kout_dev, &rad_dev, &zero_bytes);
+    g.st = c.arena->status;
+    ra.st = c.arena->status;
+    g.timeout_cycles = timeout_cycles(c.o);
+
+    KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
+    const void *src;
+    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, staging, &src);
+    if (r != KC_OK) return r;
+    {
+        TraceStep t("pack", c.s);
+        KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)g.pk, (int32_t *)g.range2, c.arena->status, c.s),
+                "pack launch");
+    }
+    {
+        TraceStep t("gonzalez", c.s);
+        KC_CUDA(launch_gon(g, c.s), "gonzalez launch");
+    }
+    {
+        TraceStep t("radius_recheck", c.s);
+        KC_CUDA(launch_radius(ra, c.s), "radius launch");
+    }
+
+    if (!dev_cen)
+        KC_CUDA(cudaMemcpyAsync(centers, cen_dev, (size_t)keff * sizeof(int64_t), cudaMemcpyDeviceToHost, c.s),
+                "copy centers out");
+    if (!dev_kout)
+        KC_CUDA(cudaMemcpyAsync(k_out, kout_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s), "copy k_out");
+    if (!dev_rad)
+        KC_CUDA(cudaMemcpyAsync(radius, rad_dev, sizeof(double), cudaMemcpyDeviceToHost, c.s), "copy radius");
+    if (c.async) return KC_OK;
+    return finish(c.arena, c.s);
+}
+
+kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *centers, int32_t kc,
+                    double *radius, int64_t *argmax_point, const kc_opts *opts) {
+    g_err.clear();
+    if (!pts || !centers || !radius) return fail(KC_ERR_ARG, "null pointer argument");
+    if (n < 1 || n > (int64_t)N_MAX) return fail(KC_ERR_ARG, "n=%lld outside [1, 2^32-2]", (long long)n);
+    if (d < 1) return fail(KC_ERR_ARG, "d=%d must be >= 1", d);
+    if (kc < 1) return fail(KC_ERR_ARG, "kc=%d must be >= 1", kc);
+    CallCtx c;
+    kc_status r = begin(opts, c);
+    if (r != KC_OK) return r;
+
+    const bool dev_pts = is_device_ptr(pts, c.dev);
+    const bool dev_cin = is_device_ptr(centers, c.dev);
+    const bool dev_rad = is_device_ptr(radius, c.dev);
+    const bool dev_arg = argmax_point ? is_device_ptr(argmax_point, c.dev) : true;
+    if (c.async && !(dev_pts && dev_cin && dev_rad && dev_arg))
+        return fail(KC_ERR_ARG, "KC_ASYNC needs device pointers for all arguments");
+    if (!dev_cin) {
+        for (int32_t i = 0; i < kc; ++i)
+            if (centers[i] < 0 || centers[i] >= n)
+                return fail(KC_ERR_ARG, "center %d index %lld outside [0, n)", i, (long long)centers[i]);
+    }
+    const int64_t nb = nblocks(n);
+    const size_t esz = 4;
+
+    RadiusArgs ra{};
+    void *staging = nullptr;
+    const int64_t *cin_dev = nullptr;
+    double *rad_dev = nullptr;
+    int64_t *arg_dev = nullptr;
+    size_t zero_bytes = 0;
+    auto layout = [&](Carve &cv) {
+        int32_t *range2 = cv.take<int32_t>(2);
+        (void)range2;
+        ra.key32 = cv.take<unsigned long long>(1);
+        ra.max64 = cv.take<unsigned long long>(1);
+        ra.arg64 = cv.take<unsigned long long>(1);
+        zero_bytes = cv.off;
+        staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
+        ra.pk = cv.take<char>((size_t)nb * BLK * d * esz);
+        ra.mind = cv.take<uint32_t>((size_t)nb * BLK);
+        ra.cen = cv.take<char>((size_t)kc * d * esz);
+        ra.m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
+        cin_dev = dev_cin ? centers : cv.take<int64_t>(kc);
+        rad_dev = dev_rad ? radius : cv.take<double>(1);
+        arg_dev = (argmax_point && dev_arg) ? argmax_point : cv.take<int64_t>(1);
+    };
+    {
+        Carve sizing(nullptr);
+        layout(sizing);
+        r = arena_reserve(c.arena, sizing.off, c.s);
+        if (r != KC_OK) return r;
+    }
+    Carve cv(c.arena->dev);
+    layout(cv);
+    int32_t *range2 = reinterpret_cast<int32_t *>(c.arena->dev);
+    ra.dtype = c.o.dtype;
+    ra.n = n;
+    ra.d = d;
+    ra.centers = cin_dev;
+    ra.kc_dev = nullptr;
+    ra.kc_max = kc;
+    ra.radius_out = rad_dev;
+    ra.argmax_out = arg_dev;
+    ra.st = c.arena->status;
+    ra.have_mind = false;
+
+    KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
+    const void *src;
+    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, staging, &src);
+    if (r != KC_OK) return r;
+    if (!dev_cin)
+        KC_CUDA(cudaMemcpyAsync((void *)cin_dev, centers, (size_t)kc * sizeof(int64_t), cudaMemcpyHostToDevice, c.s),
+                "copy centers in");
+    {
+        TraceStep t("pack", c.s);
+        KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)ra.pk, range2, c.arena->status, c.s), "pack launch");
+        if (c.o.dtype == KC_I32) KC_CUDA(launch_range_check(range2, d, c.arena->status, c.s), "range check");
+    }
+    {
+        TraceStep t("radius", c.s);
+        KC_CUDA(launch_radius(ra, c.s), "radius launch");
+    }
+    if (!dev_rad)
+        KC_CUDA(cudaMemcpyAsync(radius, rad_dev, sizeof(double), cudaMemcpyDeviceToHost, c.s), "copy radius");
+    if (argmax_point && !dev_arg)
+        KC_CUDA(cudaMemcpyAsync(argmax_point, arg_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s),
+                "copy argmax");
+    if (c.async) return KC_OK;
+    return finish(c.arena, c.s);
+}
+
+}  // extern "C"

@@ -1,0 +1,171 @@
+// kc_internal.cuh -- device helpers and internal launch interfaces shared by
+// the CUDA translation units of the library (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/kcenter.h"
+
+namespace kc {
+
+// Points are repacked into blocks of BLK points, coordinate-major inside a
+// block ("AoSoA"): element (point i, coordinate j) sits at
+//   ((i / BLK) * d + j) * BLK + i % BLK.
+// A warp streams one block: lane l owns points 4l..4l+3 and reads them with
+// one 16-byte load per coordinate, so every warp load is 512 contiguous bytes.
+constexpr int BLK = 128;
+constexpr uint32_t N_MAX = 0xFFFFFFFEu;
+
+__host__ __device__ inline int64_t nblocks(int64_t n) { return (n + BLK - 1) / BLK; }
+__host__ __device__ inline int64_t pk_index(int64_t i, int64_t j, int d) {
+    return ((i / BLK) * d + j) * BLK + (i % BLK);
+}
+
+// Device status word (first error wins).
+struct DevStatus {
+    int32_t code;
+    int32_t where;
+    int64_t info;
+};
+
+__device__ __forceinline__ void set_status(DevStatus *st, int code, int where, int64_t info) {
+    if (atomicCAS(&st->code, 0, code) == 0) {
+        st->where = where;
+        st->info = info;
+    }
+}
+
+// ---------------------------------------------------------------- keys
+// A 64-bit argmax key: the 32-bit value (float bits of a non-negative float,
+// which order like unsigned integers, or an unsigned integer) in the high
+// word and 0xFFFFFFFF - index in the low word.  The unsigned maximum of keys
+// is the largest value, lowest index among equals.  Real points have keys
+// >= 1 because index <= N_MAX.
+__device__ __forceinline__ uint64_t make_key(uint32_t v, uint32_t idx) {
+    return ((uint64_t)v << 32) | (uint64_t)(0xFFFFFFFFu - idx);
+}
+__device__ __forceinline__ uint32_t key_idx(uint64_t k) { return 0xFFFFFFFFu - (uint32_t)k; }
+__device__ __forceinline__ uint32_t key_val(uint64_t k) { return (uint32_t)(k >> 32); }
+
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
+__device__ __forceinline__ uint64_t warp_max_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v = umax64(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ uint64_t ld_acquire_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ int32_t ld_volatile_i32(const int32_t *p) {
+    return *(const volatile int32_t *)p;
+}
+
+// ------------------------------------------------------- squared distance
+// Canonical FP32 term: t = x - c rounded to float, acc = fma(t, t, acc).
+// Zero-padded coordinates (x = c = 0) leave acc unchanged, so padding never
+// alters the value.
+__device__ __forceinline__ float sq_step(float acc, float x, float c) {
+    float t = __fsub_rn(x, c);
+    return __fmaf_rn(t, t, acc);
+}
+// Exact int32 term in 32-bit unsigned arithmetic (the caller guarantees
+// d * range^2 < 2^32, so neither the difference nor the sum wraps).
+__device__ __forceinline__ uint32_t sq_step(uint32_t acc, int32_t x, int32_t c) {
+    uint32_t t = (uint32_t)(x - c);
+    return acc + t * t;
+}
+template <typename T> struct AccOf;
+template <> struct AccOf<float> { using type = float; };
+template <> struct AccOf<int32_t> { using type = uint32_t; };
+
+__device__ __forceinline__ uint32_t acc_bits(float a) { return __float_as_uint(a); }
+__device__ __forceinline__ uint32_t acc_bits(uint32_t a) { return a; }
+
+// int32 exactness check: d * (max - min)^2 < 2^32, where range2 holds the
+// pack kernel's order-preserving maxima of ~bias(v) and bias(v).
+__device__ __forceinline__ bool int_range_ok(const int32_t *range2, int d) {
+    const uint32_t *r = (const uint32_t *)range2;
+    const int64_t mn = (int64_t)(int32_t)((0xFFFFFFFFu - r[0]) ^ 0x80000000u);
+    const int64_t mx = (int64_t)(int32_t)(r[1] ^ 0x80000000u);
+    const uint64_t span = (uint64_t)(mx - mn);
+    if (span >= 65536u) return false;
+    return (uint64_t)d * span * span < (1ull << 32);
+}
+
+// FP64 squared distance in coordinate order, separate multiply and add.
+__device__ __forceinline__ double sq_step64(double acc, float x, float c) {
+    double t = __dsub_rn((double)x, (double)c);
+    return __dadd_rn(acc, __dmul_rn(t, t));
+}
+
+// Relative error bound of the canonical FP32 squared distance against the
+// exact value: (d + 2) u / (1 - (d + 2) u), u = 2^-24 (one rounding in the
+// difference, squared, and one per accumulation).
+__host__ __device__ inline double f32_gamma(int d) {
+    const double u = 5.9604644775390625e-08;
+    const double m = (double)(d + 2) * u;
+    return m / (1.0 - m);
+}
+
+// --------------------------------------------------------- launchers
+// Every launcher reports the number of kernels it launched (tracing and the
+// process-wide launch counter).
+void note_launches(int kernels);
+
+// Repack row-major points into the AoSoA layout (zero padding), checking
+// finiteness (float) or accumulating the coordinate range (int32).
+cudaError_t launch_pack(const void *src, int dtype, int64_t n, int d, void *dst, int32_t *range2,
+                        DevStatus *st, cudaStream_t s);
+// int32 only: record KC_ERR_RANGE unless squared distances fit 32 bits.
+cudaError_t launch_range_check(const int32_t *range2, int d, DevStatus *st, cudaStream_t s);
+
+struct GonArgs {
+    const void *pk;          // packed points
+    int dtype;
+    int64_t n;
+    int d;
+    int k;
+    int64_t first;
+    uint32_t *mind;          // [nblocks*BLK] running minimum (value bits)
+    uint64_t *slots;         // [k * grid] per-iteration, per-CTA argmax keys
+    int64_t *centers;        // [k] out (device)
+    int32_t *k_out;          // out (device)
+    uint64_t *final_key;     // out: key of the largest final minimum
+    const int32_t *range2;   // int32 only: [min, max] of all coordinates
+    DevStatus *st;
+    long long timeout_cycles;
+    int grid;                // CTAs (set by the launcher)
+};
+cudaError_t launch_gon(GonArgs &a, cudaStream_t s);
+int gon_max_grid(int dtype, int d);
+
+struct RadiusArgs {
+    const void *pk;
+    int dtype;
+    int64_t n;
+    int d;
+    const int64_t *centers;  // [kc_max] device indices
+    const int32_t *kc_dev;   // device count (nullptr: use kc_max)
+    int kc_max;
+    void *cen;               // scratch [kc_max * d] gathered center coordinates
+    uint32_t *mind;          // [nblocks*BLK] values (input if have_mind)
+    unsigned long long *key32;   // argmax key of mind (input if have_mind)
+    unsigned long long *max64;   // scratch
+    unsigned long long *arg64;   // scratch
+    double *m64;             // scratch [n] FP64 values of flagged points
+    double *radius_out;      // device out
+    int64_t *argmax_out;     // device out (may be null)
+    DevStatus *st;
+    bool have_mind;          // mind/key32 already hold the FP32 minima
+};
+cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s);
+
+}  // namespace kc

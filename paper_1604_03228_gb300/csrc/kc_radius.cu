@@ -1,0 +1,278 @@
+// kc_radius.cu -- covering radius of a center set (the solution value of
+// Section 7): max over points of the distance to the nearest center.
+//
+//   gather      center coordinates -> scratch [kc][d] (indices validated)
+//   min         canonical FP32 (or exact int32) minimum over centers per
+//               point, plus the (value, lowest index) maximum key
+//   recheck     float only: every point whose FP32 minimum can still reach
+//               the FP64 maximum (within the FP32 error bound) gets its FP64
+//               minimum over all centers; the largest FP64 value wins, then
+//               the lowest index holding it
+//   finalize    radius = sqrt(value), argmax index
+// The FP32 bound: a canonical FP32 squared distance is within a factor
+// (1 +- gamma), gamma = (d+2) 2^-24 / (1 - (d+2) 2^-24), of the exact one, and
+// the FP64 value within (1 +- ~d 2^-53).  So the FP64 maximiser x* satisfies
+// m32(x*) >= M32 (1 - gamma)(1 - g64) / ((1 + gamma)(1 + g64)) > M32 (1 - 3 gamma):
+// flagging m32 >= M32 (1 - 3 gamma) can never miss it.
+#include <type_traits>
+
+#include "kc_internal.cuh"
+
+namespace kc {
+
+namespace {
+
+constexpr int RAD_NT = 256;
+constexpr int RAD_W = RAD_NT / 32;
+constexpr int RAD_TILE_BYTES = 32 * 1024;
+
+template <typename T>
+__global__ void gather_kernel(const T *__restrict__ pk, int64_t n, int d,
+                              const int64_t *__restrict__ centers, const int32_t *kc_dev, int kc_max,
+                              T *__restrict__ cen, DevStatus *st) {
+    const int kc = kc_dev ? *kc_dev : kc_max;
+    const int64_t total = (int64_t)kc * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / d), j = (int)(e - (int64_t)i * d);
+        const int64_t c = centers[i];
+        if (c < 0 || c >= n) {
+            set_status(st, KC_ERR_ARG, 4, i);
+            cen[e] = T(0);
+            continue;
+        }
+        cen[e] = pk[pk_index(c, j, d)];
+    }
+}
+
+// Minimum over all centers for the 4 points of each lane.  Centers are staged
+// through shared memory in tiles with a row stride of DR >= d coordinates,
+// zero-padded (a zero term leaves the canonical sum unchanged), and the
+// lane's points are held in registers when d <= DR.
+template <typename T, int DR>
+__global__ void __launch_bounds__(RAD_NT) radius_min_kernel(
+    const T *__restrict__ pk, int64_t n, int d, const T *__restrict__ cen, const int32_t *kc_dev,
+    int kc_max, uint32_t *__restrict__ mind, unsigned long long *key32, const DevStatus *st) {
+    using A = typename AccOf<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *cs = reinterpret_cast<T *>(smem_raw);
+    if (ld_volatile_i32(&st->code) != 0) return;
+    const int kc = kc_dev ? *kc_dev : kc_max;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t nb = nblocks(n);
+    const int tile = RAD_TILE_BYTES / (DR * (int)sizeof(T));
+    uint64_t best = 0;
+    for (int64_t g = blockIdx.x; g * RAD_W < nb; g += gridDim.x) {
+        const int64_t b = g * RAD_W + warp;
+        const bool active = b < nb;
+        T x[DR][4];
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            x[j][0] = x[j][1] = x[j][2] = x[j][3] = T(0);
+            if (active && j < d) {
+                const T *p = pk + (b * d + j) * BLK + lane * 4;
+                x[j][0] = p[0];
+                x[j][1] = p[1];
+                x[j][2] = p[2];
+                x[j][3] = p[3];
+            }
+        }
+        uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+        for (int t0 = 0; t0 < kc; t0 += tile) {
+            const int tc = (kc - t0) < tile ? (kc - t0) : tile;
+            __syncthreads();
+            for (int e = tid; e < tc * DR; e += RAD_NT) {
+                const int ci = e / DR, j = e - ci * DR;
+                cs[e] = j < d ? cen[(int64_t)(t0 + ci) * d + j] : T(0);
+            }
+            __syncthreads();
+            if (active) {
+                for (int ci = 0; ci < tc; ++ci) {
+                    const T *cc = cs + ci * DR;
+                    A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0);
+#pragma unroll
+                    for (int j = 0; j < DR; ++j) {
+                        const T c = cc[j];
+                        a0 = sq_step(a0, x[j][0], c);
+                        a1 = sq_step(a1, x[j][1], c);
+                        a2 = sq_step(a2, x[j][2], c);
+                        a3 = sq_step(a3, x[j][3], c);
+                    }
+                    m[0] = min(m[0], acc_bits(a0));
+                    m[1] = min(m[1], acc_bits(a1));
+                    m[2] = min(m[2], acc_bits(a2));
+                    m[3] = min(m[3], acc_bits(a3));
+                }
+            }
+        }
+        if (active) {
+            reinterpret_cast<uint4 *>(mind + b * BLK)[lane] = make_uint4(m[0], m[1], m[2], m[3]);
+            const int64_t i0 = b * BLK + lane * 4;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (i0 + q < n) best = umax64(best, make_key(m[q], (uint32_t)(i0 + q)));
+        }
+    }
+    best = warp_max_u64(best);
+    if (lane == 0 && best) atomicMax(key32, (unsigned long long)best);
+}
+
+// Generic version for d > 16: one point per thread, coordinates re-read from
+// the packed layout for every center (cache-resident).
+template <typename T>
+__global__ void __launch_bounds__(RAD_NT) radius_min_generic_kernel(
+    const T *__restrict__ pk, int64_t n, int d, const T *__restrict__ cen, const int32_t *kc_dev,
+    int kc_max, uint32_t *__restrict__ mind, unsigned long long *key32, const DevStatus *st) {
+    using A = typename AccOf<T>::type;
+    if (ld_volatile_i32(&st->code) != 0) return;
+    const int kc = kc_dev ? *kc_dev : kc_max;
+    uint64_t best = 0;
+    for (int64_t x = blockIdx.x * (int64_t)RAD_NT + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * RAD_NT) {
+        uint32_t m = 0xFFFFFFFFu;
+        for (int ci = 0; ci < kc; ++ci) {
+            A a = A(0);
+            for (int j = 0; j < d; ++j) a = sq_step(a, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
+            m = min(m, acc_bits(a));
+        }
+        mind[x] = m;
+        best = umax64(best, make_key(m, (uint32_t)x));
+    }
+    best = warp_max_u64(best);
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(key32, (unsigned long long)best);
+}
+
+__device__ __forceinline__ double flag_threshold(const unsigned long long *key32, int d) {
+    const float M32 = __uint_as_float(key_val(*key32));
+    return (double)M32 * (1.0 - 3.0 * f32_gamma(d));
+}
+
+__device__ double min64(const float *__restrict__ pk, int64_t x, int d, const float *__restrict__ cen,
+                        int kc) {
+    double m = INFINITY;
+    for (int ci = 0; ci < kc; ++ci) {
+        double s = 0.0;
+        for (int j = 0; j < d; ++j) s = sq_step64(s, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
+        m = fmin(m, s);
+    }
+    return m;
+}
+
+__global__ void recheck_max_kernel(const float *__restrict__ pk, int64_t n, int d,
+                                   const float *__restrict__ cen, const int32_t *kc_dev, int kc_max,
+                                   const uint32_t *__restrict__ mind, const unsigned long long *key32,
+                                   unsigned long long *max64, double *m64, const DevStatus *st) {
+    if (ld_volatile_i32(&st->code) != 0) return;
+    if (key_val(*key32) == 0) return;   // every minimum is exactly 0
+    const int kc = kc_dev ? *kc_dev : kc_max;
+    const double thr = flag_threshold(key32, d);
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if ((double)__uint_as_float(mind[x]) >= thr) {
+            const double v = min64(pk, x, d, cen, kc);
+            m64[x] = v;
+            atomicMax(max64, (unsigned long long)__double_as_longlong(v));
+        }
+    }
+}
+
+__global__ void recheck_arg_kernel(int64_t n, int d, const uint32_t *__restrict__ mind,
+                                   const unsigned long long *key32, const unsigned long long *max64,
+                                   const double *__restrict__ m64, unsigned long long *arg64,
+                                   const DevStatus *st) {
+    if (ld_volatile_i32(&st->code) != 0) return;
+    if (key_val(*key32) == 0) return;
+    const double thr = flag_threshold(key32, d);
+    const double M = __longlong_as_double((long long)*max64);
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if ((double)__uint_as_float(mind[x]) >= thr && m64[x] == M)
+            atomicMax(arg64, 0xFFFFFFFFFFFFFFFFull - (unsigned long long)x);
+    }
+}
+
+// One thread: radius and argmax from the FP64 recheck (float) or directly
+// from the exact key (int32).
+__global__ void finalize_kernel(int dtype, const unsigned long long *key32,
+                                const unsigned long long *max64, const unsigned long long *arg64,
+                                double *radius_out, int64_t *argmax_out, const DevStatus *st) {
+    if (ld_volatile_i32(&st->code) != 0) return;
+    const uint64_t K = *key32;
+    double r2;
+    int64_t am;
+    if (dtype == KC_I32 || key_val(K) == 0) {
+        r2 = dtype == KC_I32 ? (double)key_val(K) : 0.0;
+        am = key_idx(K);
+    } else {
+        r2 = __longlong_as_double((long long)*max64);
+        am = (int64_t)(0xFFFFFFFFFFFFFFFFull - *arg64);
+    }
+    *radius_out = __dsqrt_rn(r2);
+    if (argmax_out) *argmax_out = am;
+}
+
+template <typename T, int DR>
+cudaError_t run_min(RadiusArgs &a, cudaStream_t s, int grid) {
+    const int tile = RAD_TILE_BYTES / (DR * (int)sizeof(T));
+    const size_t smem = (size_t)tile * DR * sizeof(T);
+    radius_min_kernel<T, DR><<<grid, RAD_NT, smem, s>>>(
+        (const T *)a.pk, a.n, a.d, (const T *)a.cen, a.kc_dev, a.kc_max, a.mind, a.key32, a.st);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t dispatch_min(RadiusArgs &a, cudaStream_t s, int sms) {
+    const int64_t groups = (nblocks(a.n) + RAD_W - 1) / RAD_W;
+    const int64_t cap = (int64_t)sms * 8;
+    const int grid = (int)(groups < cap ? groups : cap);
+    if (a.d <= 4) return run_min<T, 4>(a, s, grid);
+    if (a.d <= 8) return run_min<T, 8>(a, s, grid);
+    if (a.d <= 16) return run_min<T, 16>(a, s, grid);
+    const int64_t g2 = (a.n + RAD_NT - 1) / RAD_NT;
+    const int grid2 = (int)(g2 < cap ? g2 : cap);
+    radius_min_generic_kernel<T><<<grid2, RAD_NT, 0, s>>>((const T *)a.pk, a.n, a.d,
+                                                          (const T *)a.cen, a.kc_dev, a.kc_max,
+                                                          a.mind, a.key32, a.st);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e;
+    {
+        const int64_t total = (int64_t)a.kc_max * a.d;
+        const int64_t g = (total + 255) / 256;
+        const int grid = (int)(g < 1 ? 1 : (g > sms * 4 ? sms * 4 : g));
+        if (a.dtype == KC_F32)
+            gather_kernel<float><<<grid, 256, 0, s>>>((const float *)a.pk, a.n, a.d, a.centers,
+                                                      a.kc_dev, a.kc_max, (float *)a.cen, a.st);
+        else
+            gather_kernel<int32_t><<<grid, 256, 0, s>>>((const int32_t *)a.pk, a.n, a.d, a.centers,
+                                                        a.kc_dev, a.kc_max, (int32_t *)a.cen, a.st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (!a.have_mind) {
+        e = a.dtype == KC_F32 ? dispatch_min<float>(a, s, sms) : dispatch_min<int32_t>(a, s, sms);
+        if (e != cudaSuccess) return e;
+    }
+    if (a.dtype == KC_F32) {
+        const int64_t g = (a.n + 255) / 256;
+        const int grid = (int)(g > sms * 8 ? sms * 8 : g);
+        recheck_max_kernel<<<grid, 256, 0, s>>>((const float *)a.pk, a.n, a.d, (const float *)a.cen,
+                                                a.kc_dev, a.kc_max, a.mind, a.key32, a.max64, a.m64,
+                                                a.st);
+        recheck_arg_kernel<<<grid, 256, 0, s>>>(a.n, a.d, a.mind, a.key32, a.max64, a.m64, a.arg64,
+                                                a.st);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    finalize_kernel<<<1, 1, 0, s>>>(a.dtype, a.key32, a.max64, a.arg64, a.radius_out, a.argmax_out,
+                                    a.st);
+    note_launches(2 + (a.have_mind ? 0 : 1) + (a.dtype == KC_F32 ? 2 : 0));
+    return cudaGetLastError();
+}
+
+}  // namespace kc

@@ -1,0 +1,189 @@
+"""GPU parity of kc_gonzalez / kc_radius against the CPU oracle (C ABI path).
+
+Integer points: bit-exact center sequences and squared radius (exact int64
+oracle).  Float points: the argmax is decided in canonical FP32 on both sides,
+so the center sequence must equal the oracle's "f32" selection exactly; the
+returned radius must equal the oracle's FP64 covering radius of those centers
+exactly (same FP64 operation order); and against the plain FP64 definition
+every selection must be within 1e-6 relative of that step's true maximum
+distance, and the radius within 1e-6 relative of the FP64 GON radius.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1604_03228_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+REL = 1e-6
+
+
+def _dev(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def check_float_gon(kc, pts, k, first=0, res=None):
+    res = res or kc.kc_gonzalez(_dev(pts), k, first=first)
+    got = res.centers.cpu().numpy()
+    ref = O.gonzalez(pts, k, first=first, mode="f32")
+    assert np.array_equal(got, ref.centers), (got[:20], ref.centers[:20])
+    assert res.k_out == len(ref.centers)
+    r64 = O.radius(pts, got, mode="f64")[0]
+    assert res.radius == r64
+    # tolerance checks against the plain FP64 definition (spec bar)
+    sel2, max2 = O.eval_sequence(pts, got, mode="f64")
+    for j in range(1, len(got)):
+        assert math.sqrt(sel2[j]) >= (1 - REL) * math.sqrt(max2[j])
+    g64 = O.gonzalez(pts, k, first=first, mode="f64")
+    if np.array_equal(g64.centers, got):
+        assert abs(res.radius - g64.radius) <= REL * g64.radius
+    return res
+
+
+def check_int_gon(kc, pts, k, first=0):
+    res = kc.kc_gonzalez(_dev(pts), k, first=first)
+    ref = O.gonzalez(pts, k, first=first)
+    got = res.centers.cpu().numpy()
+    assert np.array_equal(got, ref.centers), (got[:20], ref.centers[:20])
+    assert res.radius == math.sqrt(ref.radius2)
+    return res
+
+
+@pytest.mark.parametrize("name", ["gon_int_n10000_d2_k10", "gon_int13_n1000000_d10_k100"])
+def test_int_goldens_bit_exact(kc, name):
+    g = json.load(open(os.path.join(GOLDEN, name + ".json")))
+    w = I.gon_int_10k() if g["n"] == 10000 else I.gon_int13_1m()
+    res = kc.kc_gonzalez(_dev(w.points), g["k"], first=g["first"])
+    assert res.centers.cpu().numpy().tolist() == g["centers"]
+    assert res.radius == math.sqrt(g["radius2"])
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 127, 128, 129, 1023, 4097, 20000])
+@pytest.mark.parametrize("d", [1, 2, 3, 10, 17])
+def test_float_sizes(kc, n, d):
+    pts = I.gauss_mixture(n, d, 7 * n + d, 5, 1.0, -20.0, 20.0)
+    ks = {1, 2, min(n, 7), min(n, 100)} | ({n} if n <= 1023 else set())
+    for k in sorted(ks):
+        check_float_gon(kc, pts, k)
+
+
+@pytest.mark.parametrize("d", [8, 16, 32, 64])
+def test_float_dims_specialised(kc, d):
+    pts = I.gauss_mixture(3001, d, 11 + d, 9, 0.5, -10.0, 10.0)
+    check_float_gon(kc, pts, 40, first=17)
+
+
+@pytest.mark.parametrize("n,d", [(5, 1), (300, 2), (4099, 3), (20000, 10)])
+def test_int_small_coords_ties(kc, n, d):
+    pts = I.int_points(n, d, 5 + n, 1, 6)       # heavy ties and duplicates
+    for k in (1, 2, 13, n):
+        check_int_gon(kc, pts, k)
+
+
+def test_collinear_closed_form_on_gpu(kc):
+    for j in (3, 6, 10):
+        n = 2 ** j + 1
+        pts = I.collinear_points(n, d=2)
+        res = kc.kc_gonzalez(_dev(pts), n)
+        seq = [0, n - 1]
+        step = n - 1
+        while step > 1:
+            seq += list(range(step // 2, n, step))
+            step //= 2
+        assert res.centers.cpu().numpy().tolist() == seq and res.radius == 0.0
+        for k in (2, 3, 5, n - 1):
+            r = kc.kc_gonzalez(_dev(pts), k)
+            t = int(math.floor(math.log2(k - 1)))
+            assert r.radius == (n - 1) / 2 ** (t + 1)
+
+
+def test_duplicates_stop_early(kc):
+    pts = np.repeat(I.int_points(7, 3, 9, -50, 50), 40, axis=0)
+    res = check_int_gon(kc, pts, 20)
+    assert res.k_out == 7 and res.radius == 0.0
+    f = pts.astype(np.float32) * np.float32(0.1)
+    r = check_float_gon(kc, f, 20)
+    assert r.k_out == 7 and r.radius == 0.0
+    same = np.zeros((1000, 4), dtype=np.float32) + np.float32(3.5)
+    r = kc.kc_gonzalez(_dev(same), 5)
+    assert r.k_out == 1 and r.radius == 0.0 and r.centers.cpu().tolist() == [0]
+
+
+def test_first_center_and_negative_coords(kc):
+    pts = I.gauss_mixture(10000, 5, 3, 4, 2.0, -1e3, -5e2)
+    for first in (0, 9999, 4242):
+        check_float_gon(kc, pts, 25, first=first)
+
+
+def test_host_and_device_pointers_agree(kc):
+    import torch
+    pts = I.gauss_mixture(7777, 6, 21, 6, 1.0, -5, 5)
+    a = kc.kc_gonzalez(_dev(pts), 30)
+    b = kc.kc_gonzalez(pts, 30)                                   # numpy (pageable host)
+    c = kc.kc_gonzalez(torch.from_numpy(pts).pin_memory(), 30)    # pinned host
+    assert a.centers.cpu().numpy().tolist() == b.centers.tolist() == c.centers.tolist()
+    assert a.radius == b.radius == c.radius
+
+
+def test_config_gau_1m_full(kc):
+    w = I.gon_gau_1m()
+    res = kc.kc_gonzalez(_dev(w.points), w.k)
+    check_float_gon(kc, w.points, w.k, res=res)
+    rr = kc.kc_radius(_dev(w.points), res.centers)
+    r64, am, _ = O.radius(w.points, res.centers.cpu().numpy(), mode="f64")
+    assert rr.radius == r64 and rr.argmax == am
+
+
+# ------------------------------------------------------------------ radius
+
+@pytest.mark.parametrize("n,d,kc_", [(1, 1, 1), (129, 3, 5), (5000, 10, 100), (3000, 16, 600),
+                                      (2000, 17, 33), (1500, 64, 70)])
+def test_radius_float(kc, n, d, kc_):
+    pts = I.gauss_mixture(n, d, 100 + d, 7, 1.0, -30, 30)
+    C = I.uniform_int(55, d, kc_, 0, n - 1)
+    rr = kc.kc_radius(_dev(pts), _dev(C))
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    assert rr.radius == r64 and rr.argmax == am
+    rh = kc.kc_radius(pts, C)                   # host pointers
+    assert rh.radius == r64 and rh.argmax == am
+
+
+@pytest.mark.parametrize("n,d,kc_", [(1000, 2, 10), (4097, 10, 64), (999, 20, 7)])
+def test_radius_int(kc, n, d, kc_):
+    pts = I.int_points(n, d, 300 + d, -20, 20)
+    C = I.uniform_int(56, d, kc_, 0, n - 1)
+    rr = kc.kc_radius(_dev(pts), _dev(C))
+    r, am, r2 = O.radius(pts, C)
+    assert rr.radius == math.sqrt(r2) and rr.argmax == am
+
+
+def test_radius_all_points_are_centers(kc):
+    pts = I.gauss_mixture(300, 3, 5, 3, 1.0, 0, 1)
+    rr = kc.kc_radius(_dev(pts), _dev(np.arange(300)))
+    assert rr.radius == 0.0 and rr.argmax == 0
+
+
+# ------------------------------------------------------------------ errors
+
+def test_errors_are_status_codes(kc):
+    bad = I.gauss_mixture(500, 3, 1, 2, 1.0, 0, 1)
+    bad[123, 1] = np.nan
+    with pytest.raises(kc.KCError) as e:
+        kc.kc_gonzalez(_dev(bad), 5)
+    assert e.value.status == kc.KC_ERR_NONFINITE
+    big = np.array([[0, 0], [70000, 0]], dtype=np.int32)
+    with pytest.raises(kc.KCError) as e:
+        kc.kc_gonzalez(_dev(big), 2)
+    assert e.value.status == kc.KC_ERR_RANGE
+    with pytest.raises(kc.KCError) as e:
+        kc.kc_radius(_dev(bad[:10]), _dev(np.array([0, 10])))
+    assert e.value.status in (kc.KC_ERR_ARG, kc.KC_ERR_NONFINITE)
+    # the library stays usable after errors
+    ok = I.gauss_mixture(500, 3, 1, 2, 1.0, 0, 1)
+    check_float_gon(kc, ok, 5)
