@@ -111,6 +111,32 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
                     double *radius, int64_t *argmax_point, const kc_opts *opts);
 
 /*
+ * kc_gonzalez_noalloc -- the same Gonzalez selection as kc_gonzalez, for
+ * callers that must not allocate device memory during a call.  The paper has
+ * no counterpart; this is a deployment variant.  cudaMalloc/cudaFree can
+ * synchronise the whole device (stalling latency-critical loops such as a
+ * serving loop), and a process whose HBM is already held by another
+ * allocator may not get a fresh allocation at all.  This entry point takes
+ * all of its scratch from one static device array of KC_NOALLOC_MAX_BYTES
+ * (64 MiB), which every GPU that loads the library keeps until the process
+ * exits, and calls no allocating routine.
+ *   Arguments and results are those of kc_gonzalez, except: every pointer
+ *   must be device memory of the current device; opts->flags must be 0 (the
+ *   call always waits and returns the final status); inputs needing more
+ *   than KC_NOALLOC_MAX_BYTES of scratch (about n * (4 d + 12) bytes for
+ *   float points, n * (4 d + 4) for int32) are rejected with KC_ERR_ARG and
+ *   a message naming the size, before any work is enqueued.
+ *   The first call on a device looks up the array's address
+ *   (cudaGetSymbolAddress, with that device current); make that first call
+ *   before any stream capture.  All calls share the array and each clears
+ *   what must start at zero; calls whose GPU work overlaps in time (other
+ *   threads or streams) race on it and must be serialised by the caller.
+ */
+#define KC_NOALLOC_MAX_BYTES (64 * 1024 * 1024)
+kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, int32_t k, int64_t first,
+                              int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts);
+
+/*
  * kc_sync -- wait for all work enqueued on `stream` and return (and clear)
  * the device status word of that stream's scratch: KC_OK, or the first error
  * a kernel recorded since the last kc_sync / synchronous call.

@@ -53,6 +53,8 @@ def load(path: str | None = None):
     L.kc_gonzalez.argtypes = [vp, i64, i32, i32, i64, vp, vp, vp, popts]
     L.kc_radius.restype = ct.c_int
     L.kc_radius.argtypes = [vp, i64, i32, vp, i32, vp, vp, popts]
+    L.kc_gonzalez_noalloc.restype = ct.c_int
+    L.kc_gonzalez_noalloc.argtypes = [vp, i64, i32, i32, i64, vp, vp, vp, popts]
     L.kc_sync.restype = ct.c_int
     L.kc_sync.argtypes = [vp]
     L.kc_last_error.restype = ct.c_char_p
@@ -212,6 +214,30 @@ def kc_gonzalez(points, k: int, first: int = 0, *, stream=None, flags: int = 0,
         return centers, k_out, radius
     kk = int(_item(k_out))
     return GonResult(centers[:kk], kk, float(_item(radius)))
+
+
+def kc_gonzalez_noalloc(points, k: int, first: int = 0, *, stream=None, timeout_ms: int = 0,
+                        out=None):
+    """GON through the entry point that allocates nothing (all scratch in a
+    fixed static device array; device tensors only).  For callers that must
+    not allocate device memory during a call: see include/kcenter.h."""
+    L = load()
+    p, n, d, code = _points(points)
+    if not (_is_torch(p) and p.is_cuda):
+        raise TypeError("kc_gonzalez_noalloc takes CUDA tensors")
+    torch = _torch()
+    if out is None:
+        centers = torch.empty(k, dtype=torch.int64, device=p.device)
+        k_out = torch.empty(1, dtype=torch.int32, device=p.device)
+        radius = torch.empty(1, dtype=torch.float64, device=p.device)
+    else:
+        centers, k_out, radius = out
+    o = _opts(code, p, stream, 0, timeout_ms)
+    st = L.kc_gonzalez_noalloc(_ptr(p), n, d, k, first, _ptr(centers), _ptr(k_out), _ptr(radius),
+                               ct.byref(o))
+    _check(L, st)
+    kk = int(k_out[0].item())
+    return GonResult(centers[:kk], kk, float(radius[0].item()))
 
 
 def kc_radius(points, centers, *, stream=None, flags: int = 0, timeout_ms: int = 0, out=None):

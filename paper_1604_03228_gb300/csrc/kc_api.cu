@@ -290,6 +290,7 @@ void note_launches(int kernels) {
     g_launches += kernels;
     t_kernels += kernels;
 }
+void set_last_error(const char *text) { g_err = text ? text : ""; }
 }  // namespace kc
 
 extern "C" {
