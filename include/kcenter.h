@@ -111,6 +111,39 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
                     double *radius, int64_t *argmax_point, const kc_opts *opts);
 
 /*
+ * kc_mrg -- MRG, the two-round MapReduce Gonzalez of Algorithm 1 (Section
+ * 3.1) with its 4-approximation (Lemma 2).  Round 1: the points are split into
+ * m parts with contiguous index ranges; GON runs on every part (first center =
+ * the part's lowest index) and returns up to k centers per part.  Round 2: the
+ * union of those centers, in ascending index order, runs GON (first center =
+ * its lowest index).  On one GPU the m "reducers" of round 1 run side by side
+ * in one persistent launch, each part on a group of CTAs sized to its work.
+ *   offsets  [m+1] int64 part boundaries (part i = [offsets[i], offsets[i+1]),
+ *            offsets[0] = 0, offsets[m] = n, every part non-empty), host or
+ *            device; NULL = balanced split offsets[i] = floor(i n / m), so no
+ *            part exceeds ceil(n/m) points as Algorithm 1 asks.
+ *   centers  [k] int64 out: round-2 selection (point indices, in order).
+ *   k_out    int32 out: number of centers; radius: covering radius over all n.
+ * Errors: KC_ERR_ARG for m outside [1, n] or bad offsets; others as kc_gonzalez.
+ */
+kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, const int64_t *offsets,
+                 int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts);
+
+/*
+ * kc_gonzalez_batch -- GON on `count` independent instances in one
+ * persistent launch (the simulated parallel machines of Section 7.1, one
+ * instance per machine).  Instance i has points pts[i] (row-major n[i] x d[i],
+ * host or device), selects up to k[i] centers from its point 0, and writes
+ * centers[i][0 .. k_out[i]) (indices local to the instance) and radii[i].
+ * n, d, k, pts and centers are host arrays of `count` entries; k_out and radii
+ * are [count] arrays in host or device memory.  Instances are processed
+ * longest-first (n k d).  Errors: as kc_gonzalez, per instance.
+ */
+kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d,
+                            const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
+                            const kc_opts *opts);
+
+/*
  * kc_gonzalez_noalloc -- the same Gonzalez selection as kc_gonzalez, for
  * callers that must not allocate device memory during a call.  The paper has
  * no counterpart; this is a deployment variant.  cudaMalloc/cudaFree can

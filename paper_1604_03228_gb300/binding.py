@@ -55,6 +55,10 @@ def load(path: str | None = None):
     L.kc_radius.argtypes = [vp, i64, i32, vp, i32, vp, vp, popts]
     L.kc_gonzalez_noalloc.restype = ct.c_int
     L.kc_gonzalez_noalloc.argtypes = [vp, i64, i32, i32, i64, vp, vp, vp, popts]
+    L.kc_mrg.restype = ct.c_int
+    L.kc_mrg.argtypes = [vp, i64, i32, i32, i32, vp, vp, vp, vp, popts]
+    L.kc_gonzalez_batch.restype = ct.c_int
+    L.kc_gonzalez_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, popts]
     L.kc_sync.restype = ct.c_int
     L.kc_sync.argtypes = [vp]
     L.kc_last_error.restype = ct.c_char_p
@@ -260,6 +264,66 @@ def kc_radius(points, centers, *, stream=None, flags: int = 0, timeout_ms: int =
     if flags & KC_ASYNC:
         return radius, argmax
     return RadiusResult(float(_item(radius)), int(_item(argmax)))
+
+
+def kc_mrg(points, k: int, m: int, offsets=None, *, stream=None, flags: int = 0,
+           timeout_ms: int = 0, out=None):
+    """Two-round MRG (Algorithm 1) through the C ABI.  offsets: [m+1] part
+    boundaries (array/tensor) or None for the balanced split."""
+    L = load()
+    p, n, d, code = _points(points)
+    off = None
+    if offsets is not None:
+        if _is_torch(offsets):
+            off = offsets.to(_torch().int64).contiguous()
+        else:
+            off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if int(off.shape[0]) != m + 1:
+            raise ValueError("offsets must have m+1 entries")
+    if out is None:
+        centers = _empty_like_place(p, k, np.int64)
+        k_out = _empty_like_place(p, 1, np.int32)
+        radius = _empty_like_place(p, 1, np.float64)
+    else:
+        centers, k_out, radius = out
+    o = _opts(code, p, stream, flags, timeout_ms)
+    st = L.kc_mrg(_ptr(p), n, d, k, m, _ptr(off), _ptr(centers), _ptr(k_out), _ptr(radius), ct.byref(o))
+    _check(L, st)
+    if flags & KC_ASYNC:
+        return centers, k_out, radius
+    kk = int(_item(k_out))
+    return GonResult(centers[:kk], kk, float(_item(radius)))
+
+
+def kc_gonzalez_batch(points_list, ks, *, stream=None, flags: int = 0, timeout_ms: int = 0):
+    """GON on many independent instances (one persistent launch) through the
+    C ABI.  Returns [GonResult] in input order (centers local to each instance)."""
+    L = load()
+    count = len(points_list)
+    if count != len(ks):
+        raise ValueError("one k per instance")
+    ps = [_points(x) for x in points_list]
+    codes = {c for (_, _, _, c) in ps}
+    if len(codes) != 1:
+        raise TypeError("all instances must share one dtype")
+    ref = ps[0][0]
+    ptrs = (ct.c_void_p * count)(*[_ptr(p) for (p, _, _, _) in ps])
+    ns = np.array([n for (_, n, _, _) in ps], dtype=np.int64)
+    ds = np.array([d for (_, _, d, _) in ps], dtype=np.int32)
+    kk = np.array([int(k) for k in ks], dtype=np.int32)
+    outs = [_empty_like_place(p, max(1, min(int(k), n)), np.int64) for (p, n, _, _), k in zip(ps, ks)]
+    cptrs = (ct.c_void_p * count)(*[_ptr(c) for c in outs])
+    k_out = _empty_like_place(ref, count, np.int32)
+    radii = _empty_like_place(ref, count, np.float64)
+    o = _opts(codes.pop(), ref, stream, flags, timeout_ms)
+    st = L.kc_gonzalez_batch(count, ptrs, ns.ctypes.data, ds.ctypes.data, kk.ctypes.data, cptrs,
+                             _ptr(k_out), _ptr(radii), ct.byref(o))
+    _check(L, st)
+    if flags & KC_ASYNC:
+        return outs, k_out, radii
+    ko = k_out.cpu().numpy() if _is_torch(k_out) else k_out
+    rr = radii.cpu().numpy() if _is_torch(radii) else radii
+    return [GonResult(outs[i][:int(ko[i])], int(ko[i]), float(rr[i])) for i in range(count)]
 
 
 def kc_sync(stream=None) -> int:

@@ -1,13 +1,15 @@
 // kc_api.cu -- the C ABI (include/kcenter.h): argument checks, host/device
 // pointer handling, cached device scratch, and the launch sequence of each
 // entry point.  All arithmetic of the method runs in the kernels.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
-#include <atomic>
 #include <utility>
 #include <vector>
 
@@ -104,7 +106,36 @@ struct Arena {
     size_t bytes = 0;
     DevStatus *status = nullptr;   // persistent across calls on this stream
     DevStatus *host_status = nullptr;
+    char *pinned = nullptr;        // staging for descriptor uploads
+    size_t pinned_bytes = 0;
+    cudaEvent_t pinned_ev = nullptr;
+    bool pinned_busy = false;
 };
+
+// Copy `bytes` of host data to device memory `dst` in stream order through
+// the arena's pinned staging buffer (waiting first for the previous upload
+// from that buffer to finish).
+kc_status upload(Arena *a, cudaStream_t s, const void *src, size_t bytes, void *dst) {
+    if (bytes == 0) return KC_OK;
+    if (a->pinned_busy) {
+        KC_CUDA(cudaEventSynchronize(a->pinned_ev), "cudaEventSynchronize");
+        a->pinned_busy = false;
+    }
+    if (bytes > a->pinned_bytes) {
+        if (a->pinned) cudaFreeHost(a->pinned);
+        a->pinned = nullptr;
+        a->pinned_bytes = 0;
+        const size_t want = bytes + bytes / 4 + 4096;
+        KC_CUDA(cudaMallocHost(&a->pinned, want), "pinned staging allocation");
+        a->pinned_bytes = want;
+    }
+    if (!a->pinned_ev) KC_CUDA(cudaEventCreateWithFlags(&a->pinned_ev, cudaEventDisableTiming), "cudaEventCreate");
+    memcpy(a->pinned, src, bytes);
+    KC_CUDA(cudaMemcpyAsync(dst, a->pinned, bytes, cudaMemcpyHostToDevice, s), "descriptor upload");
+    KC_CUDA(cudaEventRecord(a->pinned_ev, s), "cudaEventRecord");
+    a->pinned_busy = true;
+    return KC_OK;
+}
 
 std::mutex g_mu;
 std::map<std::pair<int, uintptr_t>, Arena *> g_arenas;
@@ -340,6 +371,9 @@ void kc_release(void) {
         if (a->dev) cudaFree(a->dev);
         if (a->status) cudaFree(a->status);
         if (a->host_status) cudaFreeHost(a->host_status);
+        if (a->pinned_busy) cudaEventSynchronize(a->pinned_ev);
+        if (a->pinned) cudaFreeHost(a->pinned);
+        if (a->pinned_ev) cudaEventDestroy(a->pinned_ev);
         delete a;
     }
     g_arenas.clear();
@@ -394,19 +428,8 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         *cen_dev = dev_cen ? centers : cv.take<int64_t>(keff);
         *kout_dev = dev_kout ? k_out : cv.take<int32_t>(1);
         *rad_dev = dev_rad ? radius : cv.take<double>(1);
-        g.pk = pk;
-        g.dtype = c.o.dtype;
-        g.n = n;
-        g.d = d;
-        g.k = keff;
-        g.first = first;
-        g.mind = mind;
-        g.slots = slots;
-        g.centers = *cen_dev;
-        g.k_out = *kout_dev;
-        g.final_key = (uint64_t *)key32;
-        g.range2 = range2;
-        g.grid = grid;
+        gon_single(g, pk, c.o.dtype, n, d, keff, first, mind, slots, *cen_dev, *kout_dev,
+                   (uint64_t *)key32, range2, grid);
         ra.pk = pk;
         ra.dtype = c.o.dtype;
         ra.n = n;
@@ -450,7 +473,8 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     if (r != KC_OK) return r;
     {
         TraceStep t("pack", c.s);
-        KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)g.pk, (int32_t *)g.range2, c.arena->status, c.s),
+        KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)g.single.pk, (int32_t *)g.single.range2,
+                            c.arena->status, c.s),
                 "pack launch");
     }
     {
@@ -561,6 +585,437 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
     if (argmax_point && !dev_arg)
         KC_CUDA(cudaMemcpyAsync(argmax_point, arg_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s),
                 "copy argmax");
+    if (c.async) return KC_OK;
+    return finish(c.arena, c.s);
+}
+
+kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, const int64_t *offsets,
+                 int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts) {
+    g_err.clear();
+    if (!pts || !centers || !k_out || !radius) return fail(KC_ERR_ARG, "null pointer argument");
+    if (n < 1 || n > (int64_t)N_MAX) return fail(KC_ERR_ARG, "n=%lld outside [1, 2^32-2]", (long long)n);
+    if (d < 1) return fail(KC_ERR_ARG, "d=%d must be >= 1", d);
+    if (k < 1) return fail(KC_ERR_ARG, "k=%d must be >= 1", k);
+    if (m < 1 || m > n) return fail(KC_ERR_ARG, "m=%d must be in [1, n]", m);
+    CallCtx c;
+    kc_status r = begin(opts, c);
+    if (r != KC_OK) return r;
+    const bool dev_pts = is_device_ptr(pts, c.dev);
+    const bool dev_cen = is_device_ptr(centers, c.dev);
+    const bool dev_kout = is_device_ptr(k_out, c.dev);
+    const bool dev_rad = is_device_ptr(radius, c.dev);
+    if (c.async && !(dev_pts && dev_cen && dev_kout && dev_rad && (!offsets || is_device_ptr(offsets, c.dev))))
+        return fail(KC_ERR_ARG, "KC_ASYNC needs device pointers for all arguments");
+
+    // Parts: the given offsets, else the balanced split off[i] = floor(i n / m)
+    // (every part has at most ceil(n/m) points, Algorithm 1).
+    std::vector<int64_t> off((size_t)m + 1);
+    if (offsets) {
+        if (is_device_ptr(offsets, c.dev)) {
+            KC_CUDA(cudaMemcpyAsync(off.data(), offsets, off.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, c.s),
+                    "copy offsets");
+            KC_CUDA(cudaStreamSynchronize(c.s), "cudaStreamSynchronize");
+        } else {
+            memcpy(off.data(), offsets, off.size() * sizeof(int64_t));
+        }
+    } else {
+        for (int i = 0; i <= m; ++i) off[i] = (int64_t)((__int128)i * n / m);
+    }
+    if (off[0] != 0 || off[m] != n) return fail(KC_ERR_ARG, "offsets must start at 0 and end at n");
+    for (int i = 0; i < m; ++i)
+        if (off[i + 1] <= off[i]) return fail(KC_ERR_ARG, "part %d is empty or offsets decrease", i);
+
+    // Round-1 CTA groups: proportional to each part's work n_i * k_i, at least
+    // one CTA, at most one per 32 blocks (one block per warp), within the
+    // co-resident grid.  More parts than CTAs: one CTA per part from a queue.
+    const int maxg = gon_max_grid(c.o.dtype, d);
+    const int W = gon_warps_per_cta();
+    std::vector<int> G((size_t)m, 1), ki((size_t)m);
+    std::vector<int64_t> slot_off((size_t)m + 1, 0);
+    const bool queue1 = m > maxg;
+    {
+        double tot = 0;
+        std::vector<double> work((size_t)m);
+        for (int i = 0; i < m; ++i) {
+            const int64_t ni = off[i + 1] - off[i];
+            ki[i] = (int)(k < ni ? k : ni);
+            work[i] = (double)ni * ki[i];
+            tot += work[i];
+        }
+        if (!queue1) {
+            std::vector<int> cap((size_t)m);
+            int sum = 0;
+            for (int i = 0; i < m; ++i) {
+                const int64_t nbi = nblocks(off[i + 1] - off[i]) + 1;
+                cap[i] = (int)std::max<int64_t>(1, (nbi + W - 1) / W);
+                G[i] = (int)std::max(1.0, std::floor(maxg * work[i] / tot));
+                G[i] = std::min(G[i], cap[i]);
+                sum += G[i];
+            }
+            while (sum > maxg) {   // trim the largest groups
+                int j = 0;
+                for (int i = 1; i < m; ++i) if (G[i] > G[j]) j = i;
+                if (G[j] <= 1) break;
+                --G[j];
+                --sum;
+            }
+            while (sum < maxg) {   // hand out the rest to the most loaded CTAs
+                int j = -1;
+                double best = 0;
+                for (int i = 0; i < m; ++i)
+                    if (G[i] < cap[i] && work[i] / G[i] > best) {
+                        best = work[i] / G[i];
+                        j = i;
+                    }
+                if (j < 0) break;
+                ++G[j];
+                ++sum;
+            }
+        }
+        for (int i = 0; i < m; ++i) slot_off[i + 1] = slot_off[i] + (queue1 ? 0 : (int64_t)ki[i] * G[i]);
+    }
+    int grid1 = 0;
+    for (int i = 0; i < m; ++i) grid1 += G[i];
+    if (queue1) grid1 = gon_queue_grid(c.o.dtype, d);
+    const int64_t ucap = (int64_t)m * k;
+    const int G2 = (int)std::min<int64_t>(std::max<int64_t>(1, (nblocks(ucap) + W - 1) / W), std::min(maxg, 16));
+    const int64_t nb = nblocks(n);
+    const size_t esz = 4;
+
+    struct L {
+        int32_t *range2;
+        unsigned long long *key32, *max64, *arg64;
+        uint64_t *slots1, *slots2, *fk2;
+        int64_t *nU;
+        int *counter;
+        void *staging, *pk, *pkU, *cen;
+        uint32_t *mind, *mindU;
+        int64_t *c1, *U;
+        int32_t *k1;
+        uint64_t *fk1;
+        GonInst *insts1, *inst2;
+        double *m64;
+        int64_t *cen_dev;
+        int32_t *kout_dev;
+        double *rad_dev;
+        size_t zero_bytes;
+    } Lo{};
+    auto layout = [&](Carve &cv) {
+        Lo.range2 = cv.take<int32_t>(2);
+        Lo.key32 = cv.take<unsigned long long>(1);
+        Lo.max64 = cv.take<unsigned long long>(1);
+        Lo.arg64 = cv.take<unsigned long long>(1);
+        Lo.fk2 = cv.take<uint64_t>(1);
+        Lo.nU = cv.take<int64_t>(1);
+        Lo.counter = cv.take<int>(1);
+        Lo.slots1 = cv.take<uint64_t>((size_t)std::max<int64_t>(1, slot_off[m]));
+        Lo.slots2 = cv.take<uint64_t>((size_t)k * G2);
+        Lo.zero_bytes = cv.off;
+        Lo.staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
+        Lo.pk = cv.take<char>((size_t)nb * BLK * d * esz);
+        Lo.mind = cv.take<uint32_t>((size_t)nb * BLK);
+        Lo.c1 = cv.take<int64_t>((size_t)ucap);
+        Lo.k1 = cv.take<int32_t>((size_t)m);
+        Lo.fk1 = cv.take<uint64_t>((size_t)m);
+        Lo.U = cv.take<int64_t>((size_t)ucap);
+        Lo.pkU = cv.take<char>((size_t)nblocks(ucap) * BLK * d * esz);
+        Lo.mindU = cv.take<uint32_t>((size_t)nblocks(ucap) * BLK);
+        Lo.insts1 = cv.take<GonInst>((size_t)m);
+        Lo.inst2 = cv.take<GonInst>(1);
+        Lo.cen = cv.take<char>((size_t)k * d * esz);
+        Lo.m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
+        Lo.cen_dev = dev_cen ? centers : cv.take<int64_t>((size_t)k);
+        Lo.kout_dev = dev_kout ? k_out : cv.take<int32_t>(1);
+        Lo.rad_dev = dev_rad ? radius : cv.take<double>(1);
+    };
+    {
+        Carve sizing(nullptr);
+        layout(sizing);
+        r = arena_reserve(c.arena, sizing.off, c.s);
+        if (r != KC_OK) return r;
+    }
+    Carve cv(c.arena->dev);
+    layout(cv);
+    DevStatus *st = c.arena->status;
+
+    // Round-1 descriptors (host-built, uploaded once).
+    std::vector<GonInst> h1((size_t)m);
+    {
+        int cta = 0;
+        for (int i = 0; i < m; ++i) {
+            GonInst &I = h1[i];
+            memset(&I, 0, sizeof I);
+            I.pk = Lo.pk;
+            I.mind = Lo.mind;
+            I.slots = Lo.slots1 + slot_off[i];
+            I.centers = Lo.c1 + (int64_t)i * k;
+            I.k_out = Lo.k1 + i;
+            I.final_key = Lo.fk1 + i;
+            I.map = nullptr;
+            I.range2 = Lo.range2;
+            I.radius_out = nullptr;
+            I.lo = off[i];
+            I.n = off[i + 1] - off[i];
+            I.base = off[i];
+            I.first = 0;
+            I.d = d;
+            I.k = ki[i];
+            I.cta0 = queue1 ? 0 : cta;
+            I.G = queue1 ? 1 : G[i];
+            cta += I.G;
+        }
+    }
+    GonInst proto;
+    memset(&proto, 0, sizeof proto);
+    proto.pk = Lo.pkU;
+    proto.mind = Lo.mindU;
+    proto.slots = Lo.slots2;
+    proto.centers = Lo.cen_dev;
+    proto.k_out = Lo.kout_dev;
+    proto.final_key = Lo.fk2;
+    proto.map = Lo.U;
+    proto.range2 = Lo.range2;
+    proto.d = d;
+    proto.cta0 = 0;
+    proto.G = G2;
+
+    KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, Lo.zero_bytes, c.s), "scratch clear");
+    const void *src;
+    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, Lo.staging, &src);
+    if (r != KC_OK) return r;
+    r = upload(c.arena, c.s, h1.data(), h1.size() * sizeof(GonInst), Lo.insts1);
+    if (r != KC_OK) return r;
+    const long long tmo = timeout_cycles(c.o);
+    {
+        TraceStep t("pack", c.s);
+        KC_CUDA(launch_pack(src, c.o.dtype, n, d, Lo.pk, Lo.range2, st, c.s), "pack launch");
+    }
+    {
+        TraceStep t("mrg_round1", c.s);
+        GonArgs g{};
+        g.insts = Lo.insts1;
+        g.ninst = m;
+        g.dtype = c.o.dtype;
+        g.dc = d;
+        g.dmax = d;
+        g.st = st;
+        g.timeout_cycles = tmo;
+        g.grid = grid1;
+        g.queue = queue1 ? 1 : 0;
+        g.counter = Lo.counter;
+        KC_CUDA(launch_gon(g, c.s), "mrg round 1 launch");
+    }
+    {
+        TraceStep t("mrg_union", c.s);
+        KC_CUDA(launch_mrg_union(Lo.c1, Lo.k1, m, k, Lo.U, Lo.nU, c.s), "union launch");
+        KC_CUDA(launch_gather_pack(Lo.pk, c.o.dtype, d, Lo.U, Lo.nU, ucap, Lo.pkU, c.s), "gather launch");
+        KC_CUDA(launch_mrg_round2_prep(Lo.inst2, proto, Lo.nU, k, c.s), "round 2 prep");
+    }
+    {
+        TraceStep t("mrg_round2", c.s);
+        GonArgs g{};
+        g.insts = Lo.inst2;
+        g.ninst = 1;
+        g.dtype = c.o.dtype;
+        g.dc = d;
+        g.dmax = d;
+        g.st = st;
+        g.timeout_cycles = tmo;
+        g.grid = G2;
+        KC_CUDA(launch_gon(g, c.s), "mrg round 2 launch");
+    }
+    {
+        TraceStep t("radius", c.s);
+        RadiusArgs ra{};
+        ra.pk = Lo.pk;
+        ra.dtype = c.o.dtype;
+        ra.n = n;
+        ra.d = d;
+        ra.centers = Lo.cen_dev;
+        ra.kc_dev = Lo.kout_dev;
+        ra.kc_max = k;
+        ra.cen = Lo.cen;
+        ra.mind = Lo.mind;
+        ra.key32 = Lo.key32;
+        ra.max64 = Lo.max64;
+        ra.arg64 = Lo.arg64;
+        ra.m64 = Lo.m64;
+        ra.radius_out = Lo.rad_dev;
+        ra.argmax_out = nullptr;
+        ra.st = st;
+        ra.have_mind = false;
+        KC_CUDA(launch_radius(ra, c.s), "radius launch");
+    }
+    if (!dev_cen)
+        KC_CUDA(cudaMemcpyAsync(centers, Lo.cen_dev, (size_t)k * sizeof(int64_t), cudaMemcpyDeviceToHost, c.s),
+                "copy centers out");
+    if (!dev_kout)
+        KC_CUDA(cudaMemcpyAsync(k_out, Lo.kout_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s), "copy k_out");
+    if (!dev_rad)
+        KC_CUDA(cudaMemcpyAsync(radius, Lo.rad_dev, sizeof(double), cudaMemcpyDeviceToHost, c.s), "copy radius");
+    if (c.async) return KC_OK;
+    return finish(c.arena, c.s);
+}
+
+kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d,
+                            const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
+                            const kc_opts *opts) {
+    g_err.clear();
+    if (count < 1) return fail(KC_ERR_ARG, "count=%d must be >= 1", count);
+    if (!pts || !n || !d || !k || !centers || !k_out || !radii) return fail(KC_ERR_ARG, "null pointer argument");
+    for (int i = 0; i < count; ++i) {
+        if (!pts[i] || !centers[i]) return fail(KC_ERR_ARG, "instance %d: null pointer", i);
+        if (n[i] < 1 || n[i] > (int64_t)N_MAX) return fail(KC_ERR_ARG, "instance %d: n outside [1, 2^32-2]", i);
+        if (d[i] < 1) return fail(KC_ERR_ARG, "instance %d: d must be >= 1", i);
+        if (k[i] < 1) return fail(KC_ERR_ARG, "instance %d: k must be >= 1", i);
+    }
+    CallCtx c;
+    kc_status r = begin(opts, c);
+    if (r != KC_OK) return r;
+    const bool dev_kout = is_device_ptr(k_out, c.dev);
+    const bool dev_rad = is_device_ptr(radii, c.dev);
+    std::vector<char> dev_pts((size_t)count), dev_cen((size_t)count);
+    bool all_dev = dev_kout && dev_rad;
+    int dmax = 0, dcommon = d[0];
+    for (int i = 0; i < count; ++i) {
+        dev_pts[i] = is_device_ptr(pts[i], c.dev);
+        dev_cen[i] = is_device_ptr(centers[i], c.dev);
+        all_dev = all_dev && dev_pts[i] && dev_cen[i];
+        dmax = std::max(dmax, (int)d[i]);
+        if (d[i] != dcommon) dcommon = 0;
+    }
+    if (c.async && !all_dev) return fail(KC_ERR_ARG, "KC_ASYNC needs device pointers for all arguments");
+    const int dc = (dcommon == 3 || dcommon == 8 || dcommon == 32) && c.o.dtype == KC_F32 ? dcommon : 0;
+
+    // Longest processing time first: instances ordered by n * k * d.
+    std::vector<int> order((size_t)count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        const double wa = (double)n[a] * std::min<int64_t>(k[a], n[a]) * d[a];
+        const double wb = (double)n[b] * std::min<int64_t>(k[b], n[b]) * d[b];
+        return wa > wb;
+    });
+
+    const size_t esz = 4;
+    struct Per {
+        void *staging, *pk;
+        uint32_t *mind;
+        int64_t *cen;
+        int32_t *range2;
+    };
+    std::vector<Per> per((size_t)count);
+    int32_t *kout_dev = nullptr;
+    double *rad_dev = nullptr;
+    uint64_t *fkeys = nullptr;
+    int *counter = nullptr;
+    PackSeg *segs_dev = nullptr;
+    GonInst *insts_dev = nullptr;
+    size_t zero_bytes = 0;
+    auto layout = [&](Carve &cv) {
+        counter = cv.take<int>(1);
+        for (int i = 0; i < count; ++i) per[i].range2 = cv.take<int32_t>(2);
+        zero_bytes = cv.off;
+        kout_dev = dev_kout ? k_out : cv.take<int32_t>((size_t)count);
+        rad_dev = dev_rad ? radii : cv.take<double>((size_t)count);
+        fkeys = cv.take<uint64_t>((size_t)count);
+        segs_dev = cv.take<PackSeg>((size_t)count);
+        insts_dev = cv.take<GonInst>((size_t)count);
+        for (int i = 0; i < count; ++i) {
+            const int64_t nbi = nblocks(n[i]);
+            per[i].staging = dev_pts[i] ? nullptr : cv.take<char>((size_t)n[i] * d[i] * esz);
+            per[i].pk = cv.take<char>((size_t)nbi * BLK * d[i] * esz);
+            per[i].mind = cv.take<uint32_t>((size_t)nbi * BLK);
+            per[i].cen = dev_cen[i] ? centers[i] : cv.take<int64_t>((size_t)std::min<int64_t>(k[i], n[i]));
+        }
+    };
+    {
+        Carve sizing(nullptr);
+        layout(sizing);
+        r = arena_reserve(c.arena, sizing.off, c.s);
+        if (r != KC_OK) return r;
+    }
+    Carve cv(c.arena->dev);
+    layout(cv);
+    DevStatus *st = c.arena->status;
+
+    // Descriptors: PackSeg[count] then GonInst[count] (LPT order), one upload.
+    std::vector<char> host(sizeof(PackSeg) * count + sizeof(GonInst) * count + 256);
+    PackSeg *hs = reinterpret_cast<PackSeg *>(host.data());
+    const size_t gi_off = (char *)insts_dev - (char *)segs_dev;
+    GonInst *hg = reinterpret_cast<GonInst *>(host.data() + gi_off);
+    int64_t blk0 = 0;
+    for (int q = 0; q < count; ++q) {
+        const int i = order[q];
+        PackSeg &S = hs[q];
+        memset(&S, 0, sizeof S);
+        S.src = dev_pts[i] ? pts[i] : per[i].staging;
+        S.dst = per[i].pk;
+        S.range2 = per[i].range2;
+        S.n = n[i];
+        S.blk0 = blk0;
+        S.d = d[i];
+        blk0 += nblocks(n[i]);
+        GonInst &I = hg[q];
+        memset(&I, 0, sizeof I);
+        I.pk = per[i].pk;
+        I.mind = per[i].mind;
+        I.slots = nullptr;
+        I.centers = per[i].cen;
+        I.k_out = kout_dev + i;
+        I.final_key = fkeys + i;
+        I.map = nullptr;
+        I.range2 = per[i].range2;
+        I.radius_out = rad_dev + i;
+        I.lo = 0;
+        I.n = n[i];
+        I.base = 0;
+        I.first = 0;
+        I.d = d[i];
+        I.k = (int)std::min<int64_t>(k[i], n[i]);
+        I.cta0 = 0;
+        I.G = 1;
+    }
+    KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
+    for (int i = 0; i < count; ++i)
+        if (!dev_pts[i])
+            KC_CUDA(cudaMemcpyAsync(per[i].staging, pts[i], (size_t)n[i] * d[i] * esz, cudaMemcpyHostToDevice, c.s),
+                    "copy points to device");
+    r = upload(c.arena, c.s, host.data(), gi_off + sizeof(GonInst) * count, segs_dev);
+    if (r != KC_OK) return r;
+    {
+        TraceStep t("pack", c.s);
+        KC_CUDA(launch_pack_many(segs_dev, count, blk0, c.o.dtype, st, c.s), "pack launch");
+    }
+    {
+        TraceStep t("gonzalez_batch", c.s);
+        GonArgs g{};
+        g.insts = insts_dev;
+        g.ninst = count;
+        g.dtype = c.o.dtype;
+        g.dc = dc;
+        g.dmax = dmax;
+        g.st = st;
+        g.timeout_cycles = timeout_cycles(c.o);
+        g.grid = std::min(gon_queue_grid(c.o.dtype, dc), count);
+        g.queue = 1;
+        g.counter = counter;
+        KC_CUDA(launch_gon(g, c.s), "batch launch");
+    }
+    {
+        TraceStep t("radius_batch", c.s);
+        KC_CUDA(launch_batch_radius(insts_dev, count, c.o.dtype, st, c.s), "batch radius launch");
+    }
+    for (int i = 0; i < count; ++i)
+        if (!dev_cen[i])
+            KC_CUDA(cudaMemcpyAsync(centers[i], per[i].cen, (size_t)std::min<int64_t>(k[i], n[i]) * sizeof(int64_t),
+                                    cudaMemcpyDeviceToHost, c.s),
+                    "copy centers out");
+    if (!dev_kout)
+        KC_CUDA(cudaMemcpyAsync(k_out, kout_dev, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost, c.s),
+                "copy k_out");
+    if (!dev_rad)
+        KC_CUDA(cudaMemcpyAsync(radii, rad_dev, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, c.s),
+                "copy radii");
     if (c.async) return KC_OK;
     return finish(c.arena, c.s);
 }

@@ -1,22 +1,28 @@
-// kc_gon.cu -- persistent Gonzalez kernel: all k farthest-point steps of GON
-// (Section 3.1; O(k n) distance evaluations, Section 5.1) in one cooperative
-// launch, without relaunching between steps.
+// kc_gon.cu -- persistent Gonzalez kernels: all k farthest-point steps of GON
+// (Section 3.1; O(k n) distance evaluations, Section 5.1) in one launch.
 //
-// Each step, every CTA
-//   1. reads the newest center's d coordinates into shared memory,
-//   2. sweeps its points (a warp streams one 128-point block at a time, lane
-//      l owning 4 points with one 16-byte load per coordinate): squared
-//      distance to the center, running minimum update (the minimum is only
-//      written back where it fell), and the running (value, lowest index)
-//      maximum as a 64-bit key,
-//   3. reduces the key over the CTA (warp shuffles, then shared memory) and
-//      publishes it with a release store into its own slot for this step,
-//   4. polls all CTAs' slots of this step (acquire loads, bounded by a cycle
-//      budget) and reduces them to the same global key in every CTA.
-// The winner of step it is center it+1.  The slot exchange is the only grid
-// synchronisation: it carries the data, so no separate barrier or atomic is
-// needed.  Slots are per step and zeroed before the launch, so a non-zero
-// slot always belongs to the current step.
+// An instance is a contiguous index range [lo, lo + n) of a packed point
+// array, solved by a group of G CTAs (group mode, cooperative launch) or by
+// one CTA that takes instances from a queue (queue mode).  Single GON is one
+// instance over the whole array; MRG round 1 (Algorithm 1) is m instances,
+// one per part, run side by side with CTA groups sized to the parts; the
+// batched many-instance form uses the queue.
+//
+// Each step, every CTA of the group
+//   1. sweeps its blocks of the range (a warp streams one 128-point block:
+//      lane l owns points 4l..4l+3 with one 16-byte load per coordinate):
+//      squared distance to the newest center (staged in shared memory), the
+//      running minimum (written back only where it fell) and the running
+//      (value, lowest local index) maximum as a 64-bit key;
+//   2. reduces the key over the CTA (shuffles, shared memory, one barrier);
+//   3. warp 0 publishes the CTA's key in its slot for this step, polls the
+//      group's slots of this step (relaxed loads, all of a lane's slots in
+//      flight at once, bounded by a cycle budget), reduces them to the group
+//      key, and loads the winner's coordinates for the next step;
+//   4. one more barrier hands the key and the new center to the CTA.
+// Slots are per step and zeroed before the launch, so a non-zero slot always
+// belongs to the current step; the key itself is the payload, so relaxed
+// accesses suffice (no other data crosses CTAs).
 #include <type_traits>
 
 #include "kc_internal.cuh"
@@ -25,19 +31,28 @@ namespace kc {
 
 namespace {
 
-constexpr int GON_NT = 512;
-constexpr int GON_W = GON_NT / 32;
+constexpr int GROUP_NT = 1024;   // group mode: one CTA per SM
+constexpr int QUEUE_NT = 256;    // queue mode: several CTAs per SM
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> { using type = float4; };
 template <> struct Vec4<int32_t> { using type = int4; };
 
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 template <typename T, int DC>
 __device__ __forceinline__ void dist4(const T *__restrict__ blk, int d, const T *cs, int lane,
                                       typename AccOf<T>::type acc[4]) {
     using V4 = typename Vec4<T>::type;
-    const V4 *src = reinterpret_cast<const V4 *>(blk) + lane;
     using A = typename AccOf<T>::type;
+    const V4 *src = reinterpret_cast<const V4 *>(blk) + lane;
     A a0 = A(0), a1 = A(0), a2 = A(0), a3 = A(0);
     if constexpr (DC > 0) {
 #pragma unroll
@@ -66,170 +81,282 @@ __device__ __forceinline__ void dist4(const T *__restrict__ blk, int d, const T 
     acc[3] = a3;
 }
 
-template <typename T, int DC>
-__global__ void __launch_bounds__(GON_NT) gon_kernel(GonArgs a) {
-    using A = typename AccOf<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *cs = reinterpret_cast<T *>(smem_raw);
-    __shared__ uint64_t red[GON_W];
-    __shared__ uint64_t s_key;
-    __shared__ int s_abort;
-
-    const int G = gridDim.x, cta = blockIdx.x;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int d = DC > 0 ? DC : a.d;
-    const int64_t n = a.n;
-    const int64_t nb = nblocks(n);
-    const T *pk = (const T *)a.pk;
-
-    // Errors from the pack kernel (or an earlier call in async mode) stop
-    // every CTA before the first exchange; all CTAs read the same word.
-    if (ld_volatile_i32(&a.st->code) != 0) return;
-    if constexpr (std::is_same<T, int32_t>::value) {
-        if (!int_range_ok(a.range2, d)) {
-            if (cta == 0 && tid == 0) set_status(a.st, KC_ERR_RANGE, 2, 0);
-            return;
-        }
-    }
-    if (tid == 0) s_abort = 0;
-    int64_t c = a.first;
-    if (cta == 0 && tid == 0) a.centers[0] = c;
-
-    int it = 0;
-    uint64_t K = 0;
-    for (it = 0; it < a.k; ++it) {
-        for (int j = tid; j < d; j += GON_NT) cs[j] = pk[pk_index(c, j, d)];
-        __syncthreads();
-
-        uint64_t best = 0;
-        for (int64_t b = (int64_t)cta * GON_W + warp; b < nb; b += (int64_t)G * GON_W) {
-            A acc[4];
-            dist4<T, DC>(pk + b * d * BLK, d, cs, lane, acc);
-            uint4 *mp = reinterpret_cast<uint4 *>(a.mind + b * BLK) + lane;
-            uint4 m = make_uint4(acc_bits(acc[0]), acc_bits(acc[1]), acc_bits(acc[2]),
-                                 acc_bits(acc[3]));
-            if (it == 0) {
-                *mp = m;
+// One step's sweep of this CTA's share (rank r of G) of [lo, lo + n).
+template <typename T, int DC, int NT>
+__device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__restrict__ mind,
+                                          int64_t lo, int64_t n, int d, const T *cs, bool first_step,
+                                          int r, int G) {
+    constexpr int W = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t hi = lo + n;
+    const int64_t b1 = (hi - 1) / BLK;
+    uint64_t best = 0;
+    for (int64_t b = lo / BLK + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) {
+        const int64_t g0 = b * BLK + lane * 4;
+        const bool full = g0 >= lo && g0 + 3 < hi;
+        uint4 *mp = reinterpret_cast<uint4 *>(mind + b * BLK) + lane;
+        uint32_t o[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+        if (!first_step) {
+            if (full) {
+                const uint4 ov = *mp;
+                o[0] = ov.x;
+                o[1] = ov.y;
+                o[2] = ov.z;
+                o[3] = ov.w;
             } else {
-                const uint4 o = *mp;
-                const uint4 nm = make_uint4(min(o.x, m.x), min(o.y, m.y), min(o.z, m.z),
-                                            min(o.w, m.w));
-                if (nm.x != o.x || nm.y != o.y || nm.z != o.z || nm.w != o.w) *mp = nm;
-                m = nm;
-            }
-            const int64_t i0 = b * BLK + lane * 4;
-            if (i0 < n) best = umax64(best, make_key(m.x, (uint32_t)i0));
-            if (i0 + 1 < n) best = umax64(best, make_key(m.y, (uint32_t)(i0 + 1)));
-            if (i0 + 2 < n) best = umax64(best, make_key(m.z, (uint32_t)(i0 + 2)));
-            if (i0 + 3 < n) best = umax64(best, make_key(m.w, (uint32_t)(i0 + 3)));
-        }
-
-        // CTA reduction, then publish this CTA's key for step `it`.
-        best = warp_max_u64(best);
-        if (lane == 0) red[warp] = best;
-        __syncthreads();
-        if (warp == 0) {
-            uint64_t v = lane < GON_W ? red[lane] : 0;
-            v = warp_max_u64(v);
-            if (lane == 0) {
-                if (v == 0) v = 1;   // CTA without points: present, never wins
-                st_release_u64(&a.slots[(int64_t)it * G + cta], v);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (g0 + q >= lo && g0 + q < hi) o[q] = mind[g0 + q];
             }
         }
-
-        // Gather every CTA's key of this step.
-        uint64_t g = 0;
-        for (int s = tid; s < G; s += GON_NT) {
-            const uint64_t *p = &a.slots[(int64_t)it * G + s];
-            uint64_t v = ld_acquire_u64(p);
-            if (v == 0) {
-                const long long t0 = clock64();
-                while ((v = ld_acquire_u64(p)) == 0) {
-                    if (ld_volatile_i32(&a.st->code) != 0 || clock64() - t0 > a.timeout_cycles) {
-                        set_status(a.st, KC_ERR_TIMEOUT, 3, it);
-                        s_abort = 1;
-                        break;
-                    }
+        typename AccOf<T>::type acc[4];
+        dist4<T, DC>(pk + b * d * BLK, d, cs, lane, acc);
+        uint32_t m[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) m[q] = min(o[q], acc_bits(acc[q]));
+        if (full) {
+            if (first_step || m[0] != o[0] || m[1] != o[1] || m[2] != o[2] || m[3] != o[3])
+                *mp = make_uint4(m[0], m[1], m[2], m[3]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) best = umax64(best, make_key(m[q], (uint32_t)(g0 + q - lo)));
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t g = g0 + q;
+                if (g >= lo && g < hi) {
+                    if (first_step || m[q] != o[q]) mind[g] = m[q];
+                    best = umax64(best, make_key(m[q], (uint32_t)(g - lo)));
                 }
             }
-            g = umax64(g, v);
         }
-        g = warp_max_u64(g);
-        __syncthreads();   // warp 0 has finished reading red[]
-        if (lane == 0) red[warp] = g;
+    }
+    return best;
+}
+
+// Warp 0: wait for all G slots of this step and return their maximum.
+__device__ uint64_t poll_slots(const uint64_t *slots, int G, long long timeout, DevStatus *st,
+                               int step, bool *abort_out) {
+    const int lane = threadIdx.x & 31;
+    uint64_t g = 0;
+    bool ab = false;
+    for (int s0 = 0; s0 < G && !ab; s0 += 128) {
+        uint64_t v[4];
+        unsigned pend = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (s0 + q * 32 + lane < G) pend |= 1u << q;
+        const long long t0 = clock64();
+        while (pend) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (pend >> q & 1u) v[q] = ld_relaxed_u64(slots + s0 + q * 32 + lane);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((pend >> q & 1u) && v[q] != 0) {
+                    g = umax64(g, v[q]);
+                    pend &= ~(1u << q);
+                }
+            if (pend && (clock64() - t0 > timeout || ld_volatile_i32(&st->code) != 0)) {
+                set_status(st, KC_ERR_TIMEOUT, 3, step);
+                ab = true;
+                break;
+            }
+        }
+    }
+    *abort_out = __any_sync(0xFFFFFFFFu, ab);
+    return warp_max_u64(g);
+}
+
+__device__ __forceinline__ int64_t out_index(const GonInst &I, int64_t local) {
+    return I.map ? I.map[local] : I.base + local;
+}
+
+struct Shared {
+    uint64_t red[32];
+    uint64_t key;
+    int abort;
+};
+
+// All k steps of one instance by this CTA (rank r of a group of G).
+template <typename T, int DC, int NT>
+__device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, DevStatus *st,
+                          long long timeout) {
+    constexpr int W = NT / 32;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int d = DC > 0 ? DC : I.d;
+    const T *pk = (const T *)I.pk;
+    if (warp == 0) {
+        for (int j = lane; j < d; j += 32) cs[j] = pk[pk_index(I.lo + I.first, j, d)];
+        if (lane == 0) sh.abort = 0;
+    }
+    if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
+    __syncthreads();
+
+    int it;
+    uint64_t K = 0;
+    for (it = 0; it < I.k; ++it) {
+        uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G);
+        best = warp_max_u64(best);
+        if (lane == 0) sh.red[warp] = best;
         __syncthreads();
-        if (s_abort) return;
         if (warp == 0) {
-            uint64_t v = lane < GON_W ? red[lane] : 0;
+            uint64_t v = lane < W ? sh.red[lane] : 0;
             v = warp_max_u64(v);
-            if (lane == 0) s_key = v;
+            uint64_t g = v;
+            bool ab = false;
+            if (G > 1) {
+                if (lane == 0) st_relaxed_u64(&I.slots[(int64_t)it * G + r], v ? v : 1);
+                g = poll_slots(I.slots + (int64_t)it * G, G, timeout, st, it, &ab);
+            }
+            if (!ab && key_val(g) != 0 && it + 1 < I.k) {
+                const int64_t c = key_idx(g);
+                for (int j = lane; j < d; j += 32) cs[j] = pk[pk_index(I.lo + c, j, d)];
+                if (r == 0 && lane == 0) I.centers[it + 1] = out_index(I, c);
+            }
+            if (lane == 0) {
+                sh.key = g;
+                sh.abort = ab;
+            }
         }
         __syncthreads();
-        K = s_key;
-        if (key_val(K) == 0) {   // every point is a center already: stop early
+        if (sh.abort) return;
+        K = sh.key;
+        if (key_val(K) == 0) {   // every point is at distance 0: stop early
             ++it;
             break;
         }
-        if (it + 1 < a.k) {
-            c = key_idx(K);
-            if (cta == 0 && tid == 0) a.centers[it + 1] = c;
+    }
+    if (r == 0 && tid == 0) {
+        *I.k_out = it;
+        *I.final_key = K;
+    }
+}
+
+template <typename T>
+__device__ bool instance_ok(const GonInst &I, DevStatus *st) {
+    if constexpr (std::is_same<T, int32_t>::value) {
+        if (!int_range_ok(I.range2, I.d)) {
+            set_status(st, KC_ERR_RANGE, 2, 0);
+            return false;
         }
     }
-    if (cta == 0 && tid == 0) {
-        *a.k_out = it;
-        *a.final_key = K;
-    }
+    return true;
 }
 
 template <typename T, int DC>
-void *gon_fn() {
-    return (void *)gon_kernel<T, DC>;
-}
-
-void *pick_gon(int dtype, int d) {
-    if (dtype == KC_F32) {
-        switch (d) {
-            case 2: return gon_fn<float, 2>();
-            case 3: return gon_fn<float, 3>();
-            case 8: return gon_fn<float, 8>();
-            case 10: return gon_fn<float, 10>();
-            case 16: return gon_fn<float, 16>();
-            case 32: return gon_fn<float, 32>();
-            case 64: return gon_fn<float, 64>();
-            default: return gon_fn<float, 0>();
+__global__ void __launch_bounds__(GROUP_NT, 1) gon_group_kernel(GonArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *cs = reinterpret_cast<T *>(smem_raw);
+    __shared__ GonInst I;
+    __shared__ Shared sh;
+    if (threadIdx.x == 0) {
+        if (a.insts) {
+            int lo = 0, hi = a.ninst - 1;   // last instance with cta0 <= blockIdx.x
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (a.insts[mid].cta0 <= (int)blockIdx.x) lo = mid;
+                else hi = mid - 1;
+            }
+            I = a.insts[lo];
+        } else {
+            I = a.single;
         }
     }
-    switch (d) {
-        case 2: return gon_fn<int32_t, 2>();
-        case 10: return gon_fn<int32_t, 10>();
-        default: return gon_fn<int32_t, 0>();
+    __syncthreads();
+    const int r = (int)blockIdx.x - I.cta0;
+    if (r < 0 || r >= I.G) return;
+    if (ld_volatile_i32(&a.st->code) != 0) return;
+    if (!instance_ok<T>(I, a.st)) return;
+    gon_solve<T, DC, GROUP_NT>(I, r, I.G, cs, sh, a.st, a.timeout_cycles);
+}
+
+template <typename T, int DC>
+__global__ void __launch_bounds__(QUEUE_NT) gon_queue_kernel(GonArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *cs = reinterpret_cast<T *>(smem_raw);
+    __shared__ GonInst I;
+    __shared__ Shared sh;
+    __shared__ int s_i;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_i = atomicAdd(a.counter, 1);
+            if (s_i < a.ninst) I = a.insts[s_i];
+        }
+        __syncthreads();
+        if (s_i >= a.ninst) return;
+        if (ld_volatile_i32(&a.st->code) != 0) return;
+        if (instance_ok<T>(I, a.st)) gon_solve<T, DC, QUEUE_NT>(I, 0, 1, cs, sh, a.st, a.timeout_cycles);
+        __syncthreads();
     }
+}
+
+template <typename T, int DC> void *group_fn() { return (void *)gon_group_kernel<T, DC>; }
+template <typename T, int DC> void *queue_fn() { return (void *)gon_queue_kernel<T, DC>; }
+
+void *pick_group(int dtype, int dc) {
+    if (dtype == KC_F32) {
+        switch (dc) {
+            case 2: return group_fn<float, 2>();
+            case 3: return group_fn<float, 3>();
+            case 8: return group_fn<float, 8>();
+            case 10: return group_fn<float, 10>();
+            case 16: return group_fn<float, 16>();
+            case 32: return group_fn<float, 32>();
+            case 64: return group_fn<float, 64>();
+            default: return group_fn<float, 0>();
+        }
+    }
+    switch (dc) {
+        case 2: return group_fn<int32_t, 2>();
+        case 10: return group_fn<int32_t, 10>();
+        default: return group_fn<int32_t, 0>();
+    }
+}
+
+void *pick_queue(int dtype, int dc) {
+    if (dtype == KC_F32) {
+        switch (dc) {
+            case 3: return queue_fn<float, 3>();
+            case 8: return queue_fn<float, 8>();
+            case 32: return queue_fn<float, 32>();
+            default: return queue_fn<float, 0>();
+        }
+    }
+    return queue_fn<int32_t, 0>();
 }
 
 }  // namespace
+
+int gon_threads() { return GROUP_NT; }
+int gon_warps_per_cta() { return GROUP_NT / 32; }
 
 int gon_max_grid(int dtype, int d) {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_gon(dtype, d), GON_NT,
-                                                  (size_t)d * 4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_group(dtype, d), GROUP_NT, (size_t)d * 4);
     return occ * sms;
 }
 
-int gon_warps_per_cta() { return GON_W; }
+int gon_queue_grid(int dtype, int d) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_queue(dtype, d), QUEUE_NT, (size_t)d * 4);
+    return occ * sms;
+}
 
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s) {
-    void *fn = pick_gon(a.dtype, a.d);
-    const size_t smem = (size_t)a.d * 4;
+    const size_t smem = (size_t)(a.dmax > 0 ? a.dmax : 1) * 4;
+    void *fn = a.queue ? pick_queue(a.dtype, a.dc) : pick_group(a.dtype, a.dc);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     void *args[] = {&a};
     note_launches(1);
-    return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(GON_NT), args, smem, s);
+    if (a.queue) return cudaLaunchKernel(fn, dim3(a.grid), dim3(QUEUE_NT), args, smem, s);
+    return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(GROUP_NT), args, smem, s);
 }
 
 }  // namespace kc

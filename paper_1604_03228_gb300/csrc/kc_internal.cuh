@@ -127,25 +127,103 @@ cudaError_t launch_pack(const void *src, int dtype, int64_t n, int d, void *dst,
 // int32 only: record KC_ERR_RANGE unless squared distances fit 32 bits.
 cudaError_t launch_range_check(const int32_t *range2, int d, DevStatus *st, cudaStream_t s);
 
-struct GonArgs {
-    const void *pk;          // packed points
-    int dtype;
-    int64_t n;
-    int d;
-    int k;
-    int64_t first;
-    uint32_t *mind;          // [nblocks*BLK] running minimum (value bits)
-    uint64_t *slots;         // [k * grid] per-iteration, per-CTA argmax keys
-    int64_t *centers;        // [k] out (device)
-    int32_t *k_out;          // out (device)
+// One Gonzalez instance solved by a group of CTAs [cta0, cta0 + G) of a
+// persistent launch.  Indices inside an instance are local (0..n-1); the
+// centers written out are base + local index (or map[local] when map is set).
+struct GonInst {
+    const void *pk;          // packed points of this instance (block aligned)
+    uint32_t *mind;          // [nblocks(n) * BLK] running minimum (value bits)
+    uint64_t *slots;         // [k * G] per-step, per-CTA argmax keys (zeroed)
+    int64_t *centers;        // [k] out
+    int32_t *k_out;          // out
     uint64_t *final_key;     // out: key of the largest final minimum
-    const int32_t *range2;   // int32 only: [min, max] of all coordinates
+    const int64_t *map;      // optional local -> global index map (nullptr: base + local)
+    const int32_t *range2;   // int32 only: [min, max] coordinate maxima of the pack
+    double *radius_out;      // batched form: this instance's covering radius
+    int64_t lo;              // first point of the range in the packed array
+    int64_t n;
+    int64_t base;
+    int64_t first;           // local index of the first center
+    int32_t d;
+    int32_t k;
+    int32_t cta0;
+    int32_t G;
+};
+
+struct GonArgs {
+    GonInst single;          // used when insts == nullptr
+    const GonInst *insts;    // device array [ninst], sorted by cta0 (group mode)
+    int ninst;
+    int dtype;
+    int dc;                  // common d for the compile-time specialisation (0 = mixed)
+    int dmax;                // largest d of any instance (shared-memory size)
     DevStatus *st;
     long long timeout_cycles;
-    int grid;                // CTAs (set by the launcher)
+    int grid;                // CTAs
+    int queue;               // 1: one CTA per instance, instances taken from *counter
+    int *counter;            // queue mode: next instance (zeroed)
 };
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s);
 int gon_max_grid(int dtype, int d);
+int gon_queue_grid(int dtype, int d);
+int gon_threads();
+int gon_warps_per_cta();
+
+// Arguments for plain GON: one instance over the whole packed array, solved
+// by all `grid` CTAs.
+inline void gon_single(GonArgs &g, const void *pk, int dtype, int64_t n, int d, int k, int64_t first,
+                       uint32_t *mind, uint64_t *slots, int64_t *centers, int32_t *k_out,
+                       uint64_t *final_key, const int32_t *range2, int grid) {
+    GonInst &I = g.single;
+    I.pk = pk;
+    I.mind = mind;
+    I.slots = slots;
+    I.centers = centers;
+    I.k_out = k_out;
+    I.final_key = final_key;
+    I.map = nullptr;
+    I.range2 = range2;
+    I.radius_out = nullptr;
+    I.lo = 0;
+    I.n = n;
+    I.base = 0;
+    I.first = first;
+    I.d = d;
+    I.k = k;
+    I.cta0 = 0;
+    I.G = grid;
+    g.insts = nullptr;
+    g.ninst = 1;
+    g.dtype = dtype;
+    g.dc = d;
+    g.dmax = d;
+    g.grid = grid;
+    g.queue = 0;
+    g.counter = nullptr;
+}
+
+// ------------------------------------------------ MRG and batched helpers
+// One row-major array to pack; its blocks are [blk0, blk0 + nblocks(n)) of
+// the launch.
+struct PackSeg {
+    const void *src;
+    void *dst;
+    int32_t *range2;         // int32: this array's coordinate range (zeroed)
+    int64_t n;
+    int64_t blk0;
+    int32_t d;
+    int32_t pad;
+};
+cudaError_t launch_pack_many(const PackSeg *segs, int nseg, int64_t total_blocks, int dtype, DevStatus *st,
+                             cudaStream_t s);
+cudaError_t launch_mrg_union(const int64_t *c1, const int32_t *k1, int m, int k, int64_t *U, int64_t *nU,
+                             cudaStream_t s);
+cudaError_t launch_gather_pack(const void *pk, int dtype, int d, const int64_t *U, const int64_t *nU,
+                               int64_t cap, void *out, cudaStream_t s);
+cudaError_t launch_mrg_round2_prep(GonInst *inst, const GonInst &proto, const int64_t *nU, int kmax,
+                                   cudaStream_t s);
+cudaError_t launch_batch_radius(const GonInst *insts, int ninst, int dtype, const DevStatus *st,
+                                cudaStream_t s);
 
 struct RadiusArgs {
     const void *pk;

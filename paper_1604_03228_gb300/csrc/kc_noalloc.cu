@@ -170,18 +170,8 @@ extern "C" kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, 
     DevStatus *st = (DevStatus *)(p + o_status);
 
     GonArgs g{};
-    g.pk = p + o_pk;
-    g.dtype = o.dtype;
-    g.n = n;
-    g.d = d;
-    g.k = keff;
-    g.first = first;
-    g.mind = (uint32_t *)(p + o_mind);
-    g.slots = (uint64_t *)(p + o_slots);
-    g.centers = centers;
-    g.k_out = k_out;
-    g.final_key = (uint64_t *)(p + o_key32);
-    g.range2 = (const int32_t *)(p + o_range);
+    gon_single(g, p + o_pk, o.dtype, n, d, keff, first, (uint32_t *)(p + o_mind), (uint64_t *)(p + o_slots),
+               centers, k_out, (uint64_t *)(p + o_key32), (const int32_t *)(p + o_range), grid);
     g.st = st;
     {
         int khz = 0;
@@ -189,10 +179,9 @@ extern "C" kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, 
         if (khz <= 0) khz = 2100000;
         g.timeout_cycles = (o.timeout_ms > 0 ? o.timeout_ms : 2000) * (long long)khz;
     }
-    g.grid = grid;
 
     RadiusArgs ra{};
-    ra.pk = g.pk;
+    ra.pk = g.single.pk;
     ra.dtype = o.dtype;
     ra.n = n;
     ra.d = d;
@@ -200,7 +189,7 @@ extern "C" kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, 
     ra.kc_dev = k_out;
     ra.kc_max = keff;
     ra.cen = p + o_cen;
-    ra.mind = g.mind;
+    ra.mind = g.single.mind;
     ra.key32 = (unsigned long long *)(p + o_key32);
     ra.max64 = (unsigned long long *)(p + o_max64);
     ra.arg64 = (unsigned long long *)(p + o_arg64);
@@ -211,7 +200,8 @@ extern "C" kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, 
     ra.have_mind = true;
 
     NA_CUDA(cudaMemsetAsync(p, 0, zero_bytes, s), "scratch clear");
-    NA_CUDA(launch_pack(pts, o.dtype, n, d, (void *)g.pk, (int32_t *)g.range2, st, s), "pack launch");
+    NA_CUDA(launch_pack(pts, o.dtype, n, d, (void *)g.single.pk, (int32_t *)g.single.range2, st, s),
+            "pack launch");
     NA_CUDA(launch_gon(g, s), "gonzalez launch");
     NA_CUDA(launch_radius(ra, s), "radius launch");
     DevStatus hs;

@@ -147,17 +147,25 @@ __device__ __forceinline__ double flag_threshold(const unsigned long long *key32
     return (double)M32 * (1.0 - 3.0 * f32_gamma(d));
 }
 
-__device__ double min64(const float *__restrict__ pk, int64_t x, int d, const float *__restrict__ cen,
-                        int kc) {
+// FP64 minimum over all centers of point x, computed by the whole warp: lane
+// l takes centers l, l+32, ... (each sum in coordinate order), then a warp
+// minimum.  FP64 is slow on this part, so the centers are spread over lanes
+// rather than chained in one thread.
+__device__ double min64_warp(const float *__restrict__ pk, int64_t x, int d,
+                             const float *__restrict__ cen, int kc, int lane) {
     double m = INFINITY;
-    for (int ci = 0; ci < kc; ++ci) {
+    for (int ci = lane; ci < kc; ci += 32) {
         double s = 0.0;
         for (int j = 0; j < d; ++j) s = sq_step64(s, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
         m = fmin(m, s);
     }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmin(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
     return m;
 }
 
+// Each warp scans 32 points at a time; the flagged ones (ballot) are
+// recomputed one after another by the whole warp.
 __global__ void recheck_max_kernel(const float *__restrict__ pk, int64_t n, int d,
                                    const float *__restrict__ cen, const int32_t *kc_dev, int kc_max,
                                    const uint32_t *__restrict__ mind, const unsigned long long *key32,
@@ -166,12 +174,22 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, int64_t n, int 
     if (key_val(*key32) == 0) return;   // every minimum is exactly 0
     const int kc = kc_dev ? *kc_dev : kc_max;
     const double thr = flag_threshold(key32, d);
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
-        if ((double)__uint_as_float(mind[x]) >= thr) {
-            const double v = min64(pk, x, d, cen, kc);
-            m64[x] = v;
-            atomicMax(max64, (unsigned long long)__double_as_longlong(v));
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+         base += warps * 32) {
+        const int64_t x = base + lane;
+        const bool flag = x < n && (double)__uint_as_float(mind[x]) >= thr;
+        unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t xs = base + src;
+            const double v = min64_warp(pk, xs, d, cen, kc, lane);
+            if (lane == src) {
+                m64[xs] = v;
+                atomicMax(max64, (unsigned long long)__double_as_longlong(v));
+            }
         }
     }
 }
