@@ -130,6 +130,32 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
                  int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts);
 
 /*
+ * kc_eim -- EIM: the sampling scheme of Ene, Im and Moseley as generalised in
+ * Section 4 (EIM-MapReduce-Sample, Algorithm 2, with Select, Algorithm 3, and
+ * the parameter phi), followed by GON on the returned sample (Section 4.2).
+ *   S = {}, R = all points; log is the natural logarithm, n fixed.
+ *   while |R| > (4/eps) k n^eps log n:
+ *     every x in R joins S with probability min(1, 9 k n^eps log n / |R|) and
+ *     H with probability min(1, 4 n^eps log n / |R|);
+ *     v = the point at position p = min(|H|, max(1, ceil(phi log n))) of H
+ *     sorted by distance to S (farthest first, lower index first on ties);
+ *     every x in R with d(x, S) <= d(v, S) leaves R (equality removes, so R
+ *     shrinks and sampled points always leave, Section 4.1); with H or S
+ *     empty, only the new S members leave.
+ *   C = S u R in ascending index order; GON(C, k) from C's lowest index.
+ * Randomness: U(seed, it, x, stream) = splitmix64 output number
+ * (it<<33 | x<<1 | stream) + 1 of the stream seeded opts->seed, top 53 bits
+ * over 2^53; x joins S when U(.., 0) < pS and H when U(.., 1) < pH.
+ * opts->phi (<= 0: 6, the paper's choice) and opts->seed are used.  Distances
+ * are compared exactly as in kc_gonzalez (canonical FP32 or exact int32).
+ * The call runs a host loop (one synchronisation per sampling round) and
+ * does not take KC_ASYNC.  Errors: KC_ERR_ARG for eps outside (0, 1); others
+ * as kc_gonzalez.
+ */
+kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, int64_t *centers, int32_t *k_out,
+                 double *radius, const kc_opts *opts);
+
+/*
  * kc_gonzalez_batch -- GON on `count` independent instances in one
  * persistent launch (the simulated parallel machines of Section 7.1, one
  * instance per machine).  Instance i has points pts[i] (row-major n[i] x d[i],

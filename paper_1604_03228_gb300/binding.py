@@ -57,6 +57,8 @@ def load(path: str | None = None):
     L.kc_gonzalez_noalloc.argtypes = [vp, i64, i32, i32, i64, vp, vp, vp, popts]
     L.kc_mrg.restype = ct.c_int
     L.kc_mrg.argtypes = [vp, i64, i32, i32, i32, vp, vp, vp, vp, popts]
+    L.kc_eim.restype = ct.c_int
+    L.kc_eim.argtypes = [vp, i64, i32, i32, dbl, vp, vp, vp, popts]
     L.kc_gonzalez_batch.restype = ct.c_int
     L.kc_gonzalez_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, popts]
     L.kc_sync.restype = ct.c_int
@@ -291,6 +293,21 @@ def kc_mrg(points, k: int, m: int, offsets=None, *, stream=None, flags: int = 0,
     _check(L, st)
     if flags & KC_ASYNC:
         return centers, k_out, radius
+    kk = int(_item(k_out))
+    return GonResult(centers[:kk], kk, float(_item(radius)))
+
+
+def kc_eim(points, k: int, eps: float = 0.1, phi: float = 6.0, seed: int = 0, *, stream=None,
+           timeout_ms: int = 0):
+    """EIM (Algorithms 2 and 3, then GON on the sample) through the C ABI."""
+    L = load()
+    p, n, d, code = _points(points)
+    centers = _empty_like_place(p, k, np.int64)
+    k_out = _empty_like_place(p, 1, np.int32)
+    radius = _empty_like_place(p, 1, np.float64)
+    o = _opts(code, p, stream, 0, timeout_ms, seed=seed, phi=phi)
+    st = L.kc_eim(_ptr(p), n, d, k, float(eps), _ptr(centers), _ptr(k_out), _ptr(radius), ct.byref(o))
+    _check(L, st)
     kk = int(_item(k_out))
     return GonResult(centers[:kk], kk, float(_item(radius)))
 

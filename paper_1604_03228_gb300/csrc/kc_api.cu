@@ -857,6 +857,218 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
     return finish(c.arena, c.s);
 }
 
+kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, int64_t *centers, int32_t *k_out,
+                 double *radius, const kc_opts *opts) {
+    g_err.clear();
+    if (!pts || !centers || !k_out || !radius) return fail(KC_ERR_ARG, "null pointer argument");
+    if (n < 1 || n > (int64_t)N_MAX) return fail(KC_ERR_ARG, "n=%lld outside [1, 2^32-2]", (long long)n);
+    if (d < 1) return fail(KC_ERR_ARG, "d=%d must be >= 1", d);
+    if (k < 1) return fail(KC_ERR_ARG, "k=%d must be >= 1", k);
+    if (!(eps > 0.0 && eps < 1.0)) return fail(KC_ERR_ARG, "eps=%g must be in (0, 1)", eps);
+    CallCtx c;
+    kc_status r = begin(opts, c);
+    if (r != KC_OK) return r;
+    if (c.async) return fail(KC_ERR_ARG, "kc_eim runs a host loop over sampling rounds and does not take KC_ASYNC");
+    const double phi = c.o.phi > 0 ? c.o.phi : 6.0;
+    const uint64_t seed = c.o.seed;
+    const bool dev_pts = is_device_ptr(pts, c.dev);
+    const bool dev_cen = is_device_ptr(centers, c.dev);
+    const bool dev_kout = is_device_ptr(k_out, c.dev);
+    const bool dev_rad = is_device_ptr(radius, c.dev);
+
+    // Loop constants of Algorithm 2 (natural logarithm, n fixed).
+    const double ne = pow((double)n, eps);
+    const double ln = log((double)n);
+    const double base = ne * ln;
+    const double limit = (4.0 / eps) * (double)k * base;
+    const int64_t pos = (int64_t)ceil(phi * ln);
+    const int64_t hcap = std::max<int64_t>(4096, (int64_t)ceil(64.0 * base) + 1024);
+    const int64_t nb = nblocks(n);
+    const int64_t nchunks = (n + 1023) / 1024;
+    const size_t esz = 4;
+    const int keff_max = (int)std::min<int64_t>(k, n);
+    const int grid = choose_gon_grid(c.o.dtype, d, n);
+
+    struct L {
+        unsigned long long *sn, *hn, *rnn;
+        int64_t *total;
+        int32_t *range2;
+        unsigned long long *key32, *max64, *arg64;
+        uint32_t *thr, *v;
+        uint64_t *fk, *slots;
+        uint8_t *mask;
+        void *staging, *pk, *Sc, *Hc, *pkC, *cen;
+        uint32_t *mind, *mindC, *R0, *R1, *S, *H, *dH;
+        int *counts;
+        int64_t *offs, *C;
+        double *m64;
+        int64_t *cen_dev;
+        int32_t *kout_dev;
+        double *rad_dev;
+        size_t zero_bytes;
+    } Lo{};
+    auto layout = [&](Carve &cv) {
+        Lo.sn = cv.take<unsigned long long>(1);
+        Lo.hn = cv.take<unsigned long long>(1);
+        Lo.rnn = cv.take<unsigned long long>(1);
+        Lo.total = cv.take<int64_t>(1);
+        Lo.range2 = cv.take<int32_t>(2);
+        Lo.key32 = cv.take<unsigned long long>(1);
+        Lo.max64 = cv.take<unsigned long long>(1);
+        Lo.arg64 = cv.take<unsigned long long>(1);
+        Lo.thr = cv.take<uint32_t>(1);
+        Lo.v = cv.take<uint32_t>(1);
+        Lo.fk = cv.take<uint64_t>(1);
+        Lo.slots = cv.take<uint64_t>((size_t)keff_max * grid);
+        Lo.mask = cv.take<uint8_t>((size_t)n);
+        Lo.zero_bytes = cv.off;
+        Lo.staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
+        Lo.pk = cv.take<char>((size_t)nb * BLK * d * esz);
+        Lo.mind = cv.take<uint32_t>((size_t)nb * BLK);
+        Lo.R0 = cv.take<uint32_t>((size_t)n);
+        Lo.R1 = cv.take<uint32_t>((size_t)n);
+        Lo.S = cv.take<uint32_t>((size_t)n);
+        Lo.Sc = cv.take<char>((size_t)n * d * esz);
+        Lo.H = cv.take<uint32_t>((size_t)hcap);
+        Lo.Hc = cv.take<char>((size_t)hcap * d * esz);
+        Lo.dH = cv.take<uint32_t>((size_t)hcap);
+        Lo.counts = cv.take<int>((size_t)nchunks);
+        Lo.offs = cv.take<int64_t>((size_t)nchunks);
+        Lo.C = cv.take<int64_t>((size_t)n);
+        Lo.pkC = cv.take<char>((size_t)nb * BLK * d * esz);
+        Lo.mindC = cv.take<uint32_t>((size_t)nb * BLK);
+        Lo.cen = cv.take<char>((size_t)keff_max * d * esz);
+        Lo.m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
+        Lo.cen_dev = dev_cen ? centers : cv.take<int64_t>((size_t)keff_max);
+        Lo.kout_dev = dev_kout ? k_out : cv.take<int32_t>(1);
+        Lo.rad_dev = dev_rad ? radius : cv.take<double>(1);
+    };
+    {
+        Carve sizing(nullptr);
+        layout(sizing);
+        r = arena_reserve(c.arena, sizing.off, c.s);
+        if (r != KC_OK) return r;
+    }
+    Carve cv(c.arena->dev);
+    layout(cv);
+    DevStatus *st = c.arena->status;
+    auto read_u64 = [&](const unsigned long long *p, unsigned long long *out) -> kc_status {
+        KC_CUDA(cudaMemcpyAsync(out, p, sizeof *out, cudaMemcpyDeviceToHost, c.s), "count read-back");
+        KC_CUDA(cudaStreamSynchronize(c.s), "cudaStreamSynchronize");
+        return KC_OK;
+    };
+    auto device_error = [&]() -> bool {
+        DevStatus h;
+        if (cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+        return h.code != 0;
+    };
+
+    KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, Lo.zero_bytes, c.s), "scratch clear");
+    const void *src;
+    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, Lo.staging, &src);
+    if (r != KC_OK) return r;
+    {
+        TraceStep t("pack", c.s);
+        KC_CUDA(launch_pack(src, c.o.dtype, n, d, Lo.pk, Lo.range2, st, c.s), "pack launch");
+        if (c.o.dtype == KC_I32) KC_CUDA(launch_range_check(Lo.range2, d, st, c.s), "range check");
+        KC_CUDA(launch_eim_iota(Lo.R0, n, c.s), "iota launch");
+    }
+    KC_CUDA(cudaStreamSynchronize(c.s), "cudaStreamSynchronize");
+    if (device_error()) return finish(c.arena, c.s);
+
+    int64_t rn = n, sn = 0;
+    uint32_t *Rc = Lo.R0, *Rx = Lo.R1;
+    int it = 0;
+    while ((double)rn > limit) {
+        const double pS = fmin(1.0, 9.0 * (double)k * base / (double)rn);
+        const double pH = fmin(1.0, 4.0 * base / (double)rn);
+        unsigned long long sn_new = 0, hn = 0, rnn = 0;
+        {
+            TraceStep t("eim_sample", c.s);
+            KC_CUDA(cudaMemsetAsync(Lo.hn, 0, sizeof(unsigned long long), c.s), "clear");
+            KC_CUDA(cudaMemsetAsync(Lo.rnn, 0, sizeof(unsigned long long), c.s), "clear");
+            KC_CUDA(launch_eim_sample(Rc, rn, seed, it, pS, pH, Lo.mask, Lo.S, Lo.sn, Lo.H, Lo.hn, hcap, st, c.s),
+                    "sample launch");
+        }
+        if ((r = read_u64(Lo.sn, &sn_new)) != KC_OK) return r;
+        if ((r = read_u64(Lo.hn, &hn)) != KC_OK) return r;
+        if ((int64_t)hn > hcap || device_error()) return finish(c.arena, c.s);
+        KC_CUDA(launch_eim_gather_rows(src, c.o.dtype, d, Lo.S, sn, (int64_t)sn_new, Lo.Sc, c.s), "gather S");
+        sn = (int64_t)sn_new;
+        if (hn > 0 && sn > 0) {
+            {
+                TraceStep t("eim_select", c.s);
+                KC_CUDA(launch_eim_gather_rows(src, c.o.dtype, d, Lo.H, 0, (int64_t)hn, Lo.Hc, c.s), "gather H");
+                KC_CUDA(launch_eim_dist_hs(c.o.dtype, Lo.Hc, (int64_t)hn, Lo.Sc, sn, d, Lo.dH, c.s), "d(H,S)");
+                const int64_t p = std::min<int64_t>((int64_t)hn, std::max<int64_t>(1, pos));
+                KC_CUDA(launch_eim_select(Lo.H, Lo.dH, (int64_t)hn, p, Lo.thr, Lo.v, c.s), "select");
+            }
+            TraceStep t("eim_prune", c.s);
+            KC_CUDA(launch_eim_prune(c.o.dtype, src, d, Rc, rn, Lo.mask, Lo.Sc, sn, Lo.thr, Rx, Lo.rnn, c.s),
+                    "prune");
+        } else {
+            KC_CUDA(launch_eim_drop_sampled(Rc, rn, Lo.mask, Rx, Lo.rnn, c.s), "drop sampled");
+        }
+        if ((r = read_u64(Lo.rnn, &rnn)) != KC_OK) return r;
+        rn = (int64_t)rnn;
+        std::swap(Rc, Rx);
+        ++it;
+    }
+
+    // C = S u R in ascending index order, then GON on C and the radius on V.
+    int64_t nC = 0;
+    {
+        TraceStep t("eim_compact", c.s);
+        KC_CUDA(launch_eim_mark(Rc, rn, Lo.mask, c.s), "mark");
+        KC_CUDA(launch_compact(Lo.mask, n, Lo.counts, Lo.offs, Lo.C, Lo.total, c.s), "compact");
+        KC_CUDA(cudaMemcpyAsync(&nC, Lo.total, sizeof nC, cudaMemcpyDeviceToHost, c.s), "count read-back");
+        KC_CUDA(cudaStreamSynchronize(c.s), "cudaStreamSynchronize");
+        KC_CUDA(launch_gather_pack(Lo.pk, c.o.dtype, d, Lo.C, Lo.total, nC, Lo.pkC, c.s), "gather C");
+    }
+    if (nC < 1) return fail(KC_ERR_CUDA, "EIM produced an empty sample");
+    const int kC = (int)std::min<int64_t>(k, nC);
+    {
+        TraceStep t("gonzalez", c.s);
+        GonArgs g{};
+        gon_single(g, Lo.pkC, c.o.dtype, nC, d, kC, 0, Lo.mindC, Lo.slots, Lo.cen_dev, Lo.kout_dev, Lo.fk,
+                   Lo.range2, std::min(grid, choose_gon_grid(c.o.dtype, d, nC)));
+        g.single.map = Lo.C;
+        g.st = st;
+        g.timeout_cycles = timeout_cycles(c.o);
+        KC_CUDA(launch_gon(g, c.s), "gonzalez launch");
+    }
+    {
+        TraceStep t("radius", c.s);
+        RadiusArgs ra{};
+        ra.pk = Lo.pk;
+        ra.dtype = c.o.dtype;
+        ra.n = n;
+        ra.d = d;
+        ra.centers = Lo.cen_dev;
+        ra.kc_dev = Lo.kout_dev;
+        ra.kc_max = kC;
+        ra.cen = Lo.cen;
+        ra.mind = Lo.mind;
+        ra.key32 = Lo.key32;
+        ra.max64 = Lo.max64;
+        ra.arg64 = Lo.arg64;
+        ra.m64 = Lo.m64;
+        ra.radius_out = Lo.rad_dev;
+        ra.argmax_out = nullptr;
+        ra.st = st;
+        ra.have_mind = false;
+        KC_CUDA(launch_radius(ra, c.s), "radius launch");
+    }
+    if (!dev_cen)
+        KC_CUDA(cudaMemcpyAsync(centers, Lo.cen_dev, (size_t)kC * sizeof(int64_t), cudaMemcpyDeviceToHost, c.s),
+                "copy centers out");
+    if (!dev_kout)
+        KC_CUDA(cudaMemcpyAsync(k_out, Lo.kout_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c.s), "copy k_out");
+    if (!dev_rad)
+        KC_CUDA(cudaMemcpyAsync(radius, Lo.rad_dev, sizeof(double), cudaMemcpyDeviceToHost, c.s), "copy radius");
+    return finish(c.arena, c.s);
+}
+
 kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d,
                             const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
                             const kc_opts *opts) {

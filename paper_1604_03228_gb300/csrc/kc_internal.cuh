@@ -225,6 +225,26 @@ cudaError_t launch_mrg_round2_prep(GonInst *inst, const GonInst &proto, const in
 cudaError_t launch_batch_radius(const GonInst *insts, int ninst, int dtype, const DevStatus *st,
                                 cudaStream_t s);
 
+// ------------------------------------------------------------------ EIM
+cudaError_t launch_eim_iota(uint32_t *R, int64_t n, cudaStream_t s);
+cudaError_t launch_eim_sample(const uint32_t *R, int64_t rn, uint64_t seed, int it, double pS, double pH,
+                              uint8_t *inS, uint32_t *S, unsigned long long *sn, uint32_t *H, unsigned long long *hn,
+                              int64_t hcap, DevStatus *st, cudaStream_t s);
+cudaError_t launch_eim_gather_rows(const void *src, int dtype, int d, const uint32_t *idx, int64_t from, int64_t to,
+                                   void *out, cudaStream_t s);
+cudaError_t launch_eim_dist_hs(int dtype, const void *Hc, int64_t hn, const void *Sc, int64_t sn, int d, uint32_t *dH,
+                               cudaStream_t s);
+cudaError_t launch_eim_select(const uint32_t *H, const uint32_t *dH, int64_t hn, int64_t p, uint32_t *thr, uint32_t *v,
+                              cudaStream_t s);
+cudaError_t launch_eim_prune(int dtype, const void *src, int d, const uint32_t *R, int64_t rn, const uint8_t *inS,
+                             const void *Sc, int64_t sn, const uint32_t *thr, uint32_t *Rn, unsigned long long *rnn,
+                             cudaStream_t s);
+cudaError_t launch_eim_drop_sampled(const uint32_t *R, int64_t rn, const uint8_t *inS, uint32_t *Rn,
+                                    unsigned long long *rnn, cudaStream_t s);
+cudaError_t launch_eim_mark(const uint32_t *R, int64_t rn, uint8_t *mask, cudaStream_t s);
+cudaError_t launch_compact(const uint8_t *mask, int64_t n, int *counts, int64_t *offs, int64_t *out, int64_t *total,
+                           cudaStream_t s);
+
 struct RadiusArgs {
     const void *pk;
     int dtype;
