@@ -66,12 +66,25 @@ typedef enum {
 
 typedef enum { KC_F32 = 0, KC_I32 = 1 } kc_dtype;
 
+/*
+ * Storage precision of the Gonzalez sweep for float points (kc_opts.sweep).
+ * KC_SWEEP_BF16 / KC_SWEEP_FP8 stream a bf16 (or fp8 e4m3 with a per-column
+ * scale max|x_j| / 448) copy of the points and keep, per point, an error bound
+ * e_x >= ||decoded(x) - x||_2.  Every candidate whose low-precision distance
+ * could reach the step's maximum is recomputed in canonical FP32 from the
+ * FP32 points, so the selected centers, k_out and radius are identical to
+ * KC_SWEEP_F32.  Ignored for int32 points.
+ */
+typedef enum { KC_SWEEP_F32 = 0, KC_SWEEP_BF16 = 1, KC_SWEEP_FP8 = 2 } kc_sweep;
+
 /* Flags for kc_opts.flags. */
 #define KC_ASYNC 1u        /* enqueue only; see kc_sync() */
 
 typedef struct {
     int32_t dtype;          /* kc_dtype of the points */
     uint32_t flags;         /* KC_ASYNC or 0 */
+    int32_t sweep;          /* kc_sweep (float points only) */
+    int32_t reserved;       /* must be 0 */
     uint64_t seed;          /* EIM sampling seed */
     double phi;             /* EIM Select parameter (Section 4.2); <= 0 means 6 */
     void *stream;           /* cudaStream_t, NULL = legacy default stream */

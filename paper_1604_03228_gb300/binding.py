@@ -31,8 +31,13 @@ class KCError(RuntimeError):
 
 
 class kc_opts(ct.Structure):
-    _fields_ = [("dtype", ct.c_int32), ("flags", ct.c_uint32), ("seed", ct.c_uint64),
-                ("phi", ct.c_double), ("stream", ct.c_void_p), ("timeout_ms", ct.c_int64)]
+    _fields_ = [("dtype", ct.c_int32), ("flags", ct.c_uint32), ("sweep", ct.c_int32),
+                ("reserved", ct.c_int32), ("seed", ct.c_uint64), ("phi", ct.c_double),
+                ("stream", ct.c_void_p), ("timeout_ms", ct.c_int64)]
+
+
+KC_SWEEP_F32, KC_SWEEP_BF16, KC_SWEEP_FP8 = 0, 1, 2
+_SWEEPS = {"f32": 0, "bf16": 1, "fp8": 2, None: 0, 0: 0, 1: 1, 2: 2}
 
 
 _LIB = None
@@ -164,10 +169,11 @@ def _stream_handle(ref, stream):
     return None
 
 
-def _opts(code, ref, stream, flags, timeout_ms, seed=0, phi=6.0):
+def _opts(code, ref, stream, flags, timeout_ms, seed=0, phi=6.0, sweep=None):
     o = kc_opts()
     o.dtype = code
     o.flags = flags
+    o.sweep = _SWEEPS[sweep]
     o.seed = seed
     o.phi = phi
     o.stream = _stream_handle(ref, stream)
@@ -202,7 +208,7 @@ class RadiusResult:
 # --------------------------------------------------------------- entry points
 
 def kc_gonzalez(points, k: int, first: int = 0, *, stream=None, flags: int = 0,
-                timeout_ms: int = 0, out=None):
+                timeout_ms: int = 0, out=None, sweep=None):
     """GON (Section 3.1) through the C ABI.  With flags=KC_ASYNC returns the
     raw device outputs (centers[k], k_out[1], radius[1]) without waiting."""
     L = load()
@@ -213,7 +219,7 @@ def kc_gonzalez(points, k: int, first: int = 0, *, stream=None, flags: int = 0,
         radius = _empty_like_place(p, 1, np.float64)
     else:
         centers, k_out, radius = out
-    o = _opts(code, p, stream, flags, timeout_ms)
+    o = _opts(code, p, stream, flags, timeout_ms, sweep=sweep)
     st = L.kc_gonzalez(_ptr(p), n, d, k, first, _ptr(centers), _ptr(k_out), _ptr(radius), ct.byref(o))
     _check(L, st)
     if flags & KC_ASYNC:
@@ -269,7 +275,7 @@ def kc_radius(points, centers, *, stream=None, flags: int = 0, timeout_ms: int =
 
 
 def kc_mrg(points, k: int, m: int, offsets=None, *, stream=None, flags: int = 0,
-           timeout_ms: int = 0, out=None):
+           timeout_ms: int = 0, out=None, sweep=None):
     """Two-round MRG (Algorithm 1) through the C ABI.  offsets: [m+1] part
     boundaries (array/tensor) or None for the balanced split."""
     L = load()
@@ -288,7 +294,7 @@ def kc_mrg(points, k: int, m: int, offsets=None, *, stream=None, flags: int = 0,
         radius = _empty_like_place(p, 1, np.float64)
     else:
         centers, k_out, radius = out
-    o = _opts(code, p, stream, flags, timeout_ms)
+    o = _opts(code, p, stream, flags, timeout_ms, sweep=sweep)
     st = L.kc_mrg(_ptr(p), n, d, k, m, _ptr(off), _ptr(centers), _ptr(k_out), _ptr(radius), ct.byref(o))
     _check(L, st)
     if flags & KC_ASYNC:
@@ -298,21 +304,22 @@ def kc_mrg(points, k: int, m: int, offsets=None, *, stream=None, flags: int = 0,
 
 
 def kc_eim(points, k: int, eps: float = 0.1, phi: float = 6.0, seed: int = 0, *, stream=None,
-           timeout_ms: int = 0):
+           timeout_ms: int = 0, sweep=None):
     """EIM (Algorithms 2 and 3, then GON on the sample) through the C ABI."""
     L = load()
     p, n, d, code = _points(points)
     centers = _empty_like_place(p, k, np.int64)
     k_out = _empty_like_place(p, 1, np.int32)
     radius = _empty_like_place(p, 1, np.float64)
-    o = _opts(code, p, stream, 0, timeout_ms, seed=seed, phi=phi)
+    o = _opts(code, p, stream, 0, timeout_ms, seed=seed, phi=phi, sweep=sweep)
     st = L.kc_eim(_ptr(p), n, d, k, float(eps), _ptr(centers), _ptr(k_out), _ptr(radius), ct.byref(o))
     _check(L, st)
     kk = int(_item(k_out))
     return GonResult(centers[:kk], kk, float(_item(radius)))
 
 
-def kc_gonzalez_batch(points_list, ks, *, stream=None, flags: int = 0, timeout_ms: int = 0):
+def kc_gonzalez_batch(points_list, ks, *, stream=None, flags: int = 0, timeout_ms: int = 0,
+                      sweep=None):
     """GON on many independent instances (one persistent launch) through the
     C ABI.  Returns [GonResult] in input order (centers local to each instance)."""
     L = load()
@@ -332,7 +339,7 @@ def kc_gonzalez_batch(points_list, ks, *, stream=None, flags: int = 0, timeout_m
     cptrs = (ct.c_void_p * count)(*[_ptr(c) for c in outs])
     k_out = _empty_like_place(ref, count, np.int32)
     radii = _empty_like_place(ref, count, np.float64)
-    o = _opts(codes.pop(), ref, stream, flags, timeout_ms)
+    o = _opts(codes.pop(), ref, stream, flags, timeout_ms, sweep=sweep)
     st = L.kc_gonzalez_batch(count, ptrs, ns.ctypes.data, ds.ctypes.data, kk.ctypes.data, cptrs,
                              _ptr(k_out), _ptr(radii), ct.byref(o))
     _check(L, st)

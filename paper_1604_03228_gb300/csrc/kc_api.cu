@@ -272,6 +272,7 @@ kc_status begin(const kc_opts *opts, CallCtx &c) {
     c.o = opts ? *opts : default_opts();
     if (c.o.dtype != KC_F32 && c.o.dtype != KC_I32) return fail(KC_ERR_ARG, "dtype must be KC_F32 or KC_I32");
     if (c.o.flags & ~KC_ASYNC) return fail(KC_ERR_ARG, "unknown flags 0x%x", c.o.flags);
+    if (c.o.sweep < KC_SWEEP_F32 || c.o.sweep > KC_SWEEP_FP8) return fail(KC_ERR_ARG, "unknown sweep %d", c.o.sweep);
     c.s = (cudaStream_t)c.o.stream;
     c.async = (c.o.flags & KC_ASYNC) != 0;
     KC_CUDA(cudaGetDevice(&c.dev), "cudaGetDevice");
@@ -290,11 +291,48 @@ kc_status stage_points(const CallCtx &c, const void *pts, size_t bytes, bool dev
     return KC_OK;
 }
 
-int choose_gon_grid(int dtype, int d, int64_t n) {
+// Low-precision sweep kind for a call: only float points use it.
+int lp_of(const kc_opts &o) { return o.dtype == KC_F32 ? o.sweep : 0; }
+
+// Scratch of the mixed-precision sweep over one packed array of n points.
+struct LPBufs {
+    uint32_t *lp = nullptr;
+    float *eblk = nullptr, *ept = nullptr, *scale = nullptr;
+    unsigned *colmax = nullptr;
+};
+
+void take_lp(Carve &cv, LPBufs &L, int lp, int64_t n, int d) {
+    if (!lp) {
+        L = LPBufs{};
+        return;
+    }
+    const int64_t nb = nblocks(n);
+    const int ng = lp_ngroups(lp, d);
+    L.lp = cv.take<uint32_t>((size_t)nb * ng * BLK);
+    L.eblk = cv.take<float>((size_t)nb);
+    L.ept = cv.take<float>((size_t)nb * BLK);
+    L.scale = cv.take<float>((size_t)ng * 4);
+    L.colmax = cv.take<unsigned>((size_t)d);
+}
+
+// Point an instance at the low-precision data (its own cenT [d][kcap] and
+// ecmax slot).
+void attach_lp(GonInst &I, const LPBufs &L, int lp, float *cenT, int kcap, float *ecmax) {
+    I.lp = L.lp;
+    I.eblk = L.eblk;
+    I.ept = L.ept;
+    I.scale = L.scale;
+    I.cenT = cenT;
+    I.kcap = kcap;
+    I.ecmax_out = ecmax;
+    I.lp_kind = lp;
+}
+
+int choose_gon_grid(int dtype, int d, int64_t n, int lp = 0) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int maxg = gon_max_grid(dtype, d);
+    const int maxg = gon_max_grid(dtype, d, lp);
     const int W = gon_warps_per_cta();
     const int64_t nb = nblocks(n);
     // Aim for about two 128-point blocks per warp; whole waves of SMs.
@@ -407,9 +445,12 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         return fail(KC_ERR_ARG, "KC_ASYNC needs device pointers for all arguments");
 
     const int keff = (int)(k < n ? k : n);
-    const int grid = choose_gon_grid(c.o.dtype, d, n);
+    const int lp = lp_of(c.o);
+    const int grid = choose_gon_grid(c.o.dtype, d, n, lp);
     const int64_t nb = nblocks(n);
     const size_t esz = 4;
+    LPBufs LB;
+    float *cenT = nullptr, *ecmax = nullptr;
 
     auto layout = [&](Carve &cv, GonArgs &g, RadiusArgs &ra, void **staging, int64_t **cen_dev,
                       int32_t **kout_dev, double **rad_dev, size_t *zero_bytes) {
@@ -428,8 +469,17 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         *cen_dev = dev_cen ? centers : cv.take<int64_t>(keff);
         *kout_dev = dev_kout ? k_out : cv.take<int32_t>(1);
         *rad_dev = dev_rad ? radius : cv.take<double>(1);
+        take_lp(cv, LB, lp, n, d);
+        cenT = lp ? cv.take<float>((size_t)keff * d) : nullptr;
+        ecmax = lp ? cv.take<float>(1) : nullptr;
         gon_single(g, pk, c.o.dtype, n, d, keff, first, mind, slots, *cen_dev, *kout_dev,
                    (uint64_t *)key32, range2, grid);
+        if (lp) {
+            attach_lp(g.single, LB, lp, cenT, keff, ecmax);
+            g.lp_kind = lp;
+            ra.eblk = LB.eblk;
+            ra.ecmax = ecmax;
+        }
         ra.pk = pk;
         ra.dtype = c.o.dtype;
         ra.n = n;
@@ -476,6 +526,10 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)g.single.pk, (int32_t *)g.single.range2,
                             c.arena->status, c.s),
                 "pack launch");
+        if (lp)
+            KC_CUDA(launch_lp_pack(lp, (const float *)g.single.pk, n, d, LB.colmax, LB.scale, LB.lp, LB.ept,
+                                   LB.eblk, c.s),
+                    "low-precision pack");
     }
     {
         TraceStep t("gonzalez", c.s);
@@ -628,7 +682,8 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
     // Round-1 CTA groups: proportional to each part's work n_i * k_i, at least
     // one CTA, at most one per 32 blocks (one block per warp), within the
     // co-resident grid.  More parts than CTAs: one CTA per part from a queue.
-    const int maxg = gon_max_grid(c.o.dtype, d);
+    const int lp = lp_of(c.o);
+    const int maxg = gon_max_grid(c.o.dtype, d, lp);
     const int W = gon_warps_per_cta();
     std::vector<int> G((size_t)m, 1), ki((size_t)m);
     std::vector<int64_t> slot_off((size_t)m + 1, 0);
@@ -676,7 +731,11 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
     }
     int grid1 = 0;
     for (int i = 0; i < m; ++i) grid1 += G[i];
-    if (queue1) grid1 = gon_queue_grid(c.o.dtype, d);
+    if (queue1) grid1 = gon_queue_grid(c.o.dtype, d, lp);
+    std::vector<int64_t> cen_off((size_t)m + 1, 0);
+    for (int i = 0; i < m; ++i) cen_off[i + 1] = cen_off[i] + ki[i];
+    LPBufs LB;
+    float *cenT1 = nullptr, *ecmax1 = nullptr;
     const int64_t ucap = (int64_t)m * k;
     const int G2 = (int)std::min<int64_t>(std::max<int64_t>(1, (nblocks(ucap) + W - 1) / W), std::min(maxg, 16));
     const int64_t nb = nblocks(n);
@@ -721,6 +780,9 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         Lo.pkU = cv.take<char>((size_t)nblocks(ucap) * BLK * d * esz);
         Lo.mindU = cv.take<uint32_t>((size_t)nblocks(ucap) * BLK);
         Lo.insts1 = cv.take<GonInst>((size_t)m);
+        take_lp(cv, LB, lp, n, d);
+        cenT1 = lp ? cv.take<float>((size_t)cen_off[m] * d) : nullptr;
+        ecmax1 = lp ? cv.take<float>((size_t)m) : nullptr;
         Lo.inst2 = cv.take<GonInst>(1);
         Lo.cen = cv.take<char>((size_t)k * d * esz);
         Lo.m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
@@ -762,6 +824,8 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
             I.k = ki[i];
             I.cta0 = queue1 ? 0 : cta;
             I.G = queue1 ? 1 : G[i];
+            I.kcap = ki[i];
+            if (lp) attach_lp(I, LB, lp, cenT1 + cen_off[i] * d, ki[i], ecmax1 + i);
             cta += I.G;
         }
     }
@@ -789,6 +853,9 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
     {
         TraceStep t("pack", c.s);
         KC_CUDA(launch_pack(src, c.o.dtype, n, d, Lo.pk, Lo.range2, st, c.s), "pack launch");
+        if (lp)
+            KC_CUDA(launch_lp_pack(lp, (const float *)Lo.pk, n, d, LB.colmax, LB.scale, LB.lp, LB.ept, LB.eblk, c.s),
+                    "low-precision pack");
     }
     {
         TraceStep t("mrg_round1", c.s);
@@ -803,6 +870,7 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         g.grid = grid1;
         g.queue = queue1 ? 1 : 0;
         g.counter = Lo.counter;
+        g.lp_kind = lp;
         KC_CUDA(launch_gon(g, c.s), "mrg round 1 launch");
     }
     {
@@ -887,7 +955,10 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
     const int64_t nchunks = (n + 1023) / 1024;
     const size_t esz = 4;
     const int keff_max = (int)std::min<int64_t>(k, n);
-    const int grid = choose_gon_grid(c.o.dtype, d, n);
+    const int lp = lp_of(c.o);
+    const int grid = choose_gon_grid(c.o.dtype, d, n, lp);
+    LPBufs LB;
+    float *cenT = nullptr, *ecmax = nullptr;
 
     struct L {
         unsigned long long *sn, *hn, *rnn;
@@ -942,6 +1013,9 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         Lo.cen_dev = dev_cen ? centers : cv.take<int64_t>((size_t)keff_max);
         Lo.kout_dev = dev_kout ? k_out : cv.take<int32_t>(1);
         Lo.rad_dev = dev_rad ? radius : cv.take<double>(1);
+        take_lp(cv, LB, lp, n, d);
+        cenT = lp ? cv.take<float>((size_t)keff_max * d) : nullptr;
+        ecmax = lp ? cv.take<float>(1) : nullptr;
     };
     {
         Carve sizing(nullptr);
@@ -1024,6 +1098,10 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         KC_CUDA(cudaMemcpyAsync(&nC, Lo.total, sizeof nC, cudaMemcpyDeviceToHost, c.s), "count read-back");
         KC_CUDA(cudaStreamSynchronize(c.s), "cudaStreamSynchronize");
         KC_CUDA(launch_gather_pack(Lo.pk, c.o.dtype, d, Lo.C, Lo.total, nC, Lo.pkC, c.s), "gather C");
+        if (lp && nC > 0)
+            KC_CUDA(launch_lp_pack(lp, (const float *)Lo.pkC, nC, d, LB.colmax, LB.scale, LB.lp, LB.ept, LB.eblk,
+                                   c.s),
+                    "low-precision pack");
     }
     if (nC < 1) return fail(KC_ERR_CUDA, "EIM produced an empty sample");
     const int kC = (int)std::min<int64_t>(k, nC);
@@ -1031,8 +1109,12 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         TraceStep t("gonzalez", c.s);
         GonArgs g{};
         gon_single(g, Lo.pkC, c.o.dtype, nC, d, kC, 0, Lo.mindC, Lo.slots, Lo.cen_dev, Lo.kout_dev, Lo.fk,
-                   Lo.range2, std::min(grid, choose_gon_grid(c.o.dtype, d, nC)));
+                   Lo.range2, std::min(grid, choose_gon_grid(c.o.dtype, d, nC, lp)));
         g.single.map = Lo.C;
+        if (lp) {
+            attach_lp(g.single, LB, lp, cenT, kC, ecmax);
+            g.lp_kind = lp;
+        }
         g.st = st;
         g.timeout_cycles = timeout_cycles(c.o);
         KC_CUDA(launch_gon(g, c.s), "gonzalez launch");
@@ -1098,6 +1180,9 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
     }
     if (c.async && !all_dev) return fail(KC_ERR_ARG, "KC_ASYNC needs device pointers for all arguments");
     const int dc = (dcommon == 3 || dcommon == 8 || dcommon == 32) && c.o.dtype == KC_F32 ? dcommon : 0;
+    const int lp = lp_of(c.o);
+    if (lp == KC_SWEEP_FP8)
+        return fail(KC_ERR_ARG, "the batched form takes KC_SWEEP_F32 or KC_SWEEP_BF16 (fp8 needs per-instance scales)");
 
     // Longest processing time first: instances ordered by n * k * d.
     std::vector<int> order((size_t)count);
@@ -1114,6 +1199,8 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
         uint32_t *mind;
         int64_t *cen;
         int32_t *range2;
+        uint32_t *lpw;
+        float *ept, *eblk, *cenT, *ecmax;
     };
     std::vector<Per> per((size_t)count);
     int32_t *kout_dev = nullptr;
@@ -1122,6 +1209,7 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
     int *counter = nullptr;
     PackSeg *segs_dev = nullptr;
     GonInst *insts_dev = nullptr;
+    LpSeg *lsegs_dev = nullptr;
     size_t zero_bytes = 0;
     auto layout = [&](Carve &cv) {
         counter = cv.take<int>(1);
@@ -1132,12 +1220,21 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
         fkeys = cv.take<uint64_t>((size_t)count);
         segs_dev = cv.take<PackSeg>((size_t)count);
         insts_dev = cv.take<GonInst>((size_t)count);
+        lsegs_dev = cv.take<LpSeg>(lp ? (size_t)count : 0);
         for (int i = 0; i < count; ++i) {
             const int64_t nbi = nblocks(n[i]);
+            const int ki = (int)std::min<int64_t>(k[i], n[i]);
             per[i].staging = dev_pts[i] ? nullptr : cv.take<char>((size_t)n[i] * d[i] * esz);
             per[i].pk = cv.take<char>((size_t)nbi * BLK * d[i] * esz);
             per[i].mind = cv.take<uint32_t>((size_t)nbi * BLK);
-            per[i].cen = dev_cen[i] ? centers[i] : cv.take<int64_t>((size_t)std::min<int64_t>(k[i], n[i]));
+            per[i].cen = dev_cen[i] ? centers[i] : cv.take<int64_t>((size_t)ki);
+            if (lp) {
+                per[i].lpw = cv.take<uint32_t>((size_t)nbi * lp_ngroups(lp, d[i]) * BLK);
+                per[i].ept = cv.take<float>((size_t)nbi * BLK);
+                per[i].eblk = cv.take<float>((size_t)nbi);
+                per[i].cenT = cv.take<float>((size_t)ki * d[i]);
+                per[i].ecmax = cv.take<float>(1);
+            }
         }
     };
     {
@@ -1150,11 +1247,15 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
     layout(cv);
     DevStatus *st = c.arena->status;
 
-    // Descriptors: PackSeg[count] then GonInst[count] (LPT order), one upload.
-    std::vector<char> host(sizeof(PackSeg) * count + sizeof(GonInst) * count + 256);
-    PackSeg *hs = reinterpret_cast<PackSeg *>(host.data());
+    // Descriptors: PackSeg[count], GonInst[count] and LpSeg[count] (LPT
+    // order), contiguous in the arena, one upload.
     const size_t gi_off = (char *)insts_dev - (char *)segs_dev;
+    const size_t ls_off = (char *)lsegs_dev - (char *)segs_dev;
+    const size_t up_bytes = lp ? ls_off + sizeof(LpSeg) * count : gi_off + sizeof(GonInst) * count;
+    std::vector<char> host(up_bytes + 256);
+    PackSeg *hs = reinterpret_cast<PackSeg *>(host.data());
     GonInst *hg = reinterpret_cast<GonInst *>(host.data() + gi_off);
+    LpSeg *hl = reinterpret_cast<LpSeg *>(host.data() + ls_off);
     int64_t blk0 = 0;
     for (int q = 0; q < count; ++q) {
         const int i = order[q];
@@ -1166,6 +1267,17 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
         S.n = n[i];
         S.blk0 = blk0;
         S.d = d[i];
+        if (lp) {
+            LpSeg &Ls = hl[q];
+            memset(&Ls, 0, sizeof Ls);
+            Ls.pk = (const float *)per[i].pk;
+            Ls.lp = per[i].lpw;
+            Ls.ept = per[i].ept;
+            Ls.eblk = per[i].eblk;
+            Ls.n = n[i];
+            Ls.blk0 = blk0;
+            Ls.d = d[i];
+        }
         blk0 += nblocks(n[i]);
         GonInst &I = hg[q];
         memset(&I, 0, sizeof I);
@@ -1186,17 +1298,28 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
         I.k = (int)std::min<int64_t>(k[i], n[i]);
         I.cta0 = 0;
         I.G = 1;
+        I.kcap = I.k;
+        if (lp) {
+            I.lp = per[i].lpw;
+            I.eblk = per[i].eblk;
+            I.ept = per[i].ept;
+            I.scale = nullptr;
+            I.cenT = per[i].cenT;
+            I.ecmax_out = per[i].ecmax;
+            I.lp_kind = lp;
+        }
     }
     KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
     for (int i = 0; i < count; ++i)
         if (!dev_pts[i])
             KC_CUDA(cudaMemcpyAsync(per[i].staging, pts[i], (size_t)n[i] * d[i] * esz, cudaMemcpyHostToDevice, c.s),
                     "copy points to device");
-    r = upload(c.arena, c.s, host.data(), gi_off + sizeof(GonInst) * count, segs_dev);
+    r = upload(c.arena, c.s, host.data(), up_bytes, segs_dev);
     if (r != KC_OK) return r;
     {
         TraceStep t("pack", c.s);
         KC_CUDA(launch_pack_many(segs_dev, count, blk0, c.o.dtype, st, c.s), "pack launch");
+        if (lp) KC_CUDA(launch_lp_pack_many(lsegs_dev, count, blk0, c.s), "low-precision pack");
     }
     {
         TraceStep t("gonzalez_batch", c.s);
@@ -1208,9 +1331,10 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
         g.dmax = dmax;
         g.st = st;
         g.timeout_cycles = timeout_cycles(c.o);
-        g.grid = std::min(gon_queue_grid(c.o.dtype, dc), count);
+        g.grid = std::min(gon_queue_grid(c.o.dtype, dc, lp), count);
         g.queue = 1;
         g.counter = counter;
+        g.lp_kind = lp;
         KC_CUDA(launch_gon(g, c.s), "batch launch");
     }
     {

@@ -161,10 +161,21 @@ __global__ void batch_radius_kernel(const GonInst *__restrict__ insts, int ninst
         const int kc = *I.k_out;
         const T *pk = (const T *)I.pk;
         const double thr = (double)__uint_as_float(key_val(K)) * (1.0 - 3.0 * f32_gamma(d));
+        const float opg = __fadd_ru(1.f, lp_slack(d));
+        const float ecmax = I.lp_kind ? *I.ecmax_out : 0.f;
         double best = -1.0;
         for (int64_t base = (int64_t)warp * 32; base < I.n; base += (int64_t)W * 32) {
             const int64_t x = base + lane;
-            const bool flag = x < I.n && (double)__uint_as_float(I.mind[I.lo + x]) >= thr;
+            bool flag = false;
+            if (x < I.n) {
+                const uint32_t mb = I.mind[I.lo + x];
+                if (I.lp_kind) {
+                    const float U = lp_upper(mb, __fadd_ru(I.eblk[(I.lo + x) / BLK], ecmax), opg);
+                    flag = (double)U * (double)U >= thr;
+                } else {
+                    flag = (double)__uint_as_float(mb) >= thr;
+                }
+            }
             unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);
             while (todo) {
                 const int src = __ffs(todo) - 1;

@@ -23,6 +23,9 @@
 // Slots are per step and zeroed before the launch, so a non-zero slot always
 // belongs to the current step; the key itself is the payload, so relaxed
 // accesses suffice (no other data crosses CTAs).
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
 #include <type_traits>
 
 #include "kc_internal.cuh"
@@ -232,6 +235,317 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
     }
 }
 
+// ------------------------------------------------- mixed-precision sweep
+//
+// The sweep streams the low-precision words instead of FP32 coordinates and
+// keeps m~(x), the running minimum of the FP32-evaluated squared distance
+// between decoded(x) and decoded(c).  With u = 2^-24, g = (d+2)u/(1-(d+2)u)
+// + 2^-20, e_x the point's bound (its block's maximum) and E the largest
+// bound of any center so far, the canonical FP32 minimum m32(x) satisfies
+//   L(x) = (1-g)(sqrt(m~)(1-g) - e_x - E) <= sqrt(m32(x)) <= U(x)
+//        = (1+g)(sqrt(m~)(1+g) + e_x + E)
+// (triangle inequality on ||.||_2, both FP32 evaluations within (1 +- g));
+// U and L are evaluated with directed rounding.  A CTA takes T = max L over
+// its points; a point with U(x) < T cannot be the CTA's exact argmax (nor tie
+// with it), so only points with U(x) >= T are recomputed exactly (canonical
+// FP32 against every center so far, from the FP32 points and the centers'
+// FP32 coordinates) and the CTA key is the exact maximum over them, equal to
+// the FP32 sweep's.  Candidates are collected during the sweep in a per-warp
+// buffer against the warp's running max L; if it overflows, the warp
+// rescans its running minima instead.
+template <int KIND> struct LPDec;
+template <> struct LPDec<KC_SWEEP_BF16> {
+    __device__ static __forceinline__ void dec(uint32_t w, const float *, float o[2]) {
+        o[0] = __uint_as_float(w << 16);
+        o[1] = __uint_as_float(w & 0xFFFF0000u);
+    }
+};
+template <> struct LPDec<KC_SWEEP_FP8> {
+    __device__ static __forceinline__ void dec(uint32_t w, const float *sc, float o[4]) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)((w >> (8 * t)) & 0xFFu), __NV_E4M3);
+            o[t] = __fmul_rn(__half2float(__half(h)), sc[t]);
+        }
+    }
+};
+
+struct Cand {
+    uint32_t idx;   // local index
+    float U;
+};
+constexpr int LP_CAP = 64;   // candidates per warp
+
+struct ShLP {
+    uint64_t red[32];
+    uint64_t key;
+    float Lw[32];
+    int ovf[32];
+    int cnt[32];
+    float ecmax;
+    int abort;
+};
+
+
+// Canonical FP32 minimum of point gx over the first ncen centers (cenT is
+// [d][kcap]); lane l takes centers l, l+32, ...; warp minimum.
+__device__ uint32_t exact_min_warp(const float *__restrict__ pk, int64_t gx, int d, const float *__restrict__ cenT,
+                                   int kcap, int ncen, int lane) {
+    uint32_t m = 0xFFFFFFFFu;
+    for (int i = lane; i < ncen; i += 32) {
+        float acc = 0.f;
+        for (int j = 0; j < d; ++j) acc = sq_step(acc, pk[pk_index(gx, j, d)], cenT[(int64_t)j * kcap + i]);
+        m = min(m, __float_as_uint(acc));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    return m;
+}
+
+// In-place removal of buffer entries with U < lim (warp-cooperative).
+__device__ __forceinline__ int lp_compact(Cand *buf, int cnt, float lim, int lane) {
+    int out = 0;
+    for (int e0 = 0; e0 < cnt; e0 += 32) {
+        const int e = e0 + lane;
+        Cand c = {0u, 0.f};
+        const bool keep = e < cnt && (c = buf[e]).U >= lim;
+        __syncwarp();
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, keep);
+        if (keep) buf[out + __popc(bal & ((1u << lane) - 1u))] = c;
+        out += __popc(bal);
+        __syncwarp();
+    }
+    return out;
+}
+
+// The decoded low-precision center, its bound, and its FP32 coordinates
+// appended to cenT (every CTA of the group writes the same values).
+template <int KIND>
+__device__ __forceinline__ void lp_load_center(const GonInst &I, int64_t c, int d, int ng, float *cl, const float *scs,
+                                               int slot, int lane, float *ec) {
+    constexpr int LG = lp_group(KIND);
+    const float *pk = (const float *)I.pk;
+    const int64_t g = I.lo + c;
+    for (int jg = lane; jg < ng; jg += 32) {
+        const uint32_t w = I.lp[((g / BLK) * ng + jg) * BLK + g % BLK];
+        float v[LG];
+        LPDec<KIND>::dec(w, scs + jg * LG, v);
+#pragma unroll
+        for (int t = 0; t < LG; ++t) cl[jg * LG + t] = v[t];
+    }
+    for (int j = lane; j < d; j += 32) I.cenT[(int64_t)j * I.kcap + slot] = pk[pk_index(g, j, d)];
+    *ec = I.ept[g];
+}
+
+template <int KIND, int DC, int NT>
+__device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &sh, DevStatus *st, long long timeout) {
+    constexpr int W = NT / 32;
+    constexpr int LG = lp_group(KIND);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int d = DC > 0 ? DC : I.d;
+    const int ng = (d + LG - 1) / LG;
+    const int dp = ng * LG;
+    float *cl = smem;                                  // [dp] decoded center
+    float *scs = smem + dp;                            // [dp] fp8 scales
+    Cand *buf = reinterpret_cast<Cand *>(smem + 2 * ((dp + 1) & ~1)) + warp * LP_CAP;
+    const float *pk = (const float *)I.pk;
+    const float g1 = lp_slack(d);
+    const float opg = __fadd_ru(1.f, g1), omg = __fsub_rd(1.f, g1);
+    const int64_t lo = I.lo, hi = I.lo + I.n, b1 = (hi - 1) / BLK;
+
+    for (int j = tid; j < dp; j += NT) scs[j] = (KIND == KC_SWEEP_FP8) ? I.scale[j] : 1.f;
+    __syncthreads();
+    if (warp == 0) {
+        float ec;
+        lp_load_center<KIND>(I, I.first, d, ng, cl, scs, 0, lane, &ec);
+        if (lane == 0) {
+            sh.ecmax = ec;
+            sh.abort = 0;
+        }
+    }
+    if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
+    __syncthreads();
+
+    int it;
+    uint64_t K = 0;
+    for (it = 0; it < I.k; ++it) {
+        const float ecmax = sh.ecmax;
+        float Lrun = -INFINITY;
+        int cnt = 0;
+        bool ovf = false;
+        for (int64_t b = lo / BLK + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) {
+            const int64_t g0 = b * BLK + lane * 4;
+            const uint4 *src = reinterpret_cast<const uint4 *>(I.lp + b * ng * BLK) + lane;
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            if constexpr (DC > 0) {
+#pragma unroll 4
+                for (int jg = 0; jg < (DC + LG - 1) / LG; ++jg) {
+                    const uint4 w = __ldg(src + jg * (BLK / 4));
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float v[LG];
+                        LPDec<KIND>::dec(ws[q], scs + jg * LG, v);
+#pragma unroll
+                        for (int t = 0; t < LG; ++t) {
+                            const float df = __fsub_rn(v[t], cl[jg * LG + t]);
+                            a[q] = __fmaf_rn(df, df, a[q]);
+                        }
+                    }
+                }
+            } else {
+                for (int jg = 0; jg < ng; ++jg) {
+                    const uint4 w = __ldg(src + jg * (BLK / 4));
+                    const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float v[LG];
+                        LPDec<KIND>::dec(ws[q], scs + jg * LG, v);
+#pragma unroll
+                        for (int t = 0; t < LG; ++t) {
+                            const float df = __fsub_rn(v[t], cl[jg * LG + t]);
+                            a[q] = __fmaf_rn(df, df, a[q]);
+                        }
+                    }
+                }
+            }
+            // running minimum of the approximate values
+            const bool full = g0 >= lo && g0 + 3 < hi;
+            uint32_t o[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+            uint4 *mp = reinterpret_cast<uint4 *>(I.mind + b * BLK) + lane;
+            if (it > 0) {
+                if (full) {
+                    const uint4 ov = *mp;
+                    o[0] = ov.x;
+                    o[1] = ov.y;
+                    o[2] = ov.z;
+                    o[3] = ov.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (g0 + q >= lo && g0 + q < hi) o[q] = I.mind[g0 + q];
+                }
+            }
+            uint32_t m[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) m[q] = min(o[q], __float_as_uint(a[q]));
+            if (full) {
+                if (it == 0 || m[0] != o[0] || m[1] != o[1] || m[2] != o[2] || m[3] != o[3])
+                    *mp = make_uint4(m[0], m[1], m[2], m[3]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (g0 + q >= lo && g0 + q < hi && (it == 0 || m[q] != o[q])) I.mind[g0 + q] = m[q];
+            }
+            // bounds, running max of L, candidate collection
+            const float delta = __fadd_ru(I.eblk[b], ecmax);
+            float U[4];
+            float bl = -INFINITY;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool v = g0 + q >= lo && g0 + q < hi;
+                U[q] = v ? lp_upper(m[q], delta, opg) : -INFINITY;
+                if (v) bl = fmaxf(bl, lp_lower(m[q], delta, omg));
+            }
+#pragma unroll
+            for (int o2 = 16; o2; o2 >>= 1) bl = fmaxf(bl, __shfl_xor_sync(0xFFFFFFFFu, bl, o2));
+            Lrun = fmaxf(Lrun, bl);
+            if (!ovf) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool pred = U[q] >= Lrun;
+                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
+                    const int nq = __popc(bal);
+                    if (nq == 0) continue;
+                    if (cnt + nq > LP_CAP) {
+                        cnt = lp_compact(buf, cnt, Lrun, lane);
+                        if (cnt + nq > LP_CAP) {
+                            ovf = true;
+                            break;
+                        }
+                    }
+                    if (pred) buf[cnt + __popc(bal & ((1u << lane) - 1u))] = Cand{(uint32_t)(g0 + q - lo), U[q]};
+                    cnt += nq;
+                }
+            }
+        }
+        if (lane == 0) {
+            sh.Lw[warp] = Lrun;
+            sh.ovf[warp] = ovf;
+            sh.cnt[warp] = cnt;
+        }
+        __syncthreads();
+        float T = -INFINITY;
+        for (int w = 0; w < W; ++w) T = fmaxf(T, sh.Lw[w]);
+        // exact recheck of this warp's candidates with U >= T
+        uint64_t best = 0;
+        const int ncen = it + 1;
+        if (!ovf) {
+            __syncwarp();
+            for (int e = 0; e < cnt; ++e) {
+                const Cand c = buf[e];
+                if (c.U >= T) {
+                    const uint32_t mm = exact_min_warp(pk, lo + c.idx, d, I.cenT, I.kcap, ncen, lane);
+                    best = umax64(best, make_key(mm, c.idx));
+                }
+            }
+        } else {
+            for (int64_t b = lo / BLK + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) {
+                const float delta = __fadd_ru(I.eblk[b], ecmax);
+#pragma unroll 1
+                for (int q = 0; q < 4; ++q) {
+                    const int64_t g = b * BLK + lane * 4 + q;
+                    const bool v = g >= lo && g < hi;
+                    const bool pred = v && lp_upper(I.mind[g], delta, opg) >= T;
+                    unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
+                    while (bal) {
+                        const int src_lane = __ffs(bal) - 1;
+                        bal &= bal - 1;
+                        const int64_t gs = b * BLK + src_lane * 4 + q;
+                        const uint32_t mm = exact_min_warp(pk, gs, d, I.cenT, I.kcap, ncen, lane);
+                        best = umax64(best, make_key(mm, (uint32_t)(gs - lo)));
+                    }
+                }
+            }
+        }
+        if (lane == 0) sh.red[warp] = best;
+        __syncthreads();
+        if (warp == 0) {
+            uint64_t v = lane < W ? sh.red[lane] : 0;
+            v = warp_max_u64(v);
+            uint64_t g = v;
+            bool ab = false;
+            if (G > 1) {
+                if (lane == 0) st_relaxed_u64(&I.slots[(int64_t)it * G + r], v ? v : 1);
+                g = poll_slots(I.slots + (int64_t)it * G, G, timeout, st, it, &ab);
+            }
+            if (!ab && key_val(g) != 0 && it + 1 < I.k) {
+                const int64_t c = key_idx(g);
+                float ec;
+                lp_load_center<KIND>(I, c, d, ng, cl, scs, it + 1, lane, &ec);
+                if (lane == 0) sh.ecmax = fmaxf(sh.ecmax, ec);
+                if (r == 0 && lane == 0) I.centers[it + 1] = out_index(I, c);
+            }
+            if (lane == 0) {
+                sh.key = g;
+                sh.abort = ab;
+            }
+        }
+        __syncthreads();
+        if (sh.abort) return;
+        K = sh.key;
+        if (key_val(K) == 0) {
+            ++it;
+            break;
+        }
+    }
+    if (r == 0 && tid == 0) {
+        *I.k_out = it;
+        *I.final_key = K;
+        if (I.ecmax_out) *I.ecmax_out = sh.ecmax;
+    }
+}
+
 template <typename T>
 __device__ bool instance_ok(const GonInst &I, DevStatus *st) {
     if constexpr (std::is_same<T, int32_t>::value) {
@@ -290,8 +604,85 @@ __global__ void __launch_bounds__(QUEUE_NT) gon_queue_kernel(GonArgs a) {
     }
 }
 
+__device__ __forceinline__ void find_instance(const GonArgs &a, GonInst &I) {
+    if (a.insts) {
+        int lo = 0, hi = a.ninst - 1;   // last instance with cta0 <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.insts[mid].cta0 <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        I = a.insts[lo];
+    } else {
+        I = a.single;
+    }
+}
+
+template <int KIND, int DC>
+__global__ void __launch_bounds__(GROUP_NT, 1) gon_group_lp_kernel(GonArgs a) {
+    extern __shared__ __align__(16) float smem_f[];
+    __shared__ GonInst I;
+    __shared__ ShLP sh;
+    if (threadIdx.x == 0) find_instance(a, I);
+    __syncthreads();
+    const int r = (int)blockIdx.x - I.cta0;
+    if (r < 0 || r >= I.G) return;
+    if (ld_volatile_i32(&a.st->code) != 0) return;
+    gon_solve_lp<KIND, DC, GROUP_NT>(I, r, I.G, smem_f, sh, a.st, a.timeout_cycles);
+}
+
+template <int KIND, int DC>
+__global__ void __launch_bounds__(QUEUE_NT) gon_queue_lp_kernel(GonArgs a) {
+    extern __shared__ __align__(16) float smem_f[];
+    __shared__ GonInst I;
+    __shared__ ShLP sh;
+    __shared__ int s_i;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_i = atomicAdd(a.counter, 1);
+            if (s_i < a.ninst) I = a.insts[s_i];
+        }
+        __syncthreads();
+        if (s_i >= a.ninst) return;
+        if (ld_volatile_i32(&a.st->code) != 0) return;
+        gon_solve_lp<KIND, DC, QUEUE_NT>(I, 0, 1, smem_f, sh, a.st, a.timeout_cycles);
+        __syncthreads();
+    }
+}
+
 template <typename T, int DC> void *group_fn() { return (void *)gon_group_kernel<T, DC>; }
 template <typename T, int DC> void *queue_fn() { return (void *)gon_queue_kernel<T, DC>; }
+template <int KIND, int DC> void *group_lp_fn() { return (void *)gon_group_lp_kernel<KIND, DC>; }
+template <int KIND, int DC> void *queue_lp_fn() { return (void *)gon_queue_lp_kernel<KIND, DC>; }
+
+void *pick_group_lp(int kind, int dc) {
+    if (kind == KC_SWEEP_FP8) {
+        switch (dc) {
+            case 16: return group_lp_fn<KC_SWEEP_FP8, 16>();
+            default: return group_lp_fn<KC_SWEEP_FP8, 0>();
+        }
+    }
+    switch (dc) {
+        case 10: return group_lp_fn<KC_SWEEP_BF16, 10>();
+        case 16: return group_lp_fn<KC_SWEEP_BF16, 16>();
+        default: return group_lp_fn<KC_SWEEP_BF16, 0>();
+    }
+}
+
+void *pick_queue_lp(int kind, int dc) {
+    if (kind == KC_SWEEP_FP8) return queue_lp_fn<KC_SWEEP_FP8, 0>();
+    switch (dc) {
+        case 3: return queue_lp_fn<KC_SWEEP_BF16, 3>();
+        case 8: return queue_lp_fn<KC_SWEEP_BF16, 8>();
+        case 32: return queue_lp_fn<KC_SWEEP_BF16, 32>();
+        default: return queue_lp_fn<KC_SWEEP_BF16, 0>();
+    }
+}
+
+size_t lp_smem_bytes(int kind, int dmax, int nt) {
+    const int dp = lp_ngroups(kind, dmax) * lp_group(kind);
+    return (size_t)2 * ((dp + 1) & ~1) * sizeof(float) + (size_t)(nt / 32) * LP_CAP * sizeof(Cand);
+}
 
 void *pick_group(int dtype, int dc) {
     if (dtype == KC_F32) {
@@ -330,25 +721,37 @@ void *pick_queue(int dtype, int dc) {
 int gon_threads() { return GROUP_NT; }
 int gon_warps_per_cta() { return GROUP_NT / 32; }
 
-int gon_max_grid(int dtype, int d) {
+static void *pick_fn(int dtype, int lp, int dc, bool queue) {
+    if (dtype == KC_F32 && lp) return queue ? pick_queue_lp(lp, dc) : pick_group_lp(lp, dc);
+    return queue ? pick_queue(dtype, dc) : pick_group(dtype, dc);
+}
+
+static size_t smem_for(int dtype, int lp, int dmax, bool queue) {
+    if (dtype == KC_F32 && lp) return lp_smem_bytes(lp, dmax, queue ? QUEUE_NT : GROUP_NT);
+    return (size_t)(dmax > 0 ? dmax : 1) * 4;
+}
+
+int gon_max_grid(int dtype, int d, int lp) {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_group(dtype, d), GROUP_NT, (size_t)d * 4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_fn(dtype, lp, d, false), GROUP_NT,
+                                                  smem_for(dtype, lp, d, false));
     return occ * sms;
 }
 
-int gon_queue_grid(int dtype, int d) {
+int gon_queue_grid(int dtype, int d, int lp) {
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_queue(dtype, d), QUEUE_NT, (size_t)d * 4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_fn(dtype, lp, d, true), QUEUE_NT,
+                                                  smem_for(dtype, lp, d, true));
     return occ * sms;
 }
 
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s) {
-    const size_t smem = (size_t)(a.dmax > 0 ? a.dmax : 1) * 4;
-    void *fn = a.queue ? pick_queue(a.dtype, a.dc) : pick_group(a.dtype, a.dc);
+    const size_t smem = smem_for(a.dtype, a.lp_kind, a.dmax, a.queue != 0);
+    void *fn = pick_fn(a.dtype, a.lp_kind, a.dc, a.queue != 0);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

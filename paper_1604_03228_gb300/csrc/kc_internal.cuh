@@ -140,6 +140,18 @@ struct GonInst {
     const int64_t *map;      // optional local -> global index map (nullptr: base + local)
     const int32_t *range2;   // int32 only: [min, max] coordinate maxima of the pack
     double *radius_out;      // batched form: this instance's covering radius
+    // mixed-precision sweep (lp_kind != 0): low-precision words of the same
+    // packed array, per-block error bounds (indexed like blocks of pk),
+    // per-point bounds, fp8 column scales, the selected centers' FP32
+    // coordinates transposed ([d][kcap]) and the largest center bound (out)
+    const uint32_t *lp;
+    const float *eblk;
+    const float *ept;
+    const float *scale;
+    float *cenT;
+    float *ecmax_out;
+    int32_t lp_kind;
+    int32_t kcap;
     int64_t lo;              // first point of the range in the packed array
     int64_t n;
     int64_t base;
@@ -162,10 +174,11 @@ struct GonArgs {
     int grid;                // CTAs
     int queue;               // 1: one CTA per instance, instances taken from *counter
     int *counter;            // queue mode: next instance (zeroed)
+    int lp_kind;             // 0: FP32 sweep; KC_SWEEP_BF16 / KC_SWEEP_FP8 (float points)
 };
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s);
-int gon_max_grid(int dtype, int d);
-int gon_queue_grid(int dtype, int d);
+int gon_max_grid(int dtype, int d, int lp = 0);
+int gon_queue_grid(int dtype, int d, int lp = 0);
 int gon_threads();
 int gon_warps_per_cta();
 
@@ -184,6 +197,14 @@ inline void gon_single(GonArgs &g, const void *pk, int dtype, int64_t n, int d, 
     I.map = nullptr;
     I.range2 = range2;
     I.radius_out = nullptr;
+    I.lp = nullptr;
+    I.eblk = nullptr;
+    I.ept = nullptr;
+    I.scale = nullptr;
+    I.cenT = nullptr;
+    I.ecmax_out = nullptr;
+    I.lp_kind = 0;
+    I.kcap = k;
     I.lo = 0;
     I.n = n;
     I.base = 0;
@@ -200,7 +221,44 @@ inline void gon_single(GonArgs &g, const void *pk, int dtype, int64_t n, int d, 
     g.grid = grid;
     g.queue = 0;
     g.counter = nullptr;
+    g.lp_kind = 0;
 }
+
+// Bounds on sqrt(m32) from the approximate minimum m~ (value bits), the
+// absolute slack delta = e_x + E and opg = 1 + g, omg = 1 - g (see the
+// mixed-precision sweep in kc_gon.cu); directed rounding keeps them sound.
+__device__ __forceinline__ float lp_upper(uint32_t mbits, float delta, float opg) {
+    const float r = __fsqrt_ru(__uint_as_float(mbits));
+    return __fmul_ru(opg, __fadd_ru(__fmul_ru(r, opg), delta));
+}
+__device__ __forceinline__ float lp_lower(uint32_t mbits, float delta, float omg) {
+    const float r = __fsqrt_rd(__uint_as_float(mbits));
+    return __fmul_rd(omg, __fsub_rd(__fmul_rd(r, omg), delta));
+}
+__host__ __device__ inline float lp_slack(int d) { return (float)(f32_gamma(d) + 0x1p-20); }
+
+// --------------------------------------------- low-precision sweep data
+// Coordinates per 32-bit word of the low-precision copy (bf16: 2, fp8: 4).
+__host__ __device__ constexpr int lp_group(int kind) { return kind == KC_SWEEP_FP8 ? 4 : 2; }
+__host__ __device__ inline int lp_ngroups(int kind, int d) { return (d + lp_group(kind) - 1) / lp_group(kind); }
+// Build the low-precision copy of a packed FP32 array: words `lp`
+// [nblocks*ng*BLK], per-point bounds `ept` [nblocks*BLK], per-block maxima
+// `eblk` [nblocks]; fp8 also fills `scale` [ng*4] from the column maxima
+// (`colmax` [d] scratch).
+cudaError_t launch_lp_pack(int kind, const float *pk, int64_t n, int d, unsigned *colmax, float *scale, uint32_t *lp,
+                           float *ept, float *eblk, cudaStream_t s);
+// bf16 copies of many packed arrays (batched form).
+struct LpSeg {
+    const float *pk;
+    uint32_t *lp;
+    float *ept;
+    float *eblk;
+    int64_t n;
+    int64_t blk0;
+    int32_t d;
+    int32_t pad;
+};
+cudaError_t launch_lp_pack_many(const LpSeg *segs, int nseg, int64_t total_blocks, cudaStream_t s);
 
 // ------------------------------------------------ MRG and batched helpers
 // One row-major array to pack; its blocks are [blk0, blk0 + nblocks(n)) of
@@ -263,6 +321,10 @@ struct RadiusArgs {
     int64_t *argmax_out;     // device out (may be null)
     DevStatus *st;
     bool have_mind;          // mind/key32 already hold the FP32 minima
+    // set when mind holds a mixed-precision sweep's approximate minima: the
+    // flag test then uses the upper bound U(x) (eblk per block, *ecmax)
+    const float *eblk;
+    const float *ecmax;
 };
 cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s);
 

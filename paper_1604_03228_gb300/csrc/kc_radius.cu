@@ -147,6 +147,17 @@ __device__ __forceinline__ double flag_threshold(const unsigned long long *key32
     return (double)M32 * (1.0 - 3.0 * f32_gamma(d));
 }
 
+// Can point x reach the FP64 maximum?  FP32 minima: m32(x) >= thr.  After a
+// mixed-precision sweep mind holds approximate minima m~; then U(x)^2 >= thr
+// with U(x) >= sqrt of the exact minimum (kc_gon.cu), which also bounds the
+// FP64 value within the same (1 - 3 gamma) margin.
+__device__ __forceinline__ bool can_reach(const uint32_t *mind, int64_t x, double thr, const float *eblk,
+                                          const float *ecmax, float opg) {
+    if (!eblk) return (double)__uint_as_float(mind[x]) >= thr;
+    const float U = lp_upper(mind[x], __fadd_ru(eblk[x / BLK], *ecmax), opg);
+    return (double)U * (double)U >= thr;
+}
+
 // FP64 minimum over all centers of point x, computed by the whole warp: lane
 // l takes centers l, l+32, ... (each sum in coordinate order), then a warp
 // minimum.  FP64 is slow on this part, so the centers are spread over lanes
@@ -169,17 +180,19 @@ __device__ double min64_warp(const float *__restrict__ pk, int64_t x, int d,
 __global__ void recheck_max_kernel(const float *__restrict__ pk, int64_t n, int d,
                                    const float *__restrict__ cen, const int32_t *kc_dev, int kc_max,
                                    const uint32_t *__restrict__ mind, const unsigned long long *key32,
-                                   unsigned long long *max64, double *m64, const DevStatus *st) {
+                                   unsigned long long *max64, double *m64, const DevStatus *st,
+                                   const float *eblk, const float *ecmax) {
     if (ld_volatile_i32(&st->code) != 0) return;
     if (key_val(*key32) == 0) return;   // every minimum is exactly 0
     const int kc = kc_dev ? *kc_dev : kc_max;
     const double thr = flag_threshold(key32, d);
+    const float opg = __fadd_ru(1.f, lp_slack(d));
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
          base += warps * 32) {
         const int64_t x = base + lane;
-        const bool flag = x < n && (double)__uint_as_float(mind[x]) >= thr;
+        const bool flag = x < n && can_reach(mind, x, thr, eblk, ecmax, opg);
         unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);
         while (todo) {
             const int src = __ffs(todo) - 1;
@@ -197,14 +210,15 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, int64_t n, int 
 __global__ void recheck_arg_kernel(int64_t n, int d, const uint32_t *__restrict__ mind,
                                    const unsigned long long *key32, const unsigned long long *max64,
                                    const double *__restrict__ m64, unsigned long long *arg64,
-                                   const DevStatus *st) {
+                                   const DevStatus *st, const float *eblk, const float *ecmax) {
     if (ld_volatile_i32(&st->code) != 0) return;
     if (key_val(*key32) == 0) return;
     const double thr = flag_threshold(key32, d);
+    const float opg = __fadd_ru(1.f, lp_slack(d));
     const double M = __longlong_as_double((long long)*max64);
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        if ((double)__uint_as_float(mind[x]) >= thr && m64[x] == M)
+        if (can_reach(mind, x, thr, eblk, ecmax, opg) && m64[x] == M)
             atomicMax(arg64, 0xFFFFFFFFFFFFFFFFull - (unsigned long long)x);
     }
 }
@@ -282,9 +296,9 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
         const int grid = (int)(g > sms * 8 ? sms * 8 : g);
         recheck_max_kernel<<<grid, 256, 0, s>>>((const float *)a.pk, a.n, a.d, (const float *)a.cen,
                                                 a.kc_dev, a.kc_max, a.mind, a.key32, a.max64, a.m64,
-                                                a.st);
+                                                a.st, a.eblk, a.ecmax);
         recheck_arg_kernel<<<grid, 256, 0, s>>>(a.n, a.d, a.mind, a.key32, a.max64, a.m64, a.arg64,
-                                                a.st);
+                                                a.st, a.eblk, a.ecmax);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     finalize_kernel<<<1, 1, 0, s>>>(a.dtype, a.key32, a.max64, a.arg64, a.radius_out, a.argmax_out,
