@@ -244,6 +244,15 @@ void kc_trace_enable(int32_t on);
 int32_t kc_trace_read(kc_trace_rec *out, int32_t cap);
 int64_t kc_launch_count(void);
 
+/*
+ * kc_counters -- diagnostics of the mixed-precision sweep on the current
+ * device since the last call (which it resets): out[0] = candidates
+ * recomputed exactly in FP32, out[1] = candidate-buffer overflows (a warp
+ * rescanned its running minima), out[2..3] reserved.  Synchronises the
+ * device.  Returns the number of values (4), or -1 on a CUDA error.
+ */
+int32_t kc_counters(int64_t *out, int32_t cap);
+
 #ifdef __cplusplus
 }
 #endif

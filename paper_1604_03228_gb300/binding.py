@@ -76,8 +76,18 @@ def load(path: str | None = None):
     L.kc_trace_read.restype = i32
     L.kc_trace_read.argtypes = [ct.POINTER(kc_trace_rec), i32]
     L.kc_launch_count.restype = i64
+    L.kc_counters.restype = i32
+    L.kc_counters.argtypes = [vp, i32]
     _LIB = L
     return L
+
+
+def kc_counters():
+    """Mixed-precision diagnostics since the last call: (exact rechecks, overflows)."""
+    out = np.zeros(4, dtype=np.int64)
+    if load().kc_counters(out.ctypes.data, 4) < 0:
+        raise KCError(KC_ERR_CUDA, "kc_counters failed")
+    return int(out[0]), int(out[1])
 
 
 class kc_trace_rec(ct.Structure):

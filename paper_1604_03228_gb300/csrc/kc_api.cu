@@ -368,6 +368,16 @@ const char *kc_version(void) { return "kcenter-gb300 0.1 (sm_103a)"; }
 
 void kc_trace_enable(int32_t on) { g_trace_on = on ? 1 : 0; }
 
+int32_t kc_counters(int64_t *out, int32_t cap) {
+    unsigned long long v[4] = {0, 0, 0, 0};
+    if (cudaDeviceSynchronize() != cudaSuccess || read_counters(v, true) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    for (int i = 0; i < cap && i < 4; ++i) out[i] = (int64_t)v[i];
+    return 4;
+}
+
 int64_t kc_launch_count(void) { return g_launches.load(); }
 
 int32_t kc_trace_read(kc_trace_rec *out, int32_t cap) {

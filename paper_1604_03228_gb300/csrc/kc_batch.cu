@@ -168,12 +168,12 @@ __global__ void batch_radius_kernel(const GonInst *__restrict__ insts, int ninst
             const int64_t x = base + lane;
             bool flag = false;
             if (x < I.n) {
-                const uint32_t mb = I.mind[I.lo + x];
                 if (I.lp_kind) {
-                    const float U = lp_upper(mb, __fadd_ru(I.eblk[(I.lo + x) / BLK], ecmax), opg);
+                    const uint32_t hi = ((uint32_t)reinterpret_cast<const uint16_t *>(I.mind)[I.lo + x] + 1u) << 16;
+                    const float U = lp_upper(hi, __fadd_ru(I.eblk[(I.lo + x) / BLK], ecmax), opg);
                     flag = (double)U * (double)U >= thr;
                 } else {
-                    flag = (double)__uint_as_float(mb) >= thr;
+                    flag = (double)__uint_as_float(I.mind[I.lo + x]) >= thr;
                 }
             }
             unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);

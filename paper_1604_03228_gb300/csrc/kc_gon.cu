@@ -32,6 +32,10 @@
 
 namespace kc {
 
+// Diagnostic counters of the mixed-precision sweep (since the last read):
+// [0] exact FP32 rechecks of candidates, [1] candidate-buffer overflows.
+__device__ unsigned long long g_counters[4];
+
 namespace {
 
 constexpr int GROUP_NT = 1024;   // group mode: one CTA per SM
@@ -409,51 +413,64 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                     }
                 }
             }
-            // running minimum of the approximate values
+            // Running minimum of the approximate values, kept in 16 bits: the
+            // float bits shifted right by 16 (bf16 rounded toward zero).
+            // Truncation commutes with min, so the stored code t satisfies
+            // lo(t) <= m~ < hi(t) with lo(t) = t << 16, hi(t) = (t + 1) << 16.
             const bool full = g0 >= lo && g0 + 3 < hi;
-            uint32_t o[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-            uint4 *mp = reinterpret_cast<uint4 *>(I.mind + b * BLK) + lane;
+            uint32_t o[4] = {0xFFFFu, 0xFFFFu, 0xFFFFu, 0xFFFFu};
+            uint16_t *m16 = reinterpret_cast<uint16_t *>(I.mind);
+            uint2 *mp = reinterpret_cast<uint2 *>(m16 + b * BLK) + lane;
             if (it > 0) {
                 if (full) {
-                    const uint4 ov = *mp;
-                    o[0] = ov.x;
-                    o[1] = ov.y;
-                    o[2] = ov.z;
-                    o[3] = ov.w;
+                    const uint2 ov = *mp;
+                    o[0] = ov.x & 0xFFFFu;
+                    o[1] = ov.x >> 16;
+                    o[2] = ov.y & 0xFFFFu;
+                    o[3] = ov.y >> 16;
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (g0 + q >= lo && g0 + q < hi) o[q] = I.mind[g0 + q];
+                        if (g0 + q >= lo && g0 + q < hi) o[q] = m16[g0 + q];
                 }
             }
             uint32_t m[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) m[q] = min(o[q], __float_as_uint(a[q]));
+            for (int q = 0; q < 4; ++q) m[q] = min(o[q], __float_as_uint(a[q]) >> 16);
             if (full) {
                 if (it == 0 || m[0] != o[0] || m[1] != o[1] || m[2] != o[2] || m[3] != o[3])
-                    *mp = make_uint4(m[0], m[1], m[2], m[3]);
+                    *mp = make_uint2(m[0] | (m[1] << 16), m[2] | (m[3] << 16));
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (g0 + q >= lo && g0 + q < hi && (it == 0 || m[q] != o[q])) I.mind[g0 + q] = m[q];
+                    if (g0 + q >= lo && g0 + q < hi && (it == 0 || m[q] != o[q])) m16[g0 + q] = (uint16_t)m[q];
             }
-            // bounds, running max of L, candidate collection
+            // Bounds.  L and U increase with m~ and delta is per block, so the
+            // block's largest L comes from its largest code, and U(x) >= Lrun
+            // holds iff hi(x) >= tau with tau = ((Lrun/(1+g) - delta)/(1+g))^2;
+            // tau is rounded down (admitting a superset), so no per-point
+            // square root is needed.  U is evaluated only for admitted points.
             const float delta = __fadd_ru(I.eblk[b], ecmax);
-            float U[4];
-            float bl = -INFINITY;
+            uint32_t mmax = 0;
+            bool anyv = false;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const bool v = g0 + q >= lo && g0 + q < hi;
-                U[q] = v ? lp_upper(m[q], delta, opg) : -INFINITY;
-                if (v) bl = fmaxf(bl, lp_lower(m[q], delta, omg));
-            }
+            for (int q = 0; q < 4; ++q)
+                if (g0 + q >= lo && g0 + q < hi) {
+                    mmax = max(mmax, m[q]);
+                    anyv = true;
+                }
+            float bl = anyv ? lp_lower(mmax << 16, delta, omg) : -INFINITY;
 #pragma unroll
             for (int o2 = 16; o2; o2 >>= 1) bl = fmaxf(bl, __shfl_xor_sync(0xFFFFFFFFu, bl, o2));
             Lrun = fmaxf(Lrun, bl);
             if (!ovf) {
+                const float a0 = __fsub_rd(__fdiv_rd(Lrun, opg), delta);
+                const float t0 = a0 > 0.f ? __fdiv_rd(a0, opg) : 0.f;
+                const uint32_t tau = __float_as_uint(__fmul_rd(t0, t0));
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const bool pred = U[q] >= Lrun;
+                    const uint32_t hib = (m[q] + 1u) << 16;
+                    const bool pred = g0 + q >= lo && g0 + q < hi && hib >= tau;
                     const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
                     const int nq = __popc(bal);
                     if (nq == 0) continue;
@@ -464,7 +481,9 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                             break;
                         }
                     }
-                    if (pred) buf[cnt + __popc(bal & ((1u << lane) - 1u))] = Cand{(uint32_t)(g0 + q - lo), U[q]};
+                    if (pred)
+                        buf[cnt + __popc(bal & ((1u << lane) - 1u))] =
+                            Cand{(uint32_t)(g0 + q - lo), lp_upper(hib, delta, opg)};
                     cnt += nq;
                 }
             }
@@ -480,6 +499,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
         // exact recheck of this warp's candidates with U >= T
         uint64_t best = 0;
         const int ncen = it + 1;
+        unsigned long long nre = 0;
         if (!ovf) {
             __syncwarp();
             for (int e = 0; e < cnt; ++e) {
@@ -487,16 +507,20 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                 if (c.U >= T) {
                     const uint32_t mm = exact_min_warp(pk, lo + c.idx, d, I.cenT, I.kcap, ncen, lane);
                     best = umax64(best, make_key(mm, c.idx));
+                    ++nre;
                 }
             }
         } else {
+            if (lane == 0) atomicAdd(&g_counters[1], 1ull);
             for (int64_t b = lo / BLK + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) {
                 const float delta = __fadd_ru(I.eblk[b], ecmax);
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) {
                     const int64_t g = b * BLK + lane * 4 + q;
                     const bool v = g >= lo && g < hi;
-                    const bool pred = v && lp_upper(I.mind[g], delta, opg) >= T;
+                    const bool pred =
+                        v && lp_upper(((uint32_t)reinterpret_cast<const uint16_t *>(I.mind)[g] + 1u) << 16, delta,
+                                      opg) >= T;
                     unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
                     while (bal) {
                         const int src_lane = __ffs(bal) - 1;
@@ -504,10 +528,12 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                         const int64_t gs = b * BLK + src_lane * 4 + q;
                         const uint32_t mm = exact_min_warp(pk, gs, d, I.cenT, I.kcap, ncen, lane);
                         best = umax64(best, make_key(mm, (uint32_t)(gs - lo)));
+                        ++nre;
                     }
                 }
             }
         }
+        if (lane == 0 && nre) atomicAdd(&g_counters[0], nre);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
         if (warp == 0) {
@@ -717,6 +743,15 @@ void *pick_queue(int dtype, int dc) {
 }
 
 }  // namespace
+
+cudaError_t read_counters(unsigned long long out[4], bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess && reset) {
+        const unsigned long long z[4] = {0, 0, 0, 0};
+        e = cudaMemcpyToSymbol(g_counters, z, sizeof z);
+    }
+    return e;
+}
 
 int gon_threads() { return GROUP_NT; }
 int gon_warps_per_cta() { return GROUP_NT / 32; }

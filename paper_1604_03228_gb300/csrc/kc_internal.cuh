@@ -177,6 +177,8 @@ struct GonArgs {
     int lp_kind;             // 0: FP32 sweep; KC_SWEEP_BF16 / KC_SWEEP_FP8 (float points)
 };
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s);
+// Mixed-precision diagnostics (synchronous): exact rechecks, overflows.
+cudaError_t read_counters(unsigned long long out[4], bool reset);
 int gon_max_grid(int dtype, int d, int lp = 0);
 int gon_queue_grid(int dtype, int d, int lp = 0);
 int gon_threads();

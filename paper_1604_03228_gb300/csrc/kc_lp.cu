@@ -11,7 +11,7 @@
 // (bf16: the bf16 value; fp8 e4m3: the fp8 value times the column scale
 // s_j = max_x |x_j| / 448, one FP32 multiply).  The bound
 //   e_x >= || decoded(x) - x ||_2
-// is summed in FP64 with upward rounding and rounded up to FP32.  e_pt holds it
+// sums the exact squared differences with upward rounding.  e_pt holds it
 // per point (used for the centers), e_blk the maximum over each block (used in
 // the sweep).
 #include <cuda_bf16.h>
@@ -52,7 +52,7 @@ __device__ void lp_pack_block(const float *__restrict__ pk, int64_t n, int d, co
     {
         const int i = threadIdx.x;
         const bool valid = b * BLK + i < n;
-        double e2 = 0.0;
+        float e2 = 0.f;
         for (int jg = 0; jg < ng; ++jg) {
             uint32_t word = 0;
 #pragma unroll
@@ -74,12 +74,14 @@ __device__ void lp_pack_block(const float *__restrict__ pk, int64_t n, int d, co
                     code = (uint32_t)q;
                     word |= code << (8 * t);
                 }
-                const double diff = fabs((double)x - (double)dec);
-                e2 = __fma_ru(diff, diff, e2);
+                // decoded(x) is within a factor 2 of x (or 0), so the FP32
+                // difference is exact (Sterbenz); the sum rounds upward.
+                const float diff = fabsf(__fsub_rn(x, dec));
+                e2 = __fmaf_ru(diff, diff, e2);
             }
             lp[(b * ng + jg) * BLK + i] = word;
         }
-        const float e = valid ? __double2float_ru(__dsqrt_ru(e2)) : 0.f;
+        const float e = valid ? __fsqrt_ru(e2) : 0.f;
         ept[b * BLK + i] = e;
         float m = e;
 #pragma unroll

@@ -154,7 +154,9 @@ __device__ __forceinline__ double flag_threshold(const unsigned long long *key32
 __device__ __forceinline__ bool can_reach(const uint32_t *mind, int64_t x, double thr, const float *eblk,
                                           const float *ecmax, float opg) {
     if (!eblk) return (double)__uint_as_float(mind[x]) >= thr;
-    const float U = lp_upper(mind[x], __fadd_ru(eblk[x / BLK], *ecmax), opg);
+    // mixed precision: 16-bit truncated codes, upper end of the code's interval
+    const uint32_t hi = ((uint32_t)reinterpret_cast<const uint16_t *>(mind)[x] + 1u) << 16;
+    const float U = lp_upper(hi, __fadd_ru(eblk[x / BLK], *ecmax), opg);
     return (double)U * (double)U >= thr;
 }
 
