@@ -315,6 +315,33 @@ void take_lp(Carve &cv, LPBufs &L, int lp, int64_t n, int d) {
     L.colmax = cv.take<unsigned>((size_t)d);
 }
 
+// Tensor-core radius filter scratch for kc centers over n float points
+// (left null, i.e. CUDA cores, for int32 points, d > 128, tiny center sets,
+// or KC_RADIUS_TC=0 in the environment).
+void take_tc(Carve &cv, RadiusArgs &ra, int dtype, int64_t n, int d, int kc) {
+    bool use = dtype == KC_F32 && tc_supported(d) && (int64_t)kc * d >= 256;
+    if (const char *env = getenv("KC_RADIUS_TC")) use = use && atoi(env) != 0;
+    if (!use) {
+        ra.tc_bt = nullptr;
+        return;
+    }
+    ra.tc_bt = cv.take<char>(tc_center_bytes(kc, d));
+    ra.tc_cn = cv.take<float>((size_t)tc_center_tiles(kc) * 256);
+    ra.tc_maxes = cv.take<unsigned>(2);
+    ra.tc_mlo = cv.take<float>((size_t)n);
+    ra.tc_mhi = cv.take<float>((size_t)n);
+    ra.tc_mlomax = cv.take<unsigned>(1);
+}
+
+void copy_tc(RadiusArgs &dst, const RadiusArgs &src) {
+    dst.tc_bt = src.tc_bt;
+    dst.tc_cn = src.tc_cn;
+    dst.tc_maxes = src.tc_maxes;
+    dst.tc_mlo = src.tc_mlo;
+    dst.tc_mhi = src.tc_mhi;
+    dst.tc_mlomax = src.tc_mlomax;
+}
+
 // Point an instance at the low-precision data (its own cenT [d][kcap] and
 // ecmax slot).
 void attach_lp(GonInst &I, const LPBufs &L, int lp, float *cenT, int kcap, float *ecmax) {
@@ -607,6 +634,7 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
         cin_dev = dev_cin ? centers : cv.take<int64_t>(kc);
         rad_dev = dev_rad ? radius : cv.take<double>(1);
         arg_dev = (argmax_point && dev_arg) ? argmax_point : cv.take<int64_t>(1);
+        take_tc(cv, ra, c.o.dtype, n, d, kc);
     };
     {
         Carve sizing(nullptr);
@@ -746,6 +774,7 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
     for (int i = 0; i < m; ++i) cen_off[i + 1] = cen_off[i] + ki[i];
     LPBufs LB;
     float *cenT1 = nullptr, *ecmax1 = nullptr;
+    RadiusArgs Rtc{};
     const int64_t ucap = (int64_t)m * k;
     const int G2 = (int)std::min<int64_t>(std::max<int64_t>(1, (nblocks(ucap) + W - 1) / W), std::min(maxg, 16));
     const int64_t nb = nblocks(n);
@@ -793,6 +822,7 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         take_lp(cv, LB, lp, n, d);
         cenT1 = lp ? cv.take<float>((size_t)cen_off[m] * d) : nullptr;
         ecmax1 = lp ? cv.take<float>((size_t)m) : nullptr;
+        take_tc(cv, Rtc, c.o.dtype, n, d, k);
         Lo.inst2 = cv.take<GonInst>(1);
         Lo.cen = cv.take<char>((size_t)k * d * esz);
         Lo.m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
@@ -922,6 +952,7 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         ra.argmax_out = nullptr;
         ra.st = st;
         ra.have_mind = false;
+        copy_tc(ra, Rtc);
         KC_CUDA(launch_radius(ra, c.s), "radius launch");
     }
     if (!dev_cen)
@@ -969,6 +1000,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
     const int grid = choose_gon_grid(c.o.dtype, d, n, lp);
     LPBufs LB;
     float *cenT = nullptr, *ecmax = nullptr;
+    RadiusArgs Rtc{};
 
     struct L {
         unsigned long long *sn, *hn, *rnn;
@@ -978,6 +1010,10 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         uint32_t *thr, *v;
         uint64_t *fk, *slots;
         uint8_t *mask;
+        void *tc_bt;
+        float *tc_cn;
+        unsigned *tc_maxes;
+        unsigned long long *amb;
         void *staging, *pk, *Sc, *Hc, *pkC, *cen;
         uint32_t *mind, *mindC, *R0, *R1, *S, *H, *dH;
         int *counts;
@@ -1026,6 +1062,12 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         take_lp(cv, LB, lp, n, d);
         cenT = lp ? cv.take<float>((size_t)keff_max * d) : nullptr;
         ecmax = lp ? cv.take<float>(1) : nullptr;
+        take_tc(cv, Rtc, c.o.dtype, n, d, keff_max);
+        const bool tcp = c.o.dtype == KC_F32 && tc_supported(d) && !(getenv("KC_PRUNE_TC") && !atoi(getenv("KC_PRUNE_TC")));
+        Lo.tc_bt = tcp ? cv.take<char>(tc_center_bytes((int)std::min<int64_t>(n, INT32_MAX), d)) : nullptr;
+        Lo.tc_cn = tcp ? cv.take<float>((size_t)tc_center_tiles((int)std::min<int64_t>(n, INT32_MAX)) * 256) : nullptr;
+        Lo.tc_maxes = tcp ? cv.take<unsigned>(2) : nullptr;
+        Lo.amb = cv.take<unsigned long long>(1);
     };
     {
         Carve sizing(nullptr);
@@ -1088,8 +1130,18 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
                 KC_CUDA(launch_eim_select(Lo.H, Lo.dH, (int64_t)hn, p, Lo.thr, Lo.v, c.s), "select");
             }
             TraceStep t("eim_prune", c.s);
-            KC_CUDA(launch_eim_prune(c.o.dtype, src, d, Rc, rn, Lo.mask, Lo.Sc, sn, Lo.thr, Rx, Lo.rnn, c.s),
-                    "prune");
+            if (Lo.tc_bt && sn >= 256) {
+                // tensor-core R x S block with exact rechecks of undecided pairs
+                KC_CUDA(launch_tc_prep((const float *)Lo.Sc, nullptr, (int)sn, d, Lo.tc_bt, Lo.tc_cn, Lo.tc_maxes,
+                                       c.s),
+                        "prune prep");
+                KC_CUDA(launch_tc_prune((const float *)src, d, Rc, rn, Lo.mask, (const float *)Lo.Sc, sn, Lo.tc_bt,
+                                        Lo.tc_cn, Lo.tc_maxes, Lo.thr, Rx, Lo.rnn, Lo.amb, st, c.s),
+                        "prune");
+            } else {
+                KC_CUDA(launch_eim_prune(c.o.dtype, src, d, Rc, rn, Lo.mask, Lo.Sc, sn, Lo.thr, Rx, Lo.rnn, c.s),
+                        "prune");
+            }
         } else {
             KC_CUDA(launch_eim_drop_sampled(Rc, rn, Lo.mask, Rx, Lo.rnn, c.s), "drop sampled");
         }
@@ -1149,6 +1201,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         ra.argmax_out = nullptr;
         ra.st = st;
         ra.have_mind = false;
+        copy_tc(ra, Rtc);
         KC_CUDA(launch_radius(ra, c.s), "radius launch");
     }
     if (!dev_cen)

@@ -327,7 +327,38 @@ struct RadiusArgs {
     // flag test then uses the upper bound U(x) (eblk per block, *ecmax)
     const float *eblk;
     const float *ecmax;
+    // tensor-core filter scratch (float points, d <= 128); null: CUDA cores
+    void *tc_bt;             // [tc_center_bytes] bf16 center tiles
+    float *tc_cn;            // [tiles * 256] center norms
+    unsigned *tc_maxes;      // [2]
+    float *tc_mlo, *tc_mhi;  // [n] per-point bounds
+    unsigned *tc_mlomax;     // [1]
 };
+
+// ------------------------------------------------- tensor-core blocks
+bool tc_supported(int d);
+size_t tc_center_bytes(int kc, int d);
+int tc_center_tiles(int kc);
+cudaError_t launch_tc_prep(const float *cen, const int32_t *kc_dev, int kc, int d, void *bt, float *cn, unsigned *maxes,
+                           cudaStream_t s);
+cudaError_t launch_tc_radius(const float *pk, int64_t n, int d, const float *cen, const int32_t *kc_dev, int kc,
+                             const void *bt, const float *cn, const unsigned *maxes, float *mlo, float *mhi,
+                             unsigned *mlo_max, uint32_t *mind, unsigned long long *key32, DevStatus *st,
+                             cudaStream_t s);
+cudaError_t launch_tc_prune(const float *src, int d, const uint32_t *R, int64_t rn, const uint8_t *inS, const float *Scen,
+                            int64_t sn, const void *bt, const float *cn, const unsigned *maxes, const uint32_t *thr,
+                            uint32_t *Rn, unsigned long long *rnn, unsigned long long *amb, DevStatus *st,
+                            cudaStream_t s);
+
+// Scratch for the tensor-core radius filter of kc centers over n points.
+struct TcScratch {
+    size_t bt_bytes;
+    int tiles;
+};
+inline TcScratch tc_scratch(int64_t n, int d, int kc) {
+    (void)n;
+    return TcScratch{tc_center_bytes(kc, d), tc_center_tiles(kc)};
+}
 cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s);
 
 }  // namespace kc

@@ -187,3 +187,29 @@ def test_errors_are_status_codes(kc):
     # the library stays usable after errors
     ok = I.gauss_mixture(500, 3, 1, 2, 1.0, 0, 1)
     check_float_gon(kc, ok, 5)
+
+
+# ------------------------------------------- tensor-core radius filter
+
+@pytest.mark.parametrize("n,d,kc_", [(1000, 3, 100), (40000, 10, 100), (20000, 16, 300), (9000, 17, 513),
+                                      (30000, 64, 1000), (5000, 100, 257), (4000, 128, 64), (3000, 129, 40)])
+def test_radius_tensor_core_matches_cuda_cores(kc, n, d, kc_, monkeypatch):
+    pts = I.gauss_mixture(n, d, 200 + d, 11, 0.7, -15, 15)
+    C = I.uniform_int(57, d, kc_, 0, n - 1)
+    x, c = _dev(pts), _dev(C)
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    a = kc.kc_radius(x, c)
+    monkeypatch.setenv("KC_RADIUS_TC", "0")
+    b = kc.kc_radius(x, c)
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    assert a.radius == b.radius == r64 and a.argmax == b.argmax == am
+
+
+def test_radius_tensor_core_ties_and_far_points(kc):
+    # duplicated points, centers among them, and a point far away
+    base = I.gauss_mixture(500, 12, 58, 4, 0.3, -2, 2)
+    pts = np.concatenate([np.repeat(base, 20, axis=0), np.full((1, 12), 9.0, np.float32)])
+    C = np.arange(0, 10000, 37)
+    rr = kc.kc_radius(_dev(pts), _dev(C))
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    assert rr.radius == r64 and rr.argmax == am == 10000
