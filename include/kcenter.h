@@ -248,8 +248,10 @@ int64_t kc_launch_count(void);
  * kc_counters -- diagnostics of the mixed-precision sweep on the current
  * device since the last call (which it resets): out[0] = candidates
  * recomputed exactly in FP32, out[1] = candidate-buffer overflows (a warp
- * rescanned its running minima), out[2..3] reserved.  Synchronises the
- * device.  Returns the number of values (4), or -1 on a CUDA error.
+ * rescanned its running minima); and of EIM's tensor-core prune: out[2] =
+ * (point, center) pairs left undecided by the bounds and recomputed exactly,
+ * out[3] = points processed.  Synchronises the device.  Returns the number of
+ * values (4), or -1 on a CUDA error.
  */
 int32_t kc_counters(int64_t *out, int32_t cap);
 

@@ -83,11 +83,12 @@ def load(path: str | None = None):
 
 
 def kc_counters():
-    """Mixed-precision diagnostics since the last call: (exact rechecks, overflows)."""
+    """Diagnostics since the last call: (sweep exact rechecks, sweep buffer
+    overflows, prune undecided pairs, prune points)."""
     out = np.zeros(4, dtype=np.int64)
     if load().kc_counters(out.ctypes.data, 4) < 0:
         raise KCError(KC_ERR_CUDA, "kc_counters failed")
-    return int(out[0]), int(out[1])
+    return tuple(int(v) for v in out)
 
 
 class kc_trace_rec(ct.Structure):

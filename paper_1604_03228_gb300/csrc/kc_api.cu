@@ -319,24 +319,34 @@ void take_lp(Carve &cv, LPBufs &L, int lp, int64_t n, int d) {
 // (left null, i.e. CUDA cores, for int32 points, d > 128, tiny center sets,
 // or KC_RADIUS_TC=0 in the environment).
 void take_tc(Carve &cv, RadiusArgs &ra, int dtype, int64_t n, int d, int kc) {
-    bool use = dtype == KC_F32 && tc_supported(d) && (int64_t)kc * d >= 256;
-    if (const char *env = getenv("KC_RADIUS_TC")) use = use && atoi(env) != 0;
+    bool use = dtype == KC_F32 && tc_supported(d) && (int64_t)kc * d >= 8192;
+    if (const char *env = getenv("KC_RADIUS_TC")) use = dtype == KC_F32 && tc_supported(d) && atoi(env) != 0;
     if (!use) {
-        ra.tc_bt = nullptr;
+        ra.tc_at = nullptr;
         return;
     }
+    ra.tc_at = cv.take<char>(tc_point_bytes(n, d));
+    ra.tc_an = cv.take<float>((size_t)tc_point_rows(n));
+    ra.tc_ae = cv.take<float>((size_t)tc_point_rows(n));
     ra.tc_bt = cv.take<char>(tc_center_bytes(kc, d));
     ra.tc_cn = cv.take<float>((size_t)tc_center_tiles(kc) * 256);
+    ra.tc_ce = cv.take<float>((size_t)tc_center_tiles(kc) * 256);
     ra.tc_maxes = cv.take<unsigned>(2);
+    ra.tc_absmax = cv.take<unsigned>(1);
     ra.tc_mlo = cv.take<float>((size_t)n);
     ra.tc_mhi = cv.take<float>((size_t)n);
     ra.tc_mlomax = cv.take<unsigned>(1);
 }
 
 void copy_tc(RadiusArgs &dst, const RadiusArgs &src) {
+    dst.tc_at = src.tc_at;
     dst.tc_bt = src.tc_bt;
+    dst.tc_an = src.tc_an;
+    dst.tc_ae = src.tc_ae;
     dst.tc_cn = src.tc_cn;
+    dst.tc_ce = src.tc_ce;
     dst.tc_maxes = src.tc_maxes;
+    dst.tc_absmax = src.tc_absmax;
     dst.tc_mlo = src.tc_mlo;
     dst.tc_mhi = src.tc_mhi;
     dst.tc_mlomax = src.tc_mlomax;
@@ -397,7 +407,8 @@ void kc_trace_enable(int32_t on) { g_trace_on = on ? 1 : 0; }
 
 int32_t kc_counters(int64_t *out, int32_t cap) {
     unsigned long long v[4] = {0, 0, 0, 0};
-    if (cudaDeviceSynchronize() != cudaSuccess || read_counters(v, true) != cudaSuccess) {
+    if (cudaDeviceSynchronize() != cudaSuccess || read_counters(v, true) != cudaSuccess ||
+        read_tc_counters(v + 2, true) != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }
@@ -1000,7 +1011,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
     const int grid = choose_gon_grid(c.o.dtype, d, n, lp);
     LPBufs LB;
     float *cenT = nullptr, *ecmax = nullptr;
-    RadiusArgs Rtc{};
+    RadiusArgs Rtc{}, Ptc{};
 
     struct L {
         unsigned long long *sn, *hn, *rnn;
@@ -1010,10 +1021,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         uint32_t *thr, *v;
         uint64_t *fk, *slots;
         uint8_t *mask;
-        void *tc_bt;
-        float *tc_cn;
-        unsigned *tc_maxes;
-        unsigned long long *amb;
+        PruneBufs pb;
         void *staging, *pk, *Sc, *Hc, *pkC, *cen;
         uint32_t *mind, *mindC, *R0, *R1, *S, *H, *dH;
         int *counts;
@@ -1064,10 +1072,28 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         ecmax = lp ? cv.take<float>(1) : nullptr;
         take_tc(cv, Rtc, c.o.dtype, n, d, keff_max);
         const bool tcp = c.o.dtype == KC_F32 && tc_supported(d) && !(getenv("KC_PRUNE_TC") && !atoi(getenv("KC_PRUNE_TC")));
-        Lo.tc_bt = tcp ? cv.take<char>(tc_center_bytes((int)std::min<int64_t>(n, INT32_MAX), d)) : nullptr;
-        Lo.tc_cn = tcp ? cv.take<float>((size_t)tc_center_tiles((int)std::min<int64_t>(n, INT32_MAX)) * 256) : nullptr;
-        Lo.tc_maxes = tcp ? cv.take<unsigned>(2) : nullptr;
-        Lo.amb = cv.take<unsigned long long>(1);
+        Ptc.tc_at = nullptr;
+        if (tcp) {   // tiles for up to n points of R and n centers of S
+            Ptc.tc_at = cv.take<char>(tc_point_bytes(n, d));
+            Ptc.tc_an = cv.take<float>((size_t)tc_point_rows(n));
+            Ptc.tc_ae = cv.take<float>((size_t)tc_point_rows(n));
+            Ptc.tc_bt = cv.take<char>(tc_center_bytes(n, d));
+            Ptc.tc_cn = cv.take<float>((size_t)tc_center_tiles(n) * 256);
+            Ptc.tc_ce = cv.take<float>((size_t)tc_center_tiles(n) * 256);
+            Ptc.tc_maxes = cv.take<unsigned>(2);
+            Ptc.tc_absmax = cv.take<unsigned>(1);
+        }
+        Lo.pb = PruneBufs{};
+        if (tcp) {   // deferred exact checks: up to 2 pairs per point before full rescans
+            Lo.pb.pcap = std::max<int64_t>(2 * n, 1 << 16);
+            if (const char *e = getenv("KC_PRUNE_PAIR_CAP")) Lo.pb.pcap = std::max<int64_t>(1, atoll(e));
+            Lo.pb.pairs = cv.take<uint2>((size_t)Lo.pb.pcap);
+            Lo.pb.flag = cv.take<uint8_t>((size_t)n);
+            Lo.pb.hit = cv.take<uint8_t>((size_t)n);
+            Lo.pb.pend = cv.take<uint32_t>((size_t)n);
+            Lo.pb.npairs = cv.take<unsigned long long>(1);
+            Lo.pb.npend = cv.take<unsigned long long>(1);
+        }
     };
     {
         Carve sizing(nullptr);
@@ -1098,6 +1124,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         KC_CUDA(launch_pack(src, c.o.dtype, n, d, Lo.pk, Lo.range2, st, c.s), "pack launch");
         if (c.o.dtype == KC_I32) KC_CUDA(launch_range_check(Lo.range2, d, st, c.s), "range check");
         KC_CUDA(launch_eim_iota(Lo.R0, n, c.s), "iota launch");
+        if (Ptc.tc_at) KC_CUDA(launch_tc_absmax((const float *)Lo.pk, n, d, Ptc.tc_absmax, c.s), "absmax");
     }
     KC_CUDA(cudaStreamSynchronize(c.s), "cudaStreamSynchronize");
     if (device_error()) return finish(c.arena, c.s);
@@ -1130,13 +1157,10 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
                 KC_CUDA(launch_eim_select(Lo.H, Lo.dH, (int64_t)hn, p, Lo.thr, Lo.v, c.s), "select");
             }
             TraceStep t("eim_prune", c.s);
-            if (Lo.tc_bt && sn >= 256) {
+            if (Ptc.tc_at && sn >= 256) {
                 // tensor-core R x S block with exact rechecks of undecided pairs
-                KC_CUDA(launch_tc_prep((const float *)Lo.Sc, nullptr, (int)sn, d, Lo.tc_bt, Lo.tc_cn, Lo.tc_maxes,
-                                       c.s),
-                        "prune prep");
-                KC_CUDA(launch_tc_prune((const float *)src, d, Rc, rn, Lo.mask, (const float *)Lo.Sc, sn, Lo.tc_bt,
-                                        Lo.tc_cn, Lo.tc_maxes, Lo.thr, Rx, Lo.rnn, Lo.amb, st, c.s),
+                KC_CUDA(launch_tc_prune((const float *)src, d, Rc, rn, Lo.mask, (const float *)Lo.Sc, sn, tc_bufs(Ptc),
+                                        Lo.pb, Lo.thr, Rx, Lo.rnn, st, c.s),
                         "prune");
             } else {
                 KC_CUDA(launch_eim_prune(c.o.dtype, src, d, Rc, rn, Lo.mask, Lo.Sc, sn, Lo.thr, Rx, Lo.rnn, c.s),

@@ -327,38 +327,52 @@ struct RadiusArgs {
     // flag test then uses the upper bound U(x) (eblk per block, *ecmax)
     const float *eblk;
     const float *ecmax;
-    // tensor-core filter scratch (float points, d <= 128); null: CUDA cores
-    void *tc_bt;             // [tc_center_bytes] bf16 center tiles
-    float *tc_cn;            // [tiles * 256] center norms
-    unsigned *tc_maxes;      // [2]
-    float *tc_mlo, *tc_mhi;  // [n] per-point bounds
-    unsigned *tc_mlomax;     // [1]
+    // tensor-core filter scratch (float points, d <= 128); tc_at null: CUDA cores
+    void *tc_at, *tc_bt;
+    float *tc_an, *tc_ae, *tc_cn, *tc_ce, *tc_mlo, *tc_mhi;
+    unsigned *tc_maxes, *tc_absmax, *tc_mlomax;
 };
 
 // ------------------------------------------------- tensor-core blocks
-bool tc_supported(int d);
-size_t tc_center_bytes(int kc, int d);
-int tc_center_tiles(int kc);
-cudaError_t launch_tc_prep(const float *cen, const int32_t *kc_dev, int kc, int d, void *bt, float *cn, unsigned *maxes,
-                           cudaStream_t s);
-cudaError_t launch_tc_radius(const float *pk, int64_t n, int d, const float *cen, const int32_t *kc_dev, int kc,
-                             const void *bt, const float *cn, const unsigned *maxes, float *mlo, float *mhi,
-                             unsigned *mlo_max, uint32_t *mind, unsigned long long *key32, DevStatus *st,
-                             cudaStream_t s);
-cudaError_t launch_tc_prune(const float *src, int d, const uint32_t *R, int64_t rn, const uint8_t *inS, const float *Scen,
-                            int64_t sn, const void *bt, const float *cn, const unsigned *maxes, const uint32_t *thr,
-                            uint32_t *Rn, unsigned long long *rnn, unsigned long long *amb, DevStatus *st,
-                            cudaStream_t s);
-
-// Scratch for the tensor-core radius filter of kc centers over n points.
-struct TcScratch {
-    size_t bt_bytes;
-    int tiles;
+// Scratch of one tensor-core block: fp16 point tiles (at) with norms and
+// bounds, fp16 center tiles (bt) with norms and bounds, their maxima, the
+// coordinate maximum that fixes the scale, and the radius outputs.
+struct TcBufs {
+    void *at, *bt;
+    float *an, *ae, *cn, *ce;
+    unsigned *maxes, *absmax;
+    float *mlo, *mhi;
+    unsigned *mlomax;
 };
-inline TcScratch tc_scratch(int64_t n, int d, int kc) {
-    (void)n;
-    return TcScratch{tc_center_bytes(kc, d), tc_center_tiles(kc)};
+inline TcBufs tc_bufs(const RadiusArgs &a) {
+    return TcBufs{a.tc_at, a.tc_bt, a.tc_an, a.tc_ae, a.tc_cn, a.tc_ce, a.tc_maxes, a.tc_absmax, a.tc_mlo, a.tc_mhi,
+                  a.tc_mlomax};
 }
+bool tc_supported(int d);
+cudaError_t read_tc_counters(unsigned long long out[2], bool reset);
+int tc_center_tiles(int64_t kc);
+size_t tc_center_bytes(int64_t kc, int d);
+size_t tc_point_bytes(int64_t n, int d);
+int64_t tc_point_rows(int64_t n);
+cudaError_t launch_tc_absmax(const float *pk, int64_t n, int d, unsigned *absmax, cudaStream_t s);
+cudaError_t launch_tc_radius(const float *pk, int64_t n, int d, const float *cen, const int32_t *kc_dev, int kc,
+                             const TcBufs &B, uint32_t *mind, unsigned long long *key32, DevStatus *st,
+                             cudaStream_t s);
+// Deferred exact checks of the tensor-core prune: the (row, center) pairs
+// its bounds leave undecided, per-row flags, the rows they decide, and the
+// counters of both lists.  pairs holds pcap entries; rows beyond it get a
+// full exact scan instead.  flag and hit hold one byte per row of R.
+struct PruneBufs {
+    uint2 *pairs;
+    int64_t pcap;
+    uint8_t *flag, *hit;
+    uint32_t *pend;
+    unsigned long long *npairs, *npend;
+};
+// B.absmax must already hold the coordinate maximum over a superset of R and S.
+cudaError_t launch_tc_prune(const float *src, int d, const uint32_t *R, int64_t rn, const uint8_t *inS, const float *Scen,
+                            int64_t sn, const TcBufs &B, const PruneBufs &P, const uint32_t *thr, uint32_t *Rn,
+                            unsigned long long *rnn, DevStatus *st, cudaStream_t s);
 cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s);
 
 }  // namespace kc

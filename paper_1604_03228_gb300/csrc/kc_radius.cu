@@ -290,14 +290,12 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (!a.have_mind) {
-        if (a.dtype == KC_F32 && a.tc_bt && tc_supported(a.d)) {
-            // tensor-core filter: bf16 dot products bound every point's
+        if (a.dtype == KC_F32 && a.tc_at && tc_supported(a.d)) {
+            // tensor-core filter: fp16 dot products bound every point's
             // canonical minimum; only points that can reach the maximum get
             // their exact canonical FP32 minimum (the rest get 0)
-            e = launch_tc_prep((const float *)a.cen, a.kc_dev, a.kc_max, a.d, a.tc_bt, a.tc_cn, a.tc_maxes, s);
-            if (e != cudaSuccess) return e;
-            e = launch_tc_radius((const float *)a.pk, a.n, a.d, (const float *)a.cen, a.kc_dev, a.kc_max, a.tc_bt,
-                                 a.tc_cn, a.tc_maxes, a.tc_mlo, a.tc_mhi, a.tc_mlomax, a.mind, a.key32, a.st, s);
+            e = launch_tc_radius((const float *)a.pk, a.n, a.d, (const float *)a.cen, a.kc_dev, a.kc_max, tc_bufs(a),
+                                 a.mind, a.key32, a.st, s);
         } else {
             e = a.dtype == KC_F32 ? dispatch_min<float>(a, s, sms) : dispatch_min<int32_t>(a, s, sms);
         }
@@ -315,7 +313,7 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
     }
     finalize_kernel<<<1, 1, 0, s>>>(a.dtype, a.key32, a.max64, a.arg64, a.radius_out, a.argmax_out,
                                     a.st);
-    const bool tc = a.dtype == KC_F32 && a.tc_bt && tc_supported(a.d);
+    const bool tc = a.dtype == KC_F32 && a.tc_at && tc_supported(a.d);
     note_launches(2 + (a.have_mind || tc ? 0 : 1) + (a.dtype == KC_F32 ? 2 : 0));
     return cudaGetLastError();
 }

@@ -3,35 +3,45 @@
 // EIM's prune of R against the sample S (Algorithm 2, the round Section 5.2
 // finds dominant).
 //
-// A CTA owns a tile of 128 points (the MMA's M) and streams the centers in
-// tiles of 256 (N).  Points and centers are rounded to bf16; one
-// tcgen05.mma.kind::f16 per 16 coordinates accumulates the 128 x 256 dot
-// products x~.c~ in FP32 in tensor memory (two accumulators, 512 columns),
-// while bulk copies stage the next center tile in shared memory.  Warps:
-//   0-7  epilogue: warps w and w+4 own point rows 32(w%4).. (their TMEM
-//        lanes) and split the 256 accumulator columns; each thread forms
-//        s~ = |x~|^2 + |c~|^2 - 2 x~.c~ per center from tcgen05.ld values
-//   8    producer: cp.async.bulk of pre-laid-out center tiles
-//   9    MMA issuer (one thread)
-// Operand layout in shared memory: no swizzle, K-major, 8x16-byte core
-// matrices; core matrix (row block mi, column block ki) of an R-row tile at
-// byte ((ki * R/8) + mi) * 128, so the descriptor's leading (K) byte offset
-// is R/8 * 128 and its stride (M/N) byte offset is 128.
+// Operands.  Points and centers are scaled by 2^e (e chosen so that every
+// |coordinate| <= 2^14, an exact scaling) and rounded to fp16.  A prep pass
+// writes them once as MMA tiles (128 point rows or 256 center rows by Kp =
+// d rounded up to 16 coordinates) in the shared-memory operand layout, with
+// per-row |x~|^2 and error bound e_x = ||x~ - 2^e x|| (FP32, rounded up).
 //
-// Error bound.  With e_x = ||x~ - x|| (and E = max over centers of e_c), the
-// products of bf16 values are exact and the FP32 accumulation, the norms and
-// the two epilogue operations are covered by
-//   |s~ - ||x~ - c~||^2| <= eta (|x~|^2 + |c~|^2),  eta = g_d + (K+16) 2^-21 + 2^-21,
-// a deliberately loose model of the tensor core's accumulation.  With the
-// triangle inequality ||x - c|| in [||x~-c~|| - e_x - e_c, ||x~-c~|| + e_x + e_c]
+// Kernel.  One persistent CTA per SM (it holds all 512 TMEM columns).  Warps:
+//   8    producer: cp.async.bulk of point tiles (2-stage ring) and center
+//        tiles (2-stage ring) into shared memory
+//   9    MMA issuer (one thread): tcgen05.mma.kind::f16, M=128 x N=256,
+//        Kp/16 instructions per tile pair, FP32 accumulators double-buffered
+//        in TMEM (2 x 256 columns)
+//   0-7  epilogue: warps w and w+4 own point rows 32(w%4).. (their TMEM
+//        lanes) and split the 256 columns; per (point, center) they form
+//        v = 2 x~.c~ - |c~|^2 (one FMA) and keep its maximum (radius) or
+//        compare it with the point's two decision limits (prune), since
+//        s~ = |x~|^2 - v approximates ||x~ - c~||^2.
+// Shared-memory operand layout: no swizzle, K-major, 8 x 16-byte core
+// matrices; core matrix (row block mi, column block ki) of an R-row tile at
+// byte ((ki * R/8) + mi) * 128: the descriptor's leading (K) byte offset is
+// R/8 * 128 and its stride (M/N) byte offset 128.
+//
+// Error bound.  fp16 products are exact; the FP32 accumulation, the norms and
+// the epilogue operations are covered by
+//   |s~ - ||x~ - c~||^2| <= eta (|x~|^2 + |c~|^2),  eta = g_d + (Kp+16) 2^-21 + 2^-21
+// (a deliberately loose model of the tensor core's accumulation).  With the
+// triangle inequality ||x - c|| in ||x~ - c~|| -+ (e_x + e_c) (scaled units)
 // and the canonical FP32 value within (1 +- g_d) of the exact one, every
-// decision below is taken on bounds that contain the canonical FP32 value;
-// undecided cases are recomputed exactly.
-#include <cuda_bf16.h>
+// decision is taken on bounds that contain the canonical FP32 value; the
+// undecided cases are recomputed exactly from the FP32 coordinates.
+#include <cuda_fp16.h>
 
 #include "kc_internal.cuh"
 
 namespace kc {
+
+// Diagnostics of the tensor-core prune (since the last read): [0] exact pair
+// checks of undecided pairs, [1] points processed.
+__device__ unsigned long long g_tc_counters[2];
 
 namespace {
 
@@ -53,10 +63,10 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
     return d;
 }
 
-// kind::f16 instruction descriptor: FP32 accumulate, bf16 A and B, both
+// kind::f16 instruction descriptor: FP32 accumulate, fp16 A and B, both
 // K-major, N >> 3 at bit 17, M >> 4 at bit 24.
-__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+__host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
@@ -92,7 +102,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
@@ -120,54 +130,93 @@ __host__ __device__ __forceinline__ int core_off(int R, int r, int k) {
     return ((k >> 3) * (R >> 3) + (r >> 3)) * 64 + (r & 7) * 8 + (k & 7);
 }
 
-// ------------------------------------------------------------ center prep
-// Centers (FP32 rows [kc][d]) -> bf16 tiles of TC_N rows in the core layout,
-// |c~|^2 per center (+inf for padding rows), and the maxima of e_c and |c~|^2.
-__global__ void tc_prep_kernel(const float *__restrict__ cen, const int32_t *kc_dev, int kc_max, int d, int kp,
-                               int ntiles, __nv_bfloat16 *__restrict__ bt, float *__restrict__ cn,
-                               unsigned *__restrict__ maxes) {
-    const int kc = kc_dev ? *kc_dev : kc_max;
-    const int tile_elems = TC_N * kp;
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < (int64_t)ntiles * TC_N;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(c / TC_N), r = (int)(c % TC_N);
-        __nv_bfloat16 *tile = bt + (int64_t)t * tile_elems;
+// Scale 2^e with max|coordinate| * 2^e <= 2^14 (1 for an all-zero input).
+__device__ __forceinline__ float tc_scale(const unsigned *absmax) {
+    const float m = __uint_as_float(*absmax);
+    if (!(m > 0.f)) return 1.f;
+    int ex;
+    frexpf(m, &ex);               // m = f 2^ex, f in [0.5, 1): m < 2^ex
+    return ldexpf(1.f, 14 - ex);  // m 2^(14-ex) < 2^14
+}
+
+// ------------------------------------------------------------------ prep
+__global__ void tc_absmax_kernel(const float *__restrict__ pk, int64_t n, int d, unsigned *absmax) {
+    float m = 0.f;
+    const int64_t total = nblocks(n) * (int64_t)d * BLK;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(pk[e]));   // padding is zero
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(absmax, __float_as_uint(m));
+}
+
+// Rows -> fp16 MMA tiles of R rows.  Row i is a point or center: from the
+// packed array (pk) when pk != null, else row idx ? idx[i] : i of the
+// row-major array rm.  Rows past the count are zero with norm +inf (they
+// never win a minimum or pass a threshold).  maxes (optional) gets the
+// largest e and the largest norm.
+template <int R>
+__global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__restrict__ rm,
+                               const uint32_t *__restrict__ idx, const int32_t *cnt_dev, int64_t cnt_max, int d,
+                               int kp, int64_t ntiles, const unsigned *absmax, __half *__restrict__ tiles,
+                               float *__restrict__ norm, float *__restrict__ err, unsigned *maxes) {
+    const int64_t cnt = cnt_dev ? (int64_t)*cnt_dev : cnt_max;
+    const float sc = tc_scale(absmax);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ntiles * R;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / R;
+        const int r = (int)(i % R);
+        __half *tile = tiles + t * (int64_t)R * kp;
+        const bool valid = i < cnt;
+        int64_t g = 0;
+        if (valid) g = pk ? i : (idx ? (int64_t)idx[i] : i);
         float nrm = 0.f, e2 = 0.f;
         for (int k = 0; k < kp; ++k) {
-            const float x = (c < kc && k < d) ? cen[c * d + k] : 0.f;
-            const __nv_bfloat16 q = __float2bfloat16_rn(x);
-            const float xq = __bfloat162float(q);
-            const float df = fabsf(__fsub_rn(x, xq));
+            float x = 0.f;
+            if (valid && k < d) x = __fmul_rn(pk ? pk[pk_index(g, k, d)] : rm[g * d + k], sc);   // exact
+            const __half q = __float2half_rn(x);
+            const float xq = __half2float(q);
+            const float df = fabsf(__fsub_rn(x, xq));   // exact (Sterbenz) or x itself
             e2 = __fmaf_ru(df, df, e2);
             nrm = __fmaf_rn(xq, xq, nrm);
-            tile[core_off(TC_N, r, k)] = q;
+            tile[core_off(R, r, k)] = q;
         }
-        cn[c] = c < kc ? nrm : INFINITY;
-        if (c < kc) {
-            atomicMax(&maxes[0], __float_as_uint(__fsqrt_ru(e2)));
+        const float e = __fsqrt_ru(e2);
+        norm[i] = valid ? nrm : INFINITY;
+        err[i] = valid ? e : 0.f;
+        if (maxes && valid) {
+            atomicMax(&maxes[0], __float_as_uint(e));
             atomicMax(&maxes[1], __float_as_uint(nrm));
         }
     }
 }
 
 struct TcArgs {
-    int mode;                   // 0: radius (per-point bounds), 1: EIM prune
-    int d, kp, kc, ntiles;
-    int64_t npts;               // points (radius: n; prune: |R|)
-    const float *pk;            // radius: packed FP32 points
-    const float *src;           // prune: row-major FP32 points
-    const uint32_t *R;          // prune: point indices
-    const uint8_t *inS;         // prune: sampled points (always removed)
-    const __nv_bfloat16 *bt;    // center tiles
-    const float *cn;            // [ntiles * TC_N]
-    const unsigned *maxes;      // [0] = E (max e_c), [1] = max |c~|^2 (float bits)
+    int d, kp, kc, ntiles;      // centers: kc real of ntiles * TC_N rows
+    int64_t npts;               // points (rows of the A tiles)
+    const __half *at;           // point tiles [ceil(npts/128)][128 x kp]
+    const float *an, *ae;       // point norms and bounds
+    const __half *bt;           // center tiles [ntiles][256 x kp]
+    const float *cn;            // center norms [ntiles * 256]
+    const unsigned *maxes;      // [0] = E (max e_c), [1] = max |c~|^2 (float bits), scaled units
+    const unsigned *absmax;     // max |coordinate| (float bits), for the scale
+    // radius
+    float *mlo, *mhi;           // per-point bounds on the canonical minimum (unscaled)
+    unsigned *mlo_max;
+    // prune
+    const float *src;           // row-major FP32 points
+    const uint32_t *R;          // point indices of the rows
+    const uint8_t *inS;         // sampled points (always removed)
     const float *cen;           // FP32 center rows (exact rechecks)
-    float *mlo, *mhi;           // radius: per-point bounds on the canonical minimum
-    unsigned *mlo_max;          // radius: max of mlo (float bits)
-    const uint32_t *thr;        // prune: threshold (canonical FP32 bits)
-    uint32_t *Rn;               // prune: kept points
+    const uint32_t *thr;        // threshold (canonical FP32 bits)
+    uint32_t *Rn;               // kept points
     unsigned long long *rnn;
-    unsigned long long *amb;    // prune diagnostics: exact pair checks
+    uint2 *pairs;               // undecided (row, center) pairs
+    int64_t pcap;
+    unsigned long long *npairs;
+    uint8_t *pflag;             // per row: bit 0 pairs deferred, bit 1 pair buffer overflowed
+    uint32_t *pend;             // rows decided by the pair check
+    unsigned long long *npend;
     DevStatus *st;
 };
 
@@ -180,29 +229,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int kp = a.kp;
     const uint32_t a_bytes = (uint32_t)TC_M * kp * 2, b_bytes = (uint32_t)TC_N * kp * 2;
-    __nv_bfloat16 *sA = reinterpret_cast<__nv_bfloat16 *>(smem);
-    __nv_bfloat16 *sB0 = reinterpret_cast<__nv_bfloat16 *>(smem + a_bytes);
-    __nv_bfloat16 *sB1 = reinterpret_cast<__nv_bfloat16 *>(smem + a_bytes + b_bytes);
-    __shared__ __align__(8) uint64_t b_full[2], b_empty[2], t_full[2], t_empty[2], a_full, a_empty;
+    // point tiles at smem + stage * a_bytes, center tiles after them
+    unsigned char *const sAb = smem, *const sBb = smem + 2 * a_bytes;
+    __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], t_full[2], t_empty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
-    __shared__ float s_xn[TC_M], s_ex[TC_M], s_part[TC_M];
-    __shared__ int s_gone[TC_M], s_gone2[TC_M];
+    __shared__ float s_part[TC_M];
+    __shared__ int s_gone[TC_M];   // prune: the row is surely within the threshold
+    __shared__ int s_pend[TC_M];   // prune: the row's other half deferred pairs (bit 0) or overflowed (bit 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntile_pts = (a.npts + TC_M - 1) / TC_M;
     volatile int *abort = &s_abort;
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_empty[s], 1);
             mbar_init(&b_full[s], 1);
             mbar_init(&b_empty[s], 1);
             mbar_init(&t_full[s], 1);
             mbar_init(&t_empty[s], TC_EPI);
         }
-        mbar_init(&a_full, TC_M);
-        mbar_init(&a_empty, 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < TC_M) {
+        s_gone[tid] = 0;
+        s_pend[tid] = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -217,185 +270,216 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
     if (warp == 8) {
         // ------------------------------------------------ producer
         if (lane == 0) {
-            uint32_t fills[2] = {0, 0};
-            int64_t u = 0;
-            for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x) {
+            uint32_t afill[2] = {0, 0}, bfill[2] = {0, 0};
+            int64_t u = 0, p = 0;
+            for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x, ++p) {
+                const int sa = (int)(p & 1);
+                if (!mbar_wait(&a_empty[sa], (afill[sa] & 1u) ^ 1u, abort)) {
+                    *abort = 1;
+                    set_status(a.st, KC_ERR_TIMEOUT, 6, 0);
+                    break;
+                }
+                mbar_expect_tx(&a_full[sa], a_bytes);
+                bulk_g2s(sAb + sa * a_bytes, a.at + pt * (int64_t)TC_M * kp, a_bytes, &a_full[sa]);
+                ++afill[sa];
                 for (int t = 0; t < a.ntiles; ++t, ++u) {
                     const int s = (int)(u & 1);
-                    if (!mbar_wait(&b_empty[s], (fills[s] & 1u) ^ 1u, abort)) {
+                    if (!mbar_wait(&b_empty[s], (bfill[s] & 1u) ^ 1u, abort)) {
                         *abort = 1;
                         set_status(a.st, KC_ERR_TIMEOUT, 6, t);
                         break;
                     }
                     mbar_expect_tx(&b_full[s], b_bytes);
-                    bulk_g2s(s ? sB1 : sB0, a.bt + (int64_t)t * TC_N * kp, b_bytes, &b_full[s]);
-                    ++fills[s];
+                    bulk_g2s(sBb + s * b_bytes, a.bt + (int64_t)t * TC_N * kp, b_bytes, &b_full[s]);
+                    ++bfill[s];
                 }
             }
         }
     } else if (warp == 9) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = umma_idesc_bf16(TC_M, TC_N);
+            const uint32_t idesc = umma_idesc_f16(TC_M, TC_N);
             const uint32_t a_lbo = (TC_M / 8) * 128, b_lbo = (TC_N / 8) * 128;
-            uint32_t uses_b[2] = {0, 0}, uses_t[2] = {0, 0}, pts = 0;
-            int64_t u = 0;
-            for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x, ++pts) {
-                if (!mbar_wait(&a_full, pts & 1u, abort)) {
+            uint32_t ause[2] = {0, 0}, buse[2] = {0, 0}, tuse[2] = {0, 0};
+            int64_t u = 0, p = 0;
+            for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x, ++p) {
+                const int sa = (int)(p & 1);
+                if (!mbar_wait(&a_full[sa], ause[sa] & 1u, abort)) {
                     *abort = 1;
                     set_status(a.st, KC_ERR_TIMEOUT, 7, 0);
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int t = 0; t < a.ntiles; ++t, ++u) {
                     const int s = (int)(u & 1);
-                    if (!mbar_wait(&t_empty[s], (uses_t[s] & 1u) ^ 1u, abort) ||
-                        !mbar_wait(&b_full[s], uses_b[s] & 1u, abort)) {
+                    if (!mbar_wait(&t_empty[s], (tuse[s] & 1u) ^ 1u, abort) ||
+                        !mbar_wait(&b_full[s], buse[s] & 1u, abort)) {
                         *abort = 1;
                         set_status(a.st, KC_ERR_TIMEOUT, 8, t);
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t abase = smem_u32(sA), bbase = smem_u32(s ? sB1 : sB0);
+                    const uint32_t abase = smem_u32(sAb + sa * a_bytes), bbase = smem_u32(sBb + s * b_bytes);
                     for (int kk = 0; kk < kp / 16; ++kk) {
                         const uint64_t ad = umma_desc(abase + kk * 2 * a_lbo, a_lbo, 128);
                         const uint64_t bd = umma_desc(bbase + kk * 2 * b_lbo, b_lbo, 128);
-                        umma_bf16(tmem + (uint32_t)(s * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        umma_f16(tmem + (uint32_t)(s * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
                     }
                     umma_commit(&b_empty[s]);
                     umma_commit(&t_full[s]);
-                    ++uses_b[s];
-                    ++uses_t[s];
+                    ++buse[s];
+                    ++tuse[s];
                 }
-                umma_commit(&a_empty);
+                umma_commit(&a_empty[sa]);
+                ++ause[sa];
             }
         }
     } else {
         // ------------------------------------------------ epilogue warps 0-7
-        // Warps w and w+4 share TMEM lanes 32(w%4)..: row = point of the tile;
-        // warp w < 4 takes accumulator columns 0..127, warp w+4 columns 128..255.
         const int row = (warp & 3) * 32 + lane;
         const int half = warp >> 2;
+        const float sc = tc_scale(a.absmax);
+        const float sc2 = sc * sc;                  // exact power of two
+        const float isc2 = 1.f / sc2;               // exact power of two
         const float eta = tc_eta(a.d, kp);
         const float g = lp_slack(a.d);
         const float E = __uint_as_float(a.maxes[0]);
         const float cnmax = __uint_as_float(a.maxes[1]);
-        uint32_t uses_t[2] = {0, 0}, pts = 0;
+        uint32_t tuse[2] = {0, 0};
         int64_t u = 0;
-        for (int64_t pt = blockIdx.x; pt < ntile_pts; pt += gridDim.x, ++pts) {
+        for (int64_t pt = blockIdx.x; pt < ntile_pts; pt += gridDim.x) {
             const int64_t pi = pt * TC_M + row;
             const bool valid = pi < a.npts;
-            int64_t gx = 0;
-            if (valid) gx = MODE == 0 ? pi : (int64_t)a.R[pi];
-            if (half == 0) {
-                // A tile: this thread's point, rounded to bf16, into the core layout
-                if (!mbar_wait(&a_empty, (pts & 1u) ^ 1u, abort)) {
-                    set_status(a.st, KC_ERR_TIMEOUT, 9, 0);
-                    *abort = 1;
-                }
-                float xn = 0.f, e2 = 0.f;
-                for (int k = 0; k < kp; ++k) {
-                    float x = 0.f;
-                    if (valid && k < a.d) x = MODE == 0 ? a.pk[pk_index(gx, k, a.d)] : a.src[gx * a.d + k];
-                    const __nv_bfloat16 q = __float2bfloat16_rn(x);
-                    const float xq = __bfloat162float(q);
-                    const float df = fabsf(__fsub_rn(x, xq));
-                    e2 = __fmaf_ru(df, df, e2);
-                    xn = __fmaf_rn(xq, xq, xn);
-                    sA[core_off(TC_M, row, k)] = q;
-                }
-                s_xn[row] = xn;
-                s_ex[row] = __fsqrt_ru(e2);
-                s_gone[row] = (!valid || (MODE == 1 && a.inS[gx])) ? 1 : 0;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&a_full);
-            }
-            asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory");
-            const float xn = s_xn[row];
-            const float sl = __fadd_ru(s_ex[row], E);
+            const float xn = valid ? a.an[pi] : 0.f;
+            const float sl = __fadd_ru(valid ? a.ae[pi] : 0.f, E);
             const float eps = __fmul_ru(eta, __fadd_ru(xn, cnmax));
-            bool removed = s_gone[row] != 0;
-            float lo_lim = 0.f, hi_lim = 0.f;
-            if (MODE == 1) {
-                const float thr = __uint_as_float(*a.thr);
+            int64_t gx = 0;
+            bool removed = !valid;
+            float vlo = INFINITY, vhi = INFINITY;
+            if (MODE == 1 && valid) {
+                gx = (int64_t)a.R[pi];
+                removed = a.inS[gx] != 0;
+                // s~ = xn - v; v >= vlo: s~ small enough that d(x,c) <= thr
+                // surely; v < vhi: d(x,c) > thr surely; between: exact check
+                const float thr = __fmul_rn(__uint_as_float(*a.thr), sc2);   // scaled, exact
                 const float ra = __fsub_rd(__fsqrt_rd(__fdiv_rd(thr, __fadd_ru(1.f, g))), sl);
-                lo_lim = ra > 0.f ? __fsub_rd(__fmul_rd(ra, ra), eps) : -1.f;   // s~ <= lo_lim: within thr
+                const float lo_lim = ra > 0.f ? __fsub_rd(__fmul_rd(ra, ra), eps) : -1.f;
                 const float rb = __fadd_ru(__fsqrt_ru(__fdiv_ru(thr, __fsub_rd(1.f, g))), sl);
-                hi_lim = __fadd_ru(__fmul_ru(rb, rb), eps);                    // s~ > hi_lim: beyond thr
+                const float hi_lim = __fadd_ru(__fmul_ru(rb, rb), eps);
+                vlo = lo_lim >= 0.f ? __fsub_ru(xn, lo_lim) : INFINITY;
+                vhi = __fsub_rd(xn, hi_lim);
             }
-            float m0 = INFINITY, m1 = INFINITY, m2 = INFINITY, m3 = INFINITY;
+            float v0 = -INFINITY, v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
             unsigned long long namb = 0;
+            bool emitted = false, ovf = false;
+            volatile int *s_gone_v = s_gone;
             for (int t = 0; t < a.ntiles; ++t, ++u) {
                 const int s = (int)(u & 1);
-                if (!mbar_wait(&t_full[s], uses_t[s] & 1u, abort)) {
+                if (!mbar_wait(&t_full[s], tuse[s] & 1u, abort)) {
                     set_status(a.st, KC_ERR_TIMEOUT, 10, t);
                     *abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const float *cnt = a.cn + (int64_t)t * TC_N + half * (TC_N / 2);
+                const int cbase = t * TC_N + half * (TC_N / 2);
+                const float4 *cn4 = reinterpret_cast<const float4 *>(a.cn + cbase);
+                if (MODE == 1 && !removed && s_gone_v[row]) removed = true;   // the other half decided
                 for (int c0 = 0; c0 < TC_N / 2; c0 += 32) {
+                    if (MODE == 1 && __all_sync(0xFFFFFFFFu, removed)) break;   // nothing left to read
                     uint32_t r[32];
                     tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(s * TC_N + half * (TC_N / 2) + c0),
                               r);
                     if (MODE == 0) {
 #pragma unroll
                         for (int j = 0; j < 32; j += 4) {
-                            m0 = fminf(m0, __fadd_rn(__fmaf_rn(-2.f, __uint_as_float(r[j]), xn), __ldg(cnt + c0 + j)));
-                            m1 = fminf(m1, __fadd_rn(__fmaf_rn(-2.f, __uint_as_float(r[j + 1]), xn), __ldg(cnt + c0 + j + 1)));
-                            m2 = fminf(m2, __fadd_rn(__fmaf_rn(-2.f, __uint_as_float(r[j + 2]), xn), __ldg(cnt + c0 + j + 2)));
-                            m3 = fminf(m3, __fadd_rn(__fmaf_rn(-2.f, __uint_as_float(r[j + 3]), xn), __ldg(cnt + c0 + j + 3)));
+                            const float4 c = __ldg(cn4 + (c0 + j) / 4);
+                            v0 = fmaxf(v0, __fmaf_rn(2.f, __uint_as_float(r[j]), -c.x));
+                            v1 = fmaxf(v1, __fmaf_rn(2.f, __uint_as_float(r[j + 1]), -c.y));
+                            v2 = fmaxf(v2, __fmaf_rn(2.f, __uint_as_float(r[j + 2]), -c.z));
+                            v3 = fmaxf(v3, __fmaf_rn(2.f, __uint_as_float(r[j + 3]), -c.w));
                         }
                     } else if (!removed) {
+                        // fast pass: the chunk's largest v; only a chunk that
+                        // can hold a pair within the threshold is rescanned
+                        float m = -INFINITY;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float sv = __fadd_rn(__fmaf_rn(-2.f, __uint_as_float(r[j]), xn), __ldg(cnt + c0 + j));
-                            if (sv <= lo_lim) {
-                                removed = true;
-                            } else if (sv <= hi_lim && !removed) {
-                                // undecided: the canonical FP32 distance decides
-                                const int64_t ci = (int64_t)t * TC_N + half * (TC_N / 2) + c0 + j;
-                                if (ci < a.kc) {
-                                    float acc = 0.f;
-                                    for (int k = 0; k < a.d; ++k)
-                                        acc = sq_step(acc, a.src[gx * a.d + k], a.cen[ci * a.d + k]);
-                                    ++namb;
-                                    if (__float_as_uint(acc) <= *a.thr) removed = true;
+                        for (int j = 0; j < 32; j += 4) {
+                            const float4 c = __ldg(cn4 + (c0 + j) / 4);
+                            m = fmaxf(m, fmaxf(fmaxf(__fmaf_rn(2.f, __uint_as_float(r[j]), -c.x),
+                                                     __fmaf_rn(2.f, __uint_as_float(r[j + 1]), -c.y)),
+                                               fmaxf(__fmaf_rn(2.f, __uint_as_float(r[j + 2]), -c.z),
+                                                     __fmaf_rn(2.f, __uint_as_float(r[j + 3]), -c.w))));
+                        }
+                        if (m >= vhi) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const float v = __fmaf_rn(2.f, __uint_as_float(r[j]), -__ldg(a.cn + cbase + c0 + j));
+                                if (v >= vhi && !removed) {
+                                    if (v >= vlo) {
+                                        removed = true;
+                                    } else if (!ovf) {
+                                        // undecided: deferred to the exact pair check
+                                        const int64_t ci = (int64_t)cbase + c0 + j;
+                                        if (ci < a.kc) {
+                                            const unsigned long long slot = atomicAdd(a.npairs, 1ull);
+                                            if (slot < (unsigned long long)a.pcap)
+                                                a.pairs[slot] = make_uint2((uint32_t)pi, (uint32_t)ci);
+                                            else
+                                                ovf = true;
+                                            emitted = true;
+                                            ++namb;
+                                        }
+                                    }
                                 }
                             }
+                            if (removed) s_gone_v[row] = 1;
                         }
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(&t_empty[s]);
-                ++uses_t[s];
+                ++tuse[s];
             }
             // combine the two column halves of every row
-            const float mmin = fminf(fminf(m0, m1), fminf(m2, m3));
+            const float vmax = fmaxf(fmaxf(v0, v1), fmaxf(v2, v3));
             if (half == 1) {
-                s_part[row] = mmin;
-                s_gone2[row] = removed ? 1 : 0;
-            }
-            asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory");
-            if (half == 0) {
-                if (MODE == 0) {
-                    const float mm = fminf(mmin, s_part[row]);
-                    if (valid) {
-                        // bounds on the canonical FP32 minimum over all centers
-                        const float lo_r = __fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(mm, eps), 0.f)), sl);
-                        const float lo = lo_r > 0.f ? __fmul_rd(__fmul_rd(lo_r, lo_r), __fsub_rd(1.f, g)) : 0.f;
-                        const float hi_r = __fadd_ru(__fsqrt_ru(__fadd_ru(mm, eps)), sl);
-                        const float hi = __fmul_ru(__fmul_ru(hi_r, hi_r), __fadd_ru(1.f, g));
-                        a.mlo[gx] = lo;
-                        a.mhi[gx] = hi;
-                        atomicMax(a.mlo_max, __float_as_uint(lo));
-                    }
-                } else {
-                    const bool gone = removed || s_gone2[row] != 0;
-                    if (valid && !gone) a.Rn[atomicAdd(a.rnn, 1ull)] = (uint32_t)gx;
+                s_part[row] = vmax;
+                if (MODE == 1) {
+                    if (removed) s_gone[row] = 1;
+                    s_pend[row] = (emitted ? 1 : 0) | (ovf ? 2 : 0);
                 }
             }
-            if (MODE == 1 && namb) atomicAdd(a.amb, namb);
+            asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory");
+            if (half == 0 && valid) {
+                if (MODE == 0) {
+                    // min over centers of s~ = xn - max v, then bounds on the
+                    // canonical FP32 minimum (scaled units), then unscaled
+                    const float vm = fmaxf(vmax, s_part[row]);
+                    const float mm_hi = __fsub_ru(xn, vm), mm_lo = __fsub_rd(xn, vm);
+                    const float lo_r = __fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(mm_lo, eps), 0.f)), sl);
+                    const float lo = lo_r > 0.f ? __fmul_rd(__fmul_rd(lo_r, lo_r), __fsub_rd(1.f, g)) : 0.f;
+                    const float hi_r = __fadd_ru(__fsqrt_ru(__fadd_ru(fmaxf(mm_hi, 0.f), eps)), sl);
+                    const float hi = __fmul_ru(__fmul_ru(hi_r, hi_r), __fadd_ru(1.f, g));
+                    const float lo_u = __fmul_rd(lo, isc2), hi_u = __fmul_ru(hi, isc2);
+                    a.mlo[pi] = lo_u;
+                    a.mhi[pi] = hi_u;
+                    atomicMax(a.mlo_max, __float_as_uint(lo_u));
+                } else if (!(removed || s_gone[row] != 0)) {
+                    const int pf = s_pend[row] | (emitted ? 1 : 0) | (ovf ? 2 : 0);
+                    if (pf) {
+                        // decided by the pair check (and a full scan on overflow)
+                        a.pflag[pi] = (uint8_t)pf;
+                        a.pend[atomicAdd(a.npend, 1ull)] = (uint32_t)pi;
+                    } else {
+                        a.Rn[atomicAdd(a.rnn, 1ull)] = (uint32_t)gx;
+                    }
+                }
+            }
+            if (MODE == 1 && half == 0) {
+                s_gone[row] = 0;
+                s_pend[row] = 0;
+            }
+            if (MODE == 1 && namb) atomicAdd(&g_tc_counters[0], namb);
+            if (MODE == 1 && half == 0 && valid) atomicAdd(&g_tc_counters[1], 1ull);
             asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory");   // s_* reused by the next tile
         }
     }
@@ -449,6 +533,67 @@ __global__ void tc_exact_kernel(const float *__restrict__ pk, int64_t n, int d, 
     if (lane == 0 && best) atomicMax(key32, (unsigned long long)best);
 }
 
+// Canonical FP32 squared distance of rows x and c (d coordinates), with
+// 16-byte loads when both rows allow them.
+__device__ __forceinline__ float row_dist(const float *__restrict__ x, const float *__restrict__ c, int d, bool v4) {
+    float acc = 0.f;
+    if (v4) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(x), *c4 = reinterpret_cast<const float4 *>(c);
+        for (int k = 0; k < d / 4; ++k) {
+            const float4 xa = __ldg(x4 + k), ca = __ldg(c4 + k);
+            acc = sq_step(acc, xa.x, ca.x);
+            acc = sq_step(acc, xa.y, ca.y);
+            acc = sq_step(acc, xa.z, ca.z);
+            acc = sq_step(acc, xa.w, ca.w);
+        }
+    } else {
+        for (int k = 0; k < d; ++k) acc = sq_step(acc, __ldg(x + k), __ldg(c + k));
+    }
+    return acc;
+}
+
+// Exact check of the deferred pairs: hit[row] once a pair is within the
+// threshold (canonical FP32 distance, the same test as the CUDA-core prune).
+__global__ void tc_pair_kernel(const float *__restrict__ src, int d, bool v4, const uint32_t *__restrict__ R,
+                               const float *__restrict__ cen, const uint2 *__restrict__ pairs,
+                               const unsigned long long *npairs, int64_t pcap, const uint32_t *thr, uint8_t *hit) {
+    const int64_t np = (int64_t)min(*npairs, (unsigned long long)pcap);
+    const uint32_t T = *thr;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 p = pairs[i];
+        if (hit[p.x]) continue;
+        const float acc = row_dist(src + (int64_t)R[p.x] * d, cen + (int64_t)p.y * d, d, v4);
+        if (__float_as_uint(acc) <= T) hit[p.x] = 1;
+    }
+}
+
+// Pending rows: removed on a hit; a row whose pairs overflowed the buffer is
+// scanned against every center (one warp, lanes over centers); the rest are
+// kept.
+__global__ void tc_resolve_kernel(const float *__restrict__ src, int d, bool v4, const uint32_t *__restrict__ R,
+                                  const float *__restrict__ cen, int64_t sn, const uint32_t *__restrict__ pend,
+                                  const unsigned long long *npend, const uint8_t *__restrict__ flag,
+                                  const uint8_t *__restrict__ hit, const uint32_t *thr, uint32_t *Rn,
+                                  unsigned long long *rnn) {
+    const int64_t np = (int64_t)*npend;
+    const uint32_t T = *thr;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); j < np; j += warps) {
+        const uint32_t pi = pend[j];
+        const int64_t gx = (int64_t)R[pi];
+        bool rm = hit[pi] != 0;
+        if (!rm && (flag[pi] & 2)) {
+            for (int64_t cb = 0; cb < sn && !rm; cb += 32) {
+                const int64_t ci = cb + lane;
+                const bool h = ci < sn && __float_as_uint(row_dist(src + gx * d, cen + ci * d, d, v4)) <= T;
+                rm = __any_sync(0xFFFFFFFFu, h);
+            }
+        }
+        if (!rm && lane == 0) Rn[atomicAdd(rnn, 1ull)] = (uint32_t)gx;
+    }
+}
+
 int sms() {
     int dev = 0, s = 0;
     cudaGetDevice(&dev);
@@ -456,102 +601,153 @@ int sms() {
     return s;
 }
 
-// Dynamic shared memory: the A tile and two center tiles, and at least
+int kpad(int d) { return (d + 15) / 16 * 16; }
+
+// Dynamic shared memory: two point tiles and two center tiles, and at least
 // 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM.
 size_t tc_smem(int kp) {
-    const size_t need = (size_t)TC_M * kp * 2 + (size_t)2 * TC_N * kp * 2;
+    const size_t need = (size_t)2 * TC_M * kp * 2 + (size_t)2 * TC_N * kp * 2;
     return need > 120 * 1024 ? need : 120 * 1024;
+}
+
+template <int R>
+cudaError_t rows(const float *pk, const float *rm, const uint32_t *idx, const int32_t *cnt_dev, int64_t cnt, int d,
+                 const unsigned *absmax, void *tiles, float *norm, float *err, unsigned *maxes, cudaStream_t s) {
+    const int64_t nt = (cnt + R - 1) / R;
+    if (nt == 0) return cudaSuccess;
+    const int64_t rowsn = nt * R;
+    const int grid = (int)std::min<int64_t>((rowsn + 255) / 256, (int64_t)sms() * 8);
+    tc_rows_kernel<R><<<grid, 256, 0, s>>>(pk, rm, idx, cnt_dev, cnt, d, kpad(d), nt, absmax, (__half *)tiles, norm, err,
+                                           maxes);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_supported(int d) { return d >= 1 && d <= TC_KMAX; }
 
-size_t tc_center_bytes(int kc, int d) {
-    const int kp = (d + 15) / 16 * 16;
-    const int ntiles = (kc + TC_N - 1) / TC_N;
-    return (size_t)ntiles * TC_N * kp * 2;
+cudaError_t read_tc_counters(unsigned long long out[2], bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_tc_counters, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess && reset) {
+        const unsigned long long z[2] = {0, 0};
+        e = cudaMemcpyToSymbol(g_tc_counters, z, sizeof z);
+    }
+    return e;
 }
 
-int tc_center_tiles(int kc) { return (kc + TC_N - 1) / TC_N; }
+int tc_center_tiles(int64_t kc) { return (int)((kc + TC_N - 1) / TC_N); }
+size_t tc_center_bytes(int64_t kc, int d) { return (size_t)tc_center_tiles(kc) * TC_N * kpad(d) * 2; }
+size_t tc_point_bytes(int64_t n, int d) { return (size_t)((n + TC_M - 1) / TC_M) * TC_M * kpad(d) * 2; }
+int64_t tc_point_rows(int64_t n) { return (n + TC_M - 1) / TC_M * TC_M; }
 
-cudaError_t launch_tc_prep(const float *cen, const int32_t *kc_dev, int kc, int d, void *bt, float *cn, unsigned *maxes,
-                           cudaStream_t s) {
-    const int kp = (d + 15) / 16 * 16;
-    const int ntiles = tc_center_tiles(kc);
-    cudaMemsetAsync(maxes, 0, 2 * sizeof(unsigned), s);
-    const int64_t rows = (int64_t)ntiles * TC_N;
-    const int grid = (int)std::min<int64_t>((rows + 255) / 256, (int64_t)sms() * 8);
-    tc_prep_kernel<<<grid, 256, 0, s>>>(cen, kc_dev, kc, d, kp, ntiles, (__nv_bfloat16 *)bt, cn, maxes);
+cudaError_t launch_tc_absmax(const float *pk, int64_t n, int d, unsigned *absmax, cudaStream_t s) {
+    cudaMemsetAsync(absmax, 0, sizeof(unsigned), s);
+    const int64_t total = nblocks(n) * (int64_t)d * BLK;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sms() * 8);
+    tc_absmax_kernel<<<grid, 256, 0, s>>>(pk, n, d, absmax);
     note_launches(1);
     return cudaGetLastError();
 }
 
-// Radius bounds for all n points of a packed array; then exact canonical
-// minima for the points that can reach the maximum.
+cudaError_t launch_tc_centers(const float *cen_rows, const int32_t *kc_dev, int64_t kc, int d, const unsigned *absmax,
+                              void *bt, float *cn, float *ce, unsigned *maxes, cudaStream_t s) {
+    cudaMemsetAsync(maxes, 0, 2 * sizeof(unsigned), s);
+    return rows<TC_N>(nullptr, cen_rows, nullptr, kc_dev, kc, d, absmax, bt, cn, ce, maxes, s);
+}
+
+cudaError_t launch_tc_points(const float *pk, const float *rm, const uint32_t *idx, int64_t n, int d,
+                             const unsigned *absmax, void *at, float *an, float *ae, cudaStream_t s) {
+    return rows<TC_M>(pk, rm, idx, nullptr, n, d, absmax, at, an, ae, nullptr, s);
+}
+
 cudaError_t launch_tc_radius(const float *pk, int64_t n, int d, const float *cen, const int32_t *kc_dev, int kc,
-                             const void *bt, const float *cn, const unsigned *maxes, float *mlo, float *mhi,
-                             unsigned *mlo_max, uint32_t *mind, unsigned long long *key32, DevStatus *st,
+                             const TcBufs &B, uint32_t *mind, unsigned long long *key32, DevStatus *st,
                              cudaStream_t s) {
+    cudaError_t e;
+    if ((e = launch_tc_absmax(pk, n, d, B.absmax, s)) != cudaSuccess) return e;
+    if ((e = launch_tc_points(pk, nullptr, nullptr, n, d, B.absmax, B.at, B.an, B.ae, s)) != cudaSuccess) return e;
+    if ((e = launch_tc_centers(cen, kc_dev, kc, d, B.absmax, B.bt, B.cn, B.ce, B.maxes, s)) != cudaSuccess) return e;
     TcArgs a{};
-    a.mode = 0;
     a.d = d;
-    a.kp = (d + 15) / 16 * 16;
+    a.kp = kpad(d);
     a.kc = kc;
     a.ntiles = tc_center_tiles(kc);
     a.npts = n;
-    a.pk = pk;
-    a.bt = (const __nv_bfloat16 *)bt;
-    a.cn = cn;
-    a.maxes = maxes;
-    a.cen = cen;
-    a.mlo = mlo;
-    a.mhi = mhi;
-    a.mlo_max = mlo_max;
+    a.at = (const __half *)B.at;
+    a.an = B.an;
+    a.ae = B.ae;
+    a.bt = (const __half *)B.bt;
+    a.cn = B.cn;
+    a.maxes = B.maxes;
+    a.absmax = B.absmax;
+    a.mlo = B.mlo;
+    a.mhi = B.mhi;
+    a.mlo_max = B.mlomax;
     a.st = st;
     const size_t smem = tc_smem(a.kp);
-    cudaError_t e = cudaFuncSetAttribute(tc_dmin_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    cudaMemsetAsync(mlo_max, 0, sizeof(unsigned), s);
+    if ((e = cudaFuncSetAttribute(tc_dmin_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    cudaMemsetAsync(B.mlomax, 0, sizeof(unsigned), s);
     const int64_t tiles = (n + TC_M - 1) / TC_M;
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms());
     tc_dmin_kernel<0><<<grid, TC_THREADS, smem, s>>>(a);
     const int g2 = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms() * 8);
-    tc_exact_kernel<<<g2, 256, 0, s>>>(pk, n, d, cen, kc_dev, kc, mhi, mlo_max, mind, key32, st);
+    tc_exact_kernel<<<g2, 256, 0, s>>>(pk, n, d, cen, kc_dev, kc, B.mhi, B.mlomax, mind, key32, st);
     note_launches(2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_prune(const float *src, int d, const uint32_t *R, int64_t rn, const uint8_t *inS, const float *Scen,
-                            int64_t sn, const void *bt, const float *cn, const unsigned *maxes, const uint32_t *thr,
-                            uint32_t *Rn, unsigned long long *rnn, unsigned long long *amb, DevStatus *st,
-                            cudaStream_t s) {
+                            int64_t sn, const TcBufs &B, const PruneBufs &P, const uint32_t *thr, uint32_t *Rn,
+                            unsigned long long *rnn, DevStatus *st, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = launch_tc_points(nullptr, src, R, rn, d, B.absmax, B.at, B.an, B.ae, s)) != cudaSuccess) return e;
+    if ((e = launch_tc_centers(Scen, nullptr, sn, d, B.absmax, B.bt, B.cn, B.ce, B.maxes, s)) != cudaSuccess) return e;
+    cudaMemsetAsync(P.npairs, 0, sizeof(unsigned long long), s);
+    cudaMemsetAsync(P.npend, 0, sizeof(unsigned long long), s);
+    cudaMemsetAsync(P.hit, 0, (size_t)rn, s);
     TcArgs a{};
-    a.mode = 1;
     a.d = d;
-    a.kp = (d + 15) / 16 * 16;
+    a.kp = kpad(d);
     a.kc = (int)sn;
-    a.ntiles = tc_center_tiles((int)sn);
+    a.ntiles = tc_center_tiles(sn);
     a.npts = rn;
+    a.at = (const __half *)B.at;
+    a.an = B.an;
+    a.ae = B.ae;
+    a.bt = (const __half *)B.bt;
+    a.cn = B.cn;
+    a.maxes = B.maxes;
+    a.absmax = B.absmax;
     a.src = src;
     a.R = R;
     a.inS = inS;
-    a.bt = (const __nv_bfloat16 *)bt;
-    a.cn = cn;
-    a.maxes = maxes;
     a.cen = Scen;
     a.thr = thr;
     a.Rn = Rn;
     a.rnn = rnn;
-    a.amb = amb;
+    a.pairs = P.pairs;
+    a.pcap = P.pcap;
+    a.npairs = P.npairs;
+    a.pflag = P.flag;
+    a.pend = P.pend;
+    a.npend = P.npend;
     a.st = st;
     const size_t smem = tc_smem(a.kp);
-    cudaError_t e = cudaFuncSetAttribute(tc_dmin_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(tc_dmin_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
     const int64_t tiles = (rn + TC_M - 1) / TC_M;
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms());
-    if (grid > 0) tc_dmin_kernel<1><<<grid, TC_THREADS, smem, s>>>(a);
-    note_launches(1);
+    if (grid == 0) return cudaGetLastError();
+    tc_dmin_kernel<1><<<grid, TC_THREADS, smem, s>>>(a);
+    const bool v4 = (d & 3) == 0 && ((uintptr_t)src & 15) == 0 && ((uintptr_t)Scen & 15) == 0;
+    const int g2 = sms() * 8;
+    tc_pair_kernel<<<g2, 256, 0, s>>>(src, d, v4, R, Scen, P.pairs, P.npairs, P.pcap, thr, P.hit);
+    tc_resolve_kernel<<<g2, 256, 0, s>>>(src, d, v4, R, Scen, sn, P.pend, P.npend, P.flag, P.hit, thr, Rn, rnn);
+    note_launches(3);
     return cudaGetLastError();
 }
 

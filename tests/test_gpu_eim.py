@@ -70,3 +70,25 @@ def test_eim_eps_variants(kc):
 def test_eim_bad_eps(kc):
     with pytest.raises(kc.KCError):
         kc.kc_eim(_dev(I.gauss_mixture(100, 2, 1, 2, 1.0, 0, 1)), 2, eps=1.5)
+
+
+@pytest.mark.parametrize("cap", [None, "1"])
+def test_eim_tc_prune_deferred_pairs(kc, monkeypatch, cap):
+    # Integer-valued FP32 coordinates on a small grid: many pair distances
+    # equal the threshold exactly, so the tensor-core bounds leave pairs
+    # undecided and the deferred exact check decides them.  cap=1 overflows
+    # the pair buffer at once, so the full-scan route decides those rows.
+    pts = I.int_points(40000, 8, 19, 0, 20).astype(np.float32)
+    if cap is not None:
+        monkeypatch.setenv("KC_PRUNE_PAIR_CAP", cap)
+    kc.kc_counters()
+    check_eim(kc, pts, 4, expect_loop=True)
+    assert kc.kc_counters()[2] > 0
+
+
+def test_eim_tc_prune_matches_cuda_cores(kc, monkeypatch):
+    pts = I.gauss_mixture(60000, 32, 75, 100, 0.5, -10, 10)
+    a = kc.kc_eim(_dev(pts), 8, eps=0.1, phi=6.0, seed=41)
+    monkeypatch.setenv("KC_PRUNE_TC", "0")
+    b = kc.kc_eim(_dev(pts), 8, eps=0.1, phi=6.0, seed=41)
+    assert a.centers.cpu().tolist() == b.centers.cpu().tolist() and a.radius == b.radius
