@@ -79,10 +79,11 @@ typedef enum { KC_SWEEP_F32 = 0, KC_SWEEP_BF16 = 1, KC_SWEEP_FP8 = 2 } kc_sweep;
 
 /* Flags for kc_opts.flags. */
 #define KC_ASYNC 1u        /* enqueue only; see kc_sync() */
+#define KC_AUTOTUNE 2u     /* batched form only: time launch shapes, keep the fastest */
 
 typedef struct {
     int32_t dtype;          /* kc_dtype of the points */
-    uint32_t flags;         /* KC_ASYNC or 0 */
+    uint32_t flags;         /* KC_ASYNC, KC_AUTOTUNE (batched form) or 0 */
     int32_t sweep;          /* kc_sweep (float points only) */
     int32_t reserved;       /* must be 0 */
     uint64_t seed;          /* EIM sampling seed */
@@ -175,12 +176,57 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
  * host or device), selects up to k[i] centers from its point 0, and writes
  * centers[i][0 .. k_out[i]) (indices local to the instance) and radii[i].
  * n, d, k, pts and centers are host arrays of `count` entries; k_out and radii
- * are [count] arrays in host or device memory.  Instances are processed
- * longest-first (n k d).  Errors: as kc_gonzalez, per instance.
+ * are [count] arrays in host or device memory.
+ * Launch shape: instances are ordered longest-first by modelled work
+ * n k (d b + 8) bytes (b = 4 for FP32, 2 for the bf16 sweep).  An instance
+ * whose work exceeds theta times the fair share of one resident CTA is solved
+ * by a group of CTAs sized to its work (cooperative launch); the others go
+ * through a queue, one CTA each, longest first.  theta is 1 by default; with
+ * KC_AUTOTUNE in opts->flags the first call for a batch shape (count, dtype,
+ * sweep and every (n, d, k)) solves the batch once per candidate theta
+ * (plain queue, 4, 2, 1, 0.5), keeps the fastest for later calls in the
+ * process, and returns the result of a final solve with it.  Every launch
+ * shape selects the same centers.  KC_AUTOTUNE does not combine with
+ * KC_ASYNC.  Errors: as kc_gonzalez, per instance; KC_ERR_ARG for the fp8
+ * sweep (it needs per-instance column scales).
  */
 kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d,
                             const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
                             const kc_opts *opts);
+
+/*
+ * Batch plans -- the batched form prepared once and replayed as a CUDA graph.
+ * The paper has no counterpart (it simulates its parallel machines one after
+ * another, Section 7.1); a plan is for callers that solve the same batch
+ * shape repeatedly on changing point values, e.g. inside a serving loop.
+ *
+ * kc_batch_plan_create takes the arguments of kc_gonzalez_batch, all of them
+ * device memory of the current device (KC_ERR_ARG otherwise), checks them,
+ * picks the launch shape (KC_AUTOTUNE: builds and times a plan per candidate
+ * theta, three replays each, and keeps the fastest), allocates the plan's
+ * own scratch (freed by kc_batch_plan_destroy), uploads the instance
+ * descriptors and captures pack + GON + radius into a CUDA graph.  The
+ * pointers are bound at creation: each run reads the current contents of
+ * pts[i] and writes centers[i], k_out and radii.
+ * kc_batch_plan_run enqueues one replay on `stream` (a cudaStream_t; the
+ * plan's device must be current) and returns at once.  Runs of one plan
+ * must not overlap (they share scratch): order them on one stream.
+ * kc_batch_plan_wait waits for the last run and returns its device status
+ * (KC_ERR_RANGE, KC_ERR_NONFINITE, KC_ERR_TIMEOUT as kc_gonzalez).
+ * kc_batch_plan_info reports the chosen theta, the number of group-solved
+ * instances, their CTAs, and the grid size.
+ * kc_batch_plan_destroy waits for the last run and frees the plan (NULL is
+ * accepted).
+ */
+typedef struct kc_batch_plan kc_batch_plan;
+kc_status kc_batch_plan_create(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d,
+                               const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
+                               const kc_opts *opts, kc_batch_plan **plan);
+kc_status kc_batch_plan_run(kc_batch_plan *plan, void *stream);
+kc_status kc_batch_plan_wait(kc_batch_plan *plan);
+kc_status kc_batch_plan_info(const kc_batch_plan *plan, double *theta, int32_t *nheavy, int32_t *gheavy,
+                             int32_t *grid);
+kc_status kc_batch_plan_destroy(kc_batch_plan *plan);
 
 /*
  * kc_gonzalez_noalloc -- the same Gonzalez selection as kc_gonzalez, for

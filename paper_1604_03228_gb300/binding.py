@@ -20,6 +20,7 @@ from . import build as _build
 KC_OK, KC_ERR_ARG, KC_ERR_CUDA, KC_ERR_OOM, KC_ERR_TIMEOUT, KC_ERR_RANGE, KC_ERR_NONFINITE = range(7)
 KC_F32, KC_I32 = 0, 1
 KC_ASYNC = 1
+KC_AUTOTUNE = 2
 STATUS_NAMES = {0: "KC_OK", 1: "KC_ERR_ARG", 2: "KC_ERR_CUDA", 3: "KC_ERR_OOM", 4: "KC_ERR_TIMEOUT",
                 5: "KC_ERR_RANGE", 6: "KC_ERR_NONFINITE"}
 
@@ -66,6 +67,16 @@ def load(path: str | None = None):
     L.kc_eim.argtypes = [vp, i64, i32, i32, dbl, vp, vp, vp, popts]
     L.kc_gonzalez_batch.restype = ct.c_int
     L.kc_gonzalez_batch.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, popts]
+    L.kc_batch_plan_create.restype = ct.c_int
+    L.kc_batch_plan_create.argtypes = [i32, vp, vp, vp, vp, vp, vp, vp, popts, ct.POINTER(vp)]
+    L.kc_batch_plan_run.restype = ct.c_int
+    L.kc_batch_plan_run.argtypes = [vp, vp]
+    L.kc_batch_plan_wait.restype = ct.c_int
+    L.kc_batch_plan_wait.argtypes = [vp]
+    L.kc_batch_plan_info.restype = ct.c_int
+    L.kc_batch_plan_info.argtypes = [vp, vp, vp, vp, vp]
+    L.kc_batch_plan_destroy.restype = ct.c_int
+    L.kc_batch_plan_destroy.argtypes = [vp]
     L.kc_sync.restype = ct.c_int
     L.kc_sync.argtypes = [vp]
     L.kc_last_error.restype = ct.c_char_p
@@ -359,6 +370,93 @@ def kc_gonzalez_batch(points_list, ks, *, stream=None, flags: int = 0, timeout_m
     ko = k_out.cpu().numpy() if _is_torch(k_out) else k_out
     rr = radii.cpu().numpy() if _is_torch(radii) else radii
     return [GonResult(outs[i][:int(ko[i])], int(ko[i]), float(rr[i])) for i in range(count)]
+
+
+class BatchPlan:
+    """A kc_batch_plan handle with the device outputs it is bound to:
+    centers (one int64 tensor per instance), k_out and radii."""
+
+    def __init__(self, handle, points, centers, k_out, radii):
+        self.handle = handle
+        self.points = points      # keeps the bound inputs alive
+        self.centers = centers
+        self.k_out = k_out
+        self.radii = radii
+
+    def results(self):
+        ko = self.k_out.cpu().numpy()
+        rr = self.radii.cpu().numpy()
+        return [GonResult(self.centers[i][:int(ko[i])], int(ko[i]), float(rr[i])) for i in range(len(self.centers))]
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                load().kc_batch_plan_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def kc_batch_plan_create(points_list, ks, *, sweep=None, flags: int = 0, timeout_ms: int = 0) -> BatchPlan:
+    """Prepare the batched GON of device tensors `points_list` as a CUDA
+    graph (C ABI kc_batch_plan_create); outputs are allocated on the device
+    and bound to the plan."""
+    L = load()
+    torch = _torch()
+    count = len(points_list)
+    if count != len(ks):
+        raise ValueError("one k per instance")
+    ps = [_points(x) for x in points_list]
+    codes = {c for (_, _, _, c) in ps}
+    if len(codes) != 1:
+        raise TypeError("all instances must share one dtype")
+    ref = ps[0][0]
+    if not _is_torch(ref) or not ref.is_cuda:
+        raise TypeError("a batch plan takes CUDA tensors")
+    ptrs = (ct.c_void_p * count)(*[_ptr(p) for (p, _, _, _) in ps])
+    ns = np.array([n for (_, n, _, _) in ps], dtype=np.int64)
+    ds = np.array([d for (_, _, d, _) in ps], dtype=np.int32)
+    kk = np.array([int(k) for k in ks], dtype=np.int32)
+    outs = [torch.empty(max(1, min(int(k), n)), dtype=torch.int64, device=ref.device)
+            for (_, n, _, _), k in zip(ps, ks)]
+    cptrs = (ct.c_void_p * count)(*[_ptr(c) for c in outs])
+    k_out = torch.empty(count, dtype=torch.int32, device=ref.device)
+    radii = torch.empty(count, dtype=torch.float64, device=ref.device)
+    o = _opts(codes.pop(), ref, None, flags, timeout_ms, sweep=sweep)
+    h = ct.c_void_p()
+    st = L.kc_batch_plan_create(count, ptrs, ns.ctypes.data, ds.ctypes.data, kk.ctypes.data, cptrs,
+                                _ptr(k_out), _ptr(radii), ct.byref(o), ct.byref(h))
+    _check(L, st)
+    return BatchPlan(h.value, [p for (p, _, _, _) in ps], outs, k_out, radii)
+
+
+def kc_batch_plan_run(plan: BatchPlan, stream=None) -> None:
+    """Enqueue one replay of the plan's graph on `stream` (default: torch's current stream)."""
+    L = load()
+    _check(L, L.kc_batch_plan_run(plan.handle, _stream_handle(plan.k_out, stream)))
+
+
+def kc_batch_plan_wait(plan: BatchPlan):
+    """Wait for the plan's last run; return its results ([GonResult])."""
+    L = load()
+    _check(L, L.kc_batch_plan_wait(plan.handle))
+    return plan.results()
+
+
+def kc_batch_plan_info(plan: BatchPlan):
+    """(theta, group-solved instances, their CTAs, grid size)."""
+    L = load()
+    th = ct.c_double()
+    nh, gh, gr = ct.c_int32(), ct.c_int32(), ct.c_int32()
+    _check(L, L.kc_batch_plan_info(plan.handle, ct.byref(th), ct.byref(nh), ct.byref(gh), ct.byref(gr)))
+    return th.value, nh.value, gh.value, gr.value
+
+
+def kc_batch_plan_destroy(plan: BatchPlan) -> None:
+    if plan.handle:
+        L = load()
+        h, plan.handle = plan.handle, None
+        _check(L, L.kc_batch_plan_destroy(h))
 
 
 def kc_sync(stream=None) -> int:

@@ -57,7 +57,7 @@ struct TraceStep {
     TraceRec r{};
     cudaStream_t s;
     int k0 = 0;
-    TraceStep(const char *name, cudaStream_t s_) : on(g_trace_on.load() != 0), s(s_) {
+    TraceStep(const char *name, cudaStream_t s_) : on(name != nullptr && g_trace_on.load() != 0), s(s_) {
         if (!on) return;
         strncpy(r.name, name, sizeof r.name - 1);
         r.a = ev_get();
@@ -268,10 +268,10 @@ struct CallCtx {
     Arena *arena;
 };
 
-kc_status begin(const kc_opts *opts, CallCtx &c) {
+kc_status begin(const kc_opts *opts, CallCtx &c, uint32_t allowed = KC_ASYNC) {
     c.o = opts ? *opts : default_opts();
     if (c.o.dtype != KC_F32 && c.o.dtype != KC_I32) return fail(KC_ERR_ARG, "dtype must be KC_F32 or KC_I32");
-    if (c.o.flags & ~KC_ASYNC) return fail(KC_ERR_ARG, "unknown flags 0x%x", c.o.flags);
+    if (c.o.flags & ~allowed) return fail(KC_ERR_ARG, "flags 0x%x not accepted by this call", c.o.flags);
     if (c.o.sweep < KC_SWEEP_F32 || c.o.sweep > KC_SWEEP_FP8) return fail(KC_ERR_ARG, "unknown sweep %d", c.o.sweep);
     c.s = (cudaStream_t)c.o.stream;
     c.async = (c.o.flags & KC_ASYNC) != 0;
@@ -1238,49 +1238,125 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
     return finish(c.arena, c.s);
 }
 
-kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d,
-                            const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
-                            const kc_opts *opts) {
-    g_err.clear();
-    if (count < 1) return fail(KC_ERR_ARG, "count=%d must be >= 1", count);
-    if (!pts || !n || !d || !k || !centers || !k_out || !radii) return fail(KC_ERR_ARG, "null pointer argument");
-    for (int i = 0; i < count; ++i) {
-        if (!pts[i] || !centers[i]) return fail(KC_ERR_ARG, "instance %d: null pointer", i);
-        if (n[i] < 1 || n[i] > (int64_t)N_MAX) return fail(KC_ERR_ARG, "instance %d: n outside [1, 2^32-2]", i);
-        if (d[i] < 1) return fail(KC_ERR_ARG, "instance %d: d must be >= 1", i);
-        if (k[i] < 1) return fail(KC_ERR_ARG, "instance %d: k must be >= 1", i);
-    }
-    CallCtx c;
-    kc_status r = begin(opts, c);
-    if (r != KC_OK) return r;
-    const bool dev_kout = is_device_ptr(k_out, c.dev);
-    const bool dev_rad = is_device_ptr(radii, c.dev);
-    std::vector<char> dev_pts((size_t)count), dev_cen((size_t)count);
-    bool all_dev = dev_kout && dev_rad;
-    int dmax = 0, dcommon = d[0];
-    for (int i = 0; i < count; ++i) {
-        dev_pts[i] = is_device_ptr(pts[i], c.dev);
-        dev_cen[i] = is_device_ptr(centers[i], c.dev);
-        all_dev = all_dev && dev_pts[i] && dev_cen[i];
-        dmax = std::max(dmax, (int)d[i]);
-        if (d[i] != dcommon) dcommon = 0;
-    }
-    if (c.async && !all_dev) return fail(KC_ERR_ARG, "KC_ASYNC needs device pointers for all arguments");
-    const int dc = (dcommon == 3 || dcommon == 8 || dcommon == 32) && c.o.dtype == KC_F32 ? dcommon : 0;
-    const int lp = lp_of(c.o);
-    if (lp == KC_SWEEP_FP8)
-        return fail(KC_ERR_ARG, "the batched form takes KC_SWEEP_F32 or KC_SWEEP_BF16 (fp8 needs per-instance scales)");
+}  // extern "C"
 
-    // Longest processing time first: instances ordered by n * k * d.
-    std::vector<int> order((size_t)count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        const double wa = (double)n[a] * std::min<int64_t>(k[a], n[a]) * d[a];
-        const double wb = (double)n[b] * std::min<int64_t>(k[b], n[b]) * d[b];
-        return wa > wb;
-    });
+// ------------------------------------------------------------ batched GON
+//
+// Launch policy.  Instances are ordered longest-first by modelled work
+// w = n k (d b + 8) bytes (b bytes per streamed coordinate, the running
+// minimum read and written).  With S resident queue-mode CTAs and the fair
+// share W / S of the total work W, an instance with w > theta W / S is heavy:
+// it is solved by a CTA group of G = ceil(w / (W / S)) CTAs (at most one per
+// warp's worth of 128-point blocks) at the front of a cooperative grid, while
+// the groups take at most half of the CTAs.  The other instances go through
+// the queue longest-first, and group CTAs join the queue when their instance
+// is done.  theta = +inf is the plain queue.  KC_AUTOTUNE times every theta
+// of kThetas on the batch itself and keeps the fastest per batch shape.
+namespace {
 
-    const size_t esz = 4;
+constexpr double kThetaQueue = 1e300;
+constexpr double kThetas[] = {kThetaQueue, 4.0, 2.0, 1.0, 0.5};
+constexpr double kThetaDefault = 1.0;
+
+struct BatchShape {
+    int count = 0, dtype = 0, lp = 0, dc = 0, dmax = 0;
+    std::vector<int> order;   // descriptor position -> instance
+    std::vector<int> G;       // CTAs per descriptor position (1: queue)
+    int nheavy = 0, gheavy = 0, grid = 0;
+    double theta = kThetaQueue;
+};
+
+void batch_policy(BatchShape &b, const int64_t *n, const int32_t *d, const int32_t *k, double theta) {
+    const int count = b.count;
+    const double bpc = b.lp == KC_SWEEP_BF16 ? 2.0 : 4.0;
+    std::vector<double> w((size_t)count);
+    double W = 0;
+    for (int i = 0; i < count; ++i) {
+        w[i] = (double)n[i] * (double)std::min<int64_t>(k[i], n[i]) * (d[i] * bpc + 8.0);
+        W += w[i];
+    }
+    std::vector<int> lpt((size_t)count);
+    for (int i = 0; i < count; ++i) lpt[i] = i;
+    std::stable_sort(lpt.begin(), lpt.end(), [&](int a, int c) { return w[a] > w[c]; });
+    const int slots = gon_queue_grid(b.dtype, b.dc, b.lp);
+    const double share = W / std::max(1, slots);
+    b.order.clear();
+    b.G.clear();
+    b.nheavy = b.gheavy = 0;
+    b.theta = theta;
+    std::vector<char> heavy((size_t)count, 0);
+    for (int q = 0; q < count && theta < kThetaQueue; ++q) {
+        const int i = lpt[q];
+        if (!(w[i] > theta * share)) break;
+        const int64_t gmax = std::max<int64_t>(1, nblocks(n[i]) / gon_queue_warps());
+        const int g = (int)std::min<double>(std::ceil(w[i] / share), (double)gmax);
+        if (g < 2) continue;
+        if (b.gheavy + g > slots / 2) break;
+        heavy[i] = 1;
+        b.order.push_back(i);
+        b.G.push_back(g);
+        b.gheavy += g;
+        ++b.nheavy;
+    }
+    for (int q = 0; q < count; ++q)
+        if (!heavy[lpt[q]]) {
+            b.order.push_back(lpt[q]);
+            b.G.push_back(1);
+        }
+    const int nlight = count - b.nheavy;
+    b.grid = b.nheavy ? std::max(b.gheavy, std::min(slots, b.gheavy + nlight)) : std::min(slots, count);
+}
+
+uint64_t batch_signature(const BatchShape &b, const int64_t *n, const int32_t *d, const int32_t *k) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (v >> (8 * i)) & 0xFFu;
+            h *= 1099511628211ull;
+        }
+    };
+    mix((uint64_t)b.count);
+    mix((uint64_t)b.dtype);
+    mix((uint64_t)b.lp);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    mix((uint64_t)dev);
+    for (int i = 0; i < b.count; ++i) {
+        mix((uint64_t)n[i]);
+        mix((uint64_t)d[i]);
+        mix((uint64_t)k[i]);
+    }
+    return h;
+}
+
+std::mutex g_tune_mu;
+std::map<uint64_t, double> g_tune;   // batch signature -> fastest theta
+
+// Default theta, or the one KC_BATCH_THETA names ("inf": the plain queue).
+double default_theta() {
+    const char *e = getenv("KC_BATCH_THETA");
+    if (!e || !*e) return kThetaDefault;
+    if (strcmp(e, "inf") == 0) return kThetaQueue;
+    const double v = atof(e);
+    return v > 0 ? v : kThetaDefault;
+}
+
+bool tuned_theta(uint64_t sig, double *theta) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(sig);
+    if (it == g_tune.end()) return false;
+    *theta = it->second;
+    return true;
+}
+
+void remember_theta(uint64_t sig, double theta) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[sig] = theta;
+}
+
+// Device buffers of one batch, carved from one allocation.  The zero region
+// (queue counter, per-instance range words, group slots) starts the layout.
+struct BatchBufs {
     struct Per {
         void *staging, *pk;
         uint32_t *mind;
@@ -1288,159 +1364,496 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
         int32_t *range2;
         uint32_t *lpw;
         float *ept, *eblk, *cenT, *ecmax;
+        uint64_t *slots;
     };
-    std::vector<Per> per((size_t)count);
+    std::vector<Per> per;
+    int *counter = nullptr;
+    size_t zero_bytes = 0;
     int32_t *kout_dev = nullptr;
     double *rad_dev = nullptr;
     uint64_t *fkeys = nullptr;
-    int *counter = nullptr;
     PackSeg *segs_dev = nullptr;
     GonInst *insts_dev = nullptr;
     LpSeg *lsegs_dev = nullptr;
-    size_t zero_bytes = 0;
-    auto layout = [&](Carve &cv) {
-        counter = cv.take<int>(1);
-        for (int i = 0; i < count; ++i) per[i].range2 = cv.take<int32_t>(2);
-        zero_bytes = cv.off;
-        kout_dev = dev_kout ? k_out : cv.take<int32_t>((size_t)count);
-        rad_dev = dev_rad ? radii : cv.take<double>((size_t)count);
-        fkeys = cv.take<uint64_t>((size_t)count);
-        segs_dev = cv.take<PackSeg>((size_t)count);
-        insts_dev = cv.take<GonInst>((size_t)count);
-        lsegs_dev = cv.take<LpSeg>(lp ? (size_t)count : 0);
-        for (int i = 0; i < count; ++i) {
-            const int64_t nbi = nblocks(n[i]);
-            const int ki = (int)std::min<int64_t>(k[i], n[i]);
-            per[i].staging = dev_pts[i] ? nullptr : cv.take<char>((size_t)n[i] * d[i] * esz);
-            per[i].pk = cv.take<char>((size_t)nbi * BLK * d[i] * esz);
-            per[i].mind = cv.take<uint32_t>((size_t)nbi * BLK);
-            per[i].cen = dev_cen[i] ? centers[i] : cv.take<int64_t>((size_t)ki);
-            if (lp) {
-                per[i].lpw = cv.take<uint32_t>((size_t)nbi * lp_ngroups(lp, d[i]) * BLK);
-                per[i].ept = cv.take<float>((size_t)nbi * BLK);
-                per[i].eblk = cv.take<float>((size_t)nbi);
-                per[i].cenT = cv.take<float>((size_t)ki * d[i]);
-                per[i].ecmax = cv.take<float>(1);
-            }
-        }
-    };
-    {
-        Carve sizing(nullptr);
-        layout(sizing);
-        r = arena_reserve(c.arena, sizing.off, c.s);
-        if (r != KC_OK) return r;
-    }
-    Carve cv(c.arena->dev);
-    layout(cv);
-    DevStatus *st = c.arena->status;
+    DevStatus *st = nullptr;   // set by the caller
+    char *base = nullptr;
+    int64_t blocks = 0;        // packed blocks of all instances
+};
 
-    // Descriptors: PackSeg[count], GonInst[count] and LpSeg[count] (LPT
-    // order), contiguous in the arena, one upload.
-    const size_t gi_off = (char *)insts_dev - (char *)segs_dev;
-    const size_t ls_off = (char *)lsegs_dev - (char *)segs_dev;
-    const size_t up_bytes = lp ? ls_off + sizeof(LpSeg) * count : gi_off + sizeof(GonInst) * count;
-    std::vector<char> host(up_bytes + 256);
+// Lay out the batch's buffers (sizing pass when cv's base is null).
+// staging[i] / out pointers: used as given when the caller's memory is on
+// the device (dev_* true), else carved.
+void batch_layout(Carve &cv, const BatchShape &b, BatchBufs &B, const int64_t *n, const int32_t *d, const int32_t *k,
+                  int64_t *const *centers, int32_t *k_out, double *radii, const char *dev_pts, const char *dev_cen,
+                  bool dev_kout, bool dev_rad) {
+    const int count = b.count;
+    const size_t esz = 4;
+    B.per.assign((size_t)count, BatchBufs::Per{});
+    B.base = cv.base;
+    B.counter = cv.take<int>(1);
+    for (int i = 0; i < count; ++i) B.per[i].range2 = cv.take<int32_t>(2);
+    for (int q = 0; q < b.nheavy; ++q) {
+        const int i = b.order[q];
+        B.per[i].slots = cv.take<uint64_t>((size_t)std::min<int64_t>(k[i], n[i]) * b.G[q]);
+    }
+    B.zero_bytes = cv.off;
+    B.kout_dev = dev_kout ? k_out : cv.take<int32_t>((size_t)count);
+    B.rad_dev = dev_rad ? radii : cv.take<double>((size_t)count);
+    B.fkeys = cv.take<uint64_t>((size_t)count);
+    B.segs_dev = cv.take<PackSeg>((size_t)count);
+    B.insts_dev = cv.take<GonInst>((size_t)count);
+    B.lsegs_dev = cv.take<LpSeg>(b.lp ? (size_t)count : 0);
+    for (int i = 0; i < count; ++i) {
+        const int64_t nbi = nblocks(n[i]);
+        const int ki = (int)std::min<int64_t>(k[i], n[i]);
+        BatchBufs::Per &P = B.per[i];
+        P.staging = dev_pts[i] ? nullptr : cv.take<char>((size_t)n[i] * d[i] * esz);
+        P.pk = cv.take<char>((size_t)nbi * BLK * d[i] * esz);
+        P.mind = cv.take<uint32_t>((size_t)nbi * BLK);
+        P.cen = dev_cen[i] ? centers[i] : cv.take<int64_t>((size_t)ki);
+        if (b.lp) {
+            P.lpw = cv.take<uint32_t>((size_t)nbi * lp_ngroups(b.lp, d[i]) * BLK);
+            P.ept = cv.take<float>((size_t)nbi * BLK);
+            P.eblk = cv.take<float>((size_t)nbi);
+            P.cenT = cv.take<float>((size_t)ki * d[i]);
+            P.ecmax = cv.take<float>(1);
+        }
+    }
+}
+
+// Host image of the descriptors PackSeg[count], GonInst[count] and
+// LpSeg[count] (descriptor order), contiguous from B.segs_dev.
+std::vector<char> batch_descriptors(const BatchShape &b, BatchBufs &B, const void *const *pts, const int64_t *n,
+                                    const int32_t *d, const int32_t *k, const char *dev_pts, size_t *bytes) {
+    const int count = b.count;
+    const size_t gi_off = (char *)B.insts_dev - (char *)B.segs_dev;
+    const size_t ls_off = (char *)B.lsegs_dev - (char *)B.segs_dev;
+    *bytes = b.lp ? ls_off + sizeof(LpSeg) * count : gi_off + sizeof(GonInst) * count;
+    std::vector<char> host(*bytes + 256, 0);
     PackSeg *hs = reinterpret_cast<PackSeg *>(host.data());
     GonInst *hg = reinterpret_cast<GonInst *>(host.data() + gi_off);
     LpSeg *hl = reinterpret_cast<LpSeg *>(host.data() + ls_off);
     int64_t blk0 = 0;
+    int cta0 = 0;
     for (int q = 0; q < count; ++q) {
-        const int i = order[q];
+        const int i = b.order[q];
+        const BatchBufs::Per &P = B.per[i];
         PackSeg &S = hs[q];
-        memset(&S, 0, sizeof S);
-        S.src = dev_pts[i] ? pts[i] : per[i].staging;
-        S.dst = per[i].pk;
-        S.range2 = per[i].range2;
+        S.src = dev_pts[i] ? pts[i] : P.staging;
+        S.dst = P.pk;
+        S.range2 = P.range2;
         S.n = n[i];
         S.blk0 = blk0;
         S.d = d[i];
-        if (lp) {
+        if (b.lp) {
             LpSeg &Ls = hl[q];
-            memset(&Ls, 0, sizeof Ls);
-            Ls.pk = (const float *)per[i].pk;
-            Ls.lp = per[i].lpw;
-            Ls.ept = per[i].ept;
-            Ls.eblk = per[i].eblk;
+            Ls.pk = (const float *)P.pk;
+            Ls.lp = P.lpw;
+            Ls.ept = P.ept;
+            Ls.eblk = P.eblk;
             Ls.n = n[i];
             Ls.blk0 = blk0;
             Ls.d = d[i];
         }
         blk0 += nblocks(n[i]);
         GonInst &I = hg[q];
-        memset(&I, 0, sizeof I);
-        I.pk = per[i].pk;
-        I.mind = per[i].mind;
-        I.slots = nullptr;
-        I.centers = per[i].cen;
-        I.k_out = kout_dev + i;
-        I.final_key = fkeys + i;
+        I.pk = P.pk;
+        I.mind = P.mind;
+        I.slots = q < b.nheavy ? P.slots : nullptr;
+        I.centers = P.cen;
+        I.k_out = B.kout_dev + i;
+        I.final_key = B.fkeys + i;
         I.map = nullptr;
-        I.range2 = per[i].range2;
-        I.radius_out = rad_dev + i;
+        I.range2 = P.range2;
+        I.radius_out = B.rad_dev + i;
         I.lo = 0;
         I.n = n[i];
         I.base = 0;
         I.first = 0;
         I.d = d[i];
         I.k = (int)std::min<int64_t>(k[i], n[i]);
-        I.cta0 = 0;
-        I.G = 1;
+        I.cta0 = q < b.nheavy ? cta0 : 0;
+        I.G = q < b.nheavy ? b.G[q] : 1;
+        if (q < b.nheavy) cta0 += b.G[q];
         I.kcap = I.k;
-        if (lp) {
-            I.lp = per[i].lpw;
-            I.eblk = per[i].eblk;
-            I.ept = per[i].ept;
+        if (b.lp) {
+            I.lp = P.lpw;
+            I.eblk = P.eblk;
+            I.ept = P.ept;
             I.scale = nullptr;
-            I.cenT = per[i].cenT;
-            I.ecmax_out = per[i].ecmax;
-            I.lp_kind = lp;
+            I.cenT = P.cenT;
+            I.ecmax_out = P.ecmax;
+            I.lp_kind = b.lp;
         }
     }
-    KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
-    for (int i = 0; i < count; ++i)
-        if (!dev_pts[i])
-            KC_CUDA(cudaMemcpyAsync(per[i].staging, pts[i], (size_t)n[i] * d[i] * esz, cudaMemcpyHostToDevice, c.s),
-                    "copy points to device");
-    r = upload(c.arena, c.s, host.data(), up_bytes, segs_dev);
-    if (r != KC_OK) return r;
+    B.blocks = blk0;
+    return host;
+}
+
+// Enqueue one solve of the batch (descriptors already on the device):
+// clear the zero region, pack, GON, radii.  Stream-capturable.
+kc_status batch_enqueue(const BatchShape &b, const BatchBufs &B, long long timeout, bool trace, cudaStream_t s) {
+    KC_CUDA(cudaMemsetAsync(B.base, 0, B.zero_bytes, s), "scratch clear");
     {
-        TraceStep t("pack", c.s);
-        KC_CUDA(launch_pack_many(segs_dev, count, blk0, c.o.dtype, st, c.s), "pack launch");
-        if (lp) KC_CUDA(launch_lp_pack_many(lsegs_dev, count, blk0, c.s), "low-precision pack");
+        TraceStep t(trace ? "pack" : nullptr, s);
+        KC_CUDA(launch_pack_many(B.segs_dev, b.count, B.blocks, b.dtype, B.st, s), "pack launch");
+        if (b.lp) KC_CUDA(launch_lp_pack_many(B.lsegs_dev, b.count, B.blocks, s), "low-precision pack");
     }
     {
-        TraceStep t("gonzalez_batch", c.s);
+        TraceStep t(trace ? "gonzalez_batch" : nullptr, s);
         GonArgs g{};
-        g.insts = insts_dev;
-        g.ninst = count;
-        g.dtype = c.o.dtype;
-        g.dc = dc;
-        g.dmax = dmax;
-        g.st = st;
-        g.timeout_cycles = timeout_cycles(c.o);
-        g.grid = std::min(gon_queue_grid(c.o.dtype, dc, lp), count);
+        g.insts = B.insts_dev;
+        g.ninst = b.count;
+        g.dtype = b.dtype;
+        g.dc = b.dc;
+        g.dmax = b.dmax;
+        g.st = B.st;
+        g.timeout_cycles = timeout;
+        g.grid = b.grid;
         g.queue = 1;
-        g.counter = counter;
-        g.lp_kind = lp;
-        KC_CUDA(launch_gon(g, c.s), "batch launch");
+        g.counter = B.counter;
+        g.lp_kind = b.lp;
+        g.nheavy = b.nheavy;
+        g.gheavy = b.gheavy;
+        KC_CUDA(launch_gon(g, s), "batch launch");
     }
     {
-        TraceStep t("radius_batch", c.s);
-        KC_CUDA(launch_batch_radius(insts_dev, count, c.o.dtype, st, c.s), "batch radius launch");
+        TraceStep t(trace ? "radius_batch" : nullptr, s);
+        KC_CUDA(launch_batch_radius(B.insts_dev, b.count, b.dtype, B.st, s), "batch radius launch");
     }
+    return KC_OK;
+}
+
+// Shared argument checks and the shape of a batch (everything but the policy).
+kc_status batch_check(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d, const int32_t *k,
+                      int64_t *const *centers, const int32_t *k_out, const double *radii, const kc_opts &o,
+                      BatchShape &b) {
+    if (count < 1) return fail(KC_ERR_ARG, "count=%d must be >= 1", count);
+    if (!pts || !n || !d || !k || !centers || !k_out || !radii) return fail(KC_ERR_ARG, "null pointer argument");
+    int dmax = 0, dcommon = d[0];
+    for (int i = 0; i < count; ++i) {
+        if (!pts[i] || !centers[i]) return fail(KC_ERR_ARG, "instance %d: null pointer", i);
+        if (n[i] < 1 || n[i] > (int64_t)N_MAX) return fail(KC_ERR_ARG, "instance %d: n outside [1, 2^32-2]", i);
+        if (d[i] < 1) return fail(KC_ERR_ARG, "instance %d: d must be >= 1", i);
+        if (k[i] < 1) return fail(KC_ERR_ARG, "instance %d: k must be >= 1", i);
+        dmax = std::max(dmax, (int)d[i]);
+        if (d[i] != dcommon) dcommon = 0;
+    }
+    b.count = count;
+    b.dtype = o.dtype;
+    b.lp = lp_of(o);
+    if (b.lp == KC_SWEEP_FP8)
+        return fail(KC_ERR_ARG, "the batched form takes KC_SWEEP_F32 or KC_SWEEP_BF16 (fp8 needs per-instance scales)");
+    b.dc = (dcommon == 3 || dcommon == 8 || dcommon == 32) && o.dtype == KC_F32 ? dcommon : 0;
+    b.dmax = dmax;
+    return KC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d,
+                            const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
+                            const kc_opts *opts) {
+    g_err.clear();
+    BatchShape b;
+    kc_status r = batch_check(count, pts, n, d, k, centers, k_out, radii, opts ? *opts : default_opts(), b);
+    if (r != KC_OK) return r;
+    CallCtx c;
+    if ((r = begin(opts, c, KC_ASYNC | KC_AUTOTUNE)) != KC_OK) return r;
+    const bool dev_kout = is_device_ptr(k_out, c.dev);
+    const bool dev_rad = is_device_ptr(radii, c.dev);
+    std::vector<char> dev_pts((size_t)count), dev_cen((size_t)count);
+    bool all_dev = dev_kout && dev_rad;
+    for (int i = 0; i < count; ++i) {
+        dev_pts[i] = is_device_ptr(pts[i], c.dev);
+        dev_cen[i] = is_device_ptr(centers[i], c.dev);
+        all_dev = all_dev && dev_pts[i] && dev_cen[i];
+    }
+    if (c.async && !all_dev) return fail(KC_ERR_ARG, "KC_ASYNC needs device pointers for all arguments");
+    const bool tune = (c.o.flags & KC_AUTOTUNE) != 0;
+    if (tune && c.async) return fail(KC_ERR_ARG, "KC_AUTOTUNE times the batch and does not take KC_ASYNC");
+    const uint64_t sig = batch_signature(b, n, d, k);
+    double theta = default_theta();
+    const bool known = tuned_theta(sig, &theta);
+
+    BatchBufs B;
+    // One solve with the given theta: layout, inputs, descriptors, launches.
+    auto solve = [&](double th, float *ms) -> kc_status {
+        batch_policy(b, n, d, k, th);
+        Carve sizing(nullptr);
+        batch_layout(sizing, b, B, n, d, k, centers, k_out, radii, dev_pts.data(), dev_cen.data(), dev_kout, dev_rad);
+        kc_status rr = arena_reserve(c.arena, sizing.off, c.s);
+        if (rr != KC_OK) return rr;
+        Carve cv(c.arena->dev);
+        batch_layout(cv, b, B, n, d, k, centers, k_out, radii, dev_pts.data(), dev_cen.data(), dev_kout, dev_rad);
+        B.st = c.arena->status;
+        size_t up_bytes = 0;
+        std::vector<char> host = batch_descriptors(b, B, pts, n, d, k, dev_pts.data(), &up_bytes);
+        for (int i = 0; i < count; ++i)
+            if (!dev_pts[i])
+                KC_CUDA(cudaMemcpyAsync(B.per[i].staging, pts[i], (size_t)n[i] * d[i] * 4, cudaMemcpyHostToDevice,
+                                        c.s),
+                        "copy points to device");
+        if ((rr = upload(c.arena, c.s, host.data(), up_bytes, B.segs_dev)) != KC_OK) return rr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (ms) {
+            KC_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+            KC_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+            KC_CUDA(cudaEventRecord(e0, c.s), "cudaEventRecord");
+        }
+        rr = batch_enqueue(b, B, timeout_cycles(c.o), true, c.s);
+        if (ms) {
+            if (rr == KC_OK) {
+                KC_CUDA(cudaEventRecord(e1, c.s), "cudaEventRecord");
+                KC_CUDA(cudaEventSynchronize(e1), "cudaEventSynchronize");
+                KC_CUDA(cudaEventElapsedTime(ms, e0, e1), "cudaEventElapsedTime");
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        return rr;
+    };
+
+    if (tune && !known) {
+        // Every candidate solves the batch exactly (selection does not depend
+        // on the launch shape); the fastest theta is remembered.
+        float best_ms = 0.f;
+        for (double th : kThetas) {
+            float ms = 0.f;
+            if ((r = solve(th, &ms)) != KC_OK) return r;
+            if ((r = finish(c.arena, c.s)) != KC_OK) return r;
+            if (th == kThetas[0] || ms < best_ms) {
+                best_ms = ms;
+                theta = th;
+            }
+        }
+        remember_theta(sig, theta);
+    }
+    if ((r = solve(theta, nullptr)) != KC_OK) return r;
     for (int i = 0; i < count; ++i)
         if (!dev_cen[i])
-            KC_CUDA(cudaMemcpyAsync(centers[i], per[i].cen, (size_t)std::min<int64_t>(k[i], n[i]) * sizeof(int64_t),
+            KC_CUDA(cudaMemcpyAsync(centers[i], B.per[i].cen, (size_t)std::min<int64_t>(k[i], n[i]) * sizeof(int64_t),
                                     cudaMemcpyDeviceToHost, c.s),
                     "copy centers out");
     if (!dev_kout)
-        KC_CUDA(cudaMemcpyAsync(k_out, kout_dev, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost, c.s),
+        KC_CUDA(cudaMemcpyAsync(k_out, B.kout_dev, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost, c.s),
                 "copy k_out");
     if (!dev_rad)
-        KC_CUDA(cudaMemcpyAsync(radii, rad_dev, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, c.s),
+        KC_CUDA(cudaMemcpyAsync(radii, B.rad_dev, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, c.s),
                 "copy radii");
     if (c.async) return KC_OK;
     return finish(c.arena, c.s);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ batch plans
+struct kc_batch_plan {
+    int dev = 0;
+    char *mem = nullptr;
+    DevStatus *st = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last = nullptr;
+    bool ran = false;
+    double theta = 0;
+    int nheavy = 0, gheavy = 0, grid = 0;
+};
+
+namespace {
+
+void plan_free(kc_batch_plan *p) {
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->mem) cudaFree(p->mem);
+    delete p;
+}
+
+// Build one plan: its own device allocation (outside the per-stream arena,
+// so later calls cannot move it), descriptors uploaded once, and the solve
+// captured into a CUDA graph.
+kc_status plan_build(BatchShape &b, double theta, int32_t count, const void *const *pts, const int64_t *n,
+                     const int32_t *d, const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
+                     const kc_opts &o, kc_batch_plan **out) {
+    batch_policy(b, n, d, k, theta);
+    std::vector<char> dev_pts((size_t)count, 1), dev_cen((size_t)count, 1);
+    BatchBufs B;
+    Carve sizing(nullptr);
+    sizing.take<DevStatus>(1);
+    batch_layout(sizing, b, B, n, d, k, centers, k_out, radii, dev_pts.data(), dev_cen.data(), true, true);
+    kc_batch_plan *p = new kc_batch_plan();
+    KC_CUDA(cudaGetDevice(&p->dev), "cudaGetDevice");
+    cudaError_t e = cudaMalloc(&p->mem, sizing.off + 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        plan_free(p);
+        return fail(KC_ERR_OOM, "plan allocation of %zu bytes failed", sizing.off + 256);
+    }
+    Carve cv(p->mem);
+    p->st = cv.take<DevStatus>(1);
+    batch_layout(cv, b, B, n, d, k, centers, k_out, radii, dev_pts.data(), dev_cen.data(), true, true);
+    B.st = p->st;
+    size_t up_bytes = 0;
+    std::vector<char> host = batch_descriptors(b, B, pts, n, d, k, dev_pts.data(), &up_bytes);
+    cudaStream_t cs = nullptr;
+    kc_status r = KC_OK;
+    do {
+        if ((e = cudaMemset(p->st, 0, sizeof(DevStatus))) != cudaSuccess ||
+            (e = cudaMemcpy(B.segs_dev, host.data(), up_bytes, cudaMemcpyHostToDevice)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+            r = cuda_fail(e, "plan setup");
+            break;
+        }
+        r = batch_enqueue(b, B, timeout_cycles(o), false, cs);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        if (r != KC_OK) {
+            if (g) cudaGraphDestroy(g);
+            break;
+        }
+        if (e != cudaSuccess) {
+            r = cuda_fail(e, "graph capture");
+            break;
+        }
+        p->graph = g;
+        if ((e = cudaGraphInstantiate(&p->exec, g, 0)) != cudaSuccess) r = cuda_fail(e, "graph instantiation");
+    } while (false);
+    if (cs) cudaStreamDestroy(cs);
+    if (r != KC_OK) {
+        plan_free(p);
+        return r;
+    }
+    p->theta = theta;
+    p->nheavy = b.nheavy;
+    p->gheavy = b.gheavy;
+    p->grid = b.grid;
+    *out = p;
+    return KC_OK;
+}
+
+kc_status plan_status(kc_batch_plan *p) {
+    DevStatus h;
+    KC_CUDA(cudaMemcpy(&h, p->st, sizeof h, cudaMemcpyDeviceToHost), "status read-back");
+    if (h.code != 0) {
+        KC_CUDA(cudaMemset(p->st, 0, sizeof(DevStatus)), "status reset");
+        return status_text(h);
+    }
+    return KC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kc_status kc_batch_plan_create(int32_t count, const void *const *pts, const int64_t *n, const int32_t *d,
+                               const int32_t *k, int64_t *const *centers, int32_t *k_out, double *radii,
+                               const kc_opts *opts, kc_batch_plan **plan) {
+    g_err.clear();
+    if (!plan) return fail(KC_ERR_ARG, "null plan pointer");
+    *plan = nullptr;
+    BatchShape b;
+    kc_status r = batch_check(count, pts, n, d, k, centers, k_out, radii, opts ? *opts : default_opts(), b);
+    if (r != KC_OK) return r;
+    CallCtx c;
+    if ((r = begin(opts, c, KC_AUTOTUNE)) != KC_OK) return r;
+    if (!is_device_ptr(k_out, c.dev) || !is_device_ptr(radii, c.dev))
+        return fail(KC_ERR_ARG, "a plan needs device memory for k_out and radii");
+    for (int i = 0; i < count; ++i)
+        if (!is_device_ptr(pts[i], c.dev) || !is_device_ptr(centers[i], c.dev))
+            return fail(KC_ERR_ARG, "instance %d: a plan needs device memory for points and centers", i);
+    const uint64_t sig = batch_signature(b, n, d, k);
+    double theta = default_theta();
+    const bool known = tuned_theta(sig, &theta);
+    if ((c.o.flags & KC_AUTOTUNE) && !known) {
+        // Time each candidate's graph (one warm-up, then the mean of three
+        // replays) and keep the fastest plan.
+        kc_batch_plan *best = nullptr;
+        float best_ms = 0.f;
+        cudaEvent_t e0, e1;
+        KC_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+        KC_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+        for (double th : kThetas) {
+            kc_batch_plan *p = nullptr;
+            if ((r = plan_build(b, th, count, pts, n, d, k, centers, k_out, radii, c.o, &p)) != KC_OK) break;
+            float ms = 0.f;
+            cudaError_t e = cudaGraphLaunch(p->exec, c.s);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c.s);
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = cudaGraphLaunch(p->exec, c.s);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c.s);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                r = cuda_fail(e, "plan timing");
+                plan_free(p);
+                break;
+            }
+            if ((r = plan_status(p)) != KC_OK) {
+                plan_free(p);
+                break;
+            }
+            if (!best || ms < best_ms) {
+                plan_free(best);
+                best = p;
+                best_ms = ms;
+            } else {
+                plan_free(p);
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (r != KC_OK) {
+            plan_free(best);
+            return r;
+        }
+        remember_theta(sig, best->theta);
+        *plan = best;
+        return KC_OK;
+    }
+    return plan_build(b, theta, count, pts, n, d, k, centers, k_out, radii, c.o, plan);
+}
+
+kc_status kc_batch_plan_run(kc_batch_plan *plan, void *stream) {
+    g_err.clear();
+    if (!plan) return fail(KC_ERR_ARG, "null plan");
+    int dev = 0;
+    KC_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != plan->dev) return fail(KC_ERR_ARG, "the plan belongs to device %d, current device is %d", plan->dev, dev);
+    KC_CUDA(cudaGraphLaunch(plan->exec, (cudaStream_t)stream), "graph launch");
+    plan->last = (cudaStream_t)stream;
+    plan->ran = true;
+    note_launches(3);
+    return KC_OK;
+}
+
+kc_status kc_batch_plan_wait(kc_batch_plan *plan) {
+    g_err.clear();
+    if (!plan) return fail(KC_ERR_ARG, "null plan");
+    if (!plan->ran) return KC_OK;
+    KC_CUDA(cudaStreamSynchronize(plan->last), "cudaStreamSynchronize");
+    return plan_status(plan);
+}
+
+kc_status kc_batch_plan_info(const kc_batch_plan *plan, double *theta, int32_t *nheavy, int32_t *gheavy,
+                             int32_t *grid) {
+    g_err.clear();
+    if (!plan) return fail(KC_ERR_ARG, "null plan");
+    if (theta) *theta = plan->theta;
+    if (nheavy) *nheavy = plan->nheavy;
+    if (gheavy) *gheavy = plan->gheavy;
+    if (grid) *grid = plan->grid;
+    return KC_OK;
+}
+
+kc_status kc_batch_plan_destroy(kc_batch_plan *plan) {
+    g_err.clear();
+    if (!plan) return KC_OK;
+    if (plan->ran) cudaStreamSynchronize(plan->last);
+    plan_free(plan);
+    return KC_OK;
 }
 
 }  // extern "C"

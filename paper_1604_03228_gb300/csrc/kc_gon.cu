@@ -583,6 +583,17 @@ __device__ bool instance_ok(const GonInst &I, DevStatus *st) {
     return true;
 }
 
+// Last instance of insts[0, m) whose CTA group starts at or before this CTA.
+__device__ __forceinline__ void find_group(const GonInst *insts, int m, GonInst &I) {
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (insts[mid].cta0 <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    I = insts[lo];
+}
+
 template <typename T, int DC>
 __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_kernel(GonArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -590,17 +601,8 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_kernel(GonArgs a) {
     __shared__ GonInst I;
     __shared__ Shared sh;
     if (threadIdx.x == 0) {
-        if (a.insts) {
-            int lo = 0, hi = a.ninst - 1;   // last instance with cta0 <= blockIdx.x
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (a.insts[mid].cta0 <= (int)blockIdx.x) lo = mid;
-                else hi = mid - 1;
-            }
-            I = a.insts[lo];
-        } else {
-            I = a.single;
-        }
+        if (a.insts) find_group(a.insts, a.ninst, I);
+        else I = a.single;
     }
     __syncthreads();
     const int r = (int)blockIdx.x - I.cta0;
@@ -610,6 +612,10 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_kernel(GonArgs a) {
     gon_solve<T, DC, GROUP_NT>(I, r, I.G, cs, sh, a.st, a.timeout_cycles);
 }
 
+// Queue mode, optionally with heavy instances in front: insts[0, nheavy)
+// are solved by CTA groups [cta0, cta0 + G) of the first gheavy CTAs (the
+// launch is then cooperative, so the groups are co-resident); every CTA then
+// takes the remaining instances insts[nheavy, ninst) one at a time, in order.
 template <typename T, int DC>
 __global__ void __launch_bounds__(QUEUE_NT) gon_queue_kernel(GonArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -617,9 +623,17 @@ __global__ void __launch_bounds__(QUEUE_NT) gon_queue_kernel(GonArgs a) {
     __shared__ GonInst I;
     __shared__ Shared sh;
     __shared__ int s_i;
+    if ((int)blockIdx.x < a.gheavy) {
+        if (threadIdx.x == 0) find_group(a.insts, a.nheavy, I);
+        __syncthreads();
+        const int r = (int)blockIdx.x - I.cta0;
+        if (r >= 0 && r < I.G && ld_volatile_i32(&a.st->code) == 0 && instance_ok<T>(I, a.st))
+            gon_solve<T, DC, QUEUE_NT>(I, r, I.G, cs, sh, a.st, a.timeout_cycles);
+        __syncthreads();
+    }
     for (;;) {
         if (threadIdx.x == 0) {
-            s_i = atomicAdd(a.counter, 1);
+            s_i = a.nheavy + atomicAdd(a.counter, 1);
             if (s_i < a.ninst) I = a.insts[s_i];
         }
         __syncthreads();
@@ -631,17 +645,8 @@ __global__ void __launch_bounds__(QUEUE_NT) gon_queue_kernel(GonArgs a) {
 }
 
 __device__ __forceinline__ void find_instance(const GonArgs &a, GonInst &I) {
-    if (a.insts) {
-        int lo = 0, hi = a.ninst - 1;   // last instance with cta0 <= blockIdx.x
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.insts[mid].cta0 <= (int)blockIdx.x) lo = mid;
-            else hi = mid - 1;
-        }
-        I = a.insts[lo];
-    } else {
-        I = a.single;
-    }
+    if (a.insts) find_group(a.insts, a.ninst, I);
+    else I = a.single;
 }
 
 template <int KIND, int DC>
@@ -663,9 +668,17 @@ __global__ void __launch_bounds__(QUEUE_NT) gon_queue_lp_kernel(GonArgs a) {
     __shared__ GonInst I;
     __shared__ ShLP sh;
     __shared__ int s_i;
+    if ((int)blockIdx.x < a.gheavy) {
+        if (threadIdx.x == 0) find_group(a.insts, a.nheavy, I);
+        __syncthreads();
+        const int r = (int)blockIdx.x - I.cta0;
+        if (r >= 0 && r < I.G && ld_volatile_i32(&a.st->code) == 0)
+            gon_solve_lp<KIND, DC, QUEUE_NT>(I, r, I.G, smem_f, sh, a.st, a.timeout_cycles);
+        __syncthreads();
+    }
     for (;;) {
         if (threadIdx.x == 0) {
-            s_i = atomicAdd(a.counter, 1);
+            s_i = a.nheavy + atomicAdd(a.counter, 1);
             if (s_i < a.ninst) I = a.insts[s_i];
         }
         __syncthreads();
@@ -754,6 +767,7 @@ cudaError_t read_counters(unsigned long long out[4], bool reset) {
 }
 
 int gon_threads() { return GROUP_NT; }
+int gon_queue_warps() { return QUEUE_NT / 32; }
 int gon_warps_per_cta() { return GROUP_NT / 32; }
 
 static void *pick_fn(int dtype, int lp, int dc, bool queue) {
@@ -791,10 +805,21 @@ cudaError_t launch_gon(GonArgs &a, cudaStream_t s) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    void *args[] = {&a};
     note_launches(1);
-    if (a.queue) return cudaLaunchKernel(fn, dim3(a.grid), dim3(QUEUE_NT), args, smem, s);
-    return cudaLaunchCooperativeKernel(fn, dim3(a.grid), dim3(GROUP_NT), args, smem, s);
+    // Groups that wait on one another need a cooperative launch (all CTAs
+    // co-resident); the attribute form is also accepted by stream capture.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.grid);
+    cfg.blockDim = dim3(a.queue ? QUEUE_NT : GROUP_NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = (!a.queue || a.gheavy > 0) ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *args[] = {&a};
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 }  // namespace kc

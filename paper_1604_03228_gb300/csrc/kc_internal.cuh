@@ -174,6 +174,8 @@ struct GonArgs {
     int grid;                // CTAs
     int queue;               // 1: one CTA per instance, instances taken from *counter
     int *counter;            // queue mode: next instance (zeroed)
+    int nheavy;              // queue mode: insts[0, nheavy) are solved by CTA groups first
+    int gheavy;              // queue mode: CTAs of those groups (the first gheavy of the grid)
     int lp_kind;             // 0: FP32 sweep; KC_SWEEP_BF16 / KC_SWEEP_FP8 (float points)
 };
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s);
@@ -182,6 +184,7 @@ cudaError_t read_counters(unsigned long long out[4], bool reset);
 int gon_max_grid(int dtype, int d, int lp = 0);
 int gon_queue_grid(int dtype, int d, int lp = 0);
 int gon_threads();
+int gon_queue_warps();
 int gon_warps_per_cta();
 
 // Arguments for plain GON: one instance over the whole packed array, solved

@@ -58,3 +58,19 @@ def test_binding_raises_typed_errors():
     with pytest.raises(kc.KCError) as e:
         kc.kc_gonzalez(np.zeros((4, 2), dtype=np.float32), 2, first=9)
     assert e.value.status == kc.KC_ERR_ARG
+
+
+def test_batch_plan_host_argument_errors():
+    import paper_1604_03228_gb300 as kc
+    L = kc.load()
+    h = ct.c_void_p()
+    n = np.array([10], dtype=np.int64)
+    d = np.array([2], dtype=np.int32)
+    k = np.array([2], dtype=np.int32)
+    # rejected before any CUDA call
+    assert L.kc_batch_plan_create(0, None, None, None, None, None, None, None, None, ct.byref(h)) == kc.KC_ERR_ARG
+    assert L.kc_batch_plan_create(1, None, n.ctypes.data, d.ctypes.data, k.ctypes.data, None, None, None, None,
+                                  None) == kc.KC_ERR_ARG
+    assert L.kc_batch_plan_run(None, None) == kc.KC_ERR_ARG
+    assert L.kc_batch_plan_wait(None) == kc.KC_ERR_ARG
+    assert L.kc_batch_plan_destroy(None) == kc.KC_OK

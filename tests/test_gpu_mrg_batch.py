@@ -145,3 +145,99 @@ def test_batch_many_instances_sampled(kc):
     for i in rng.choice(count, 24, replace=False):
         _check_instance(insts[i].points, insts[i].k, res[i])
     assert all(r.k_out >= 1 for r in res)
+
+
+# ------------------------------------------- launch shapes, autotune, plans
+
+def _heavy_batch():
+    """Three large instances (heavy under theta <= 8) and 40 small ones."""
+    insts = [I.gauss_mixture(150_000 + 7 * i, 8, 90 + i, 25, 0.1, 0, 1) for i in range(3)]
+    ks = [64, 40, 90]
+    for i in range(40):
+        inst = I.batch_instance(i, n_lo=200, n_hi=5_000)
+        insts.append(I.gauss_mixture(inst.points.shape[0], 8, 200 + i, 5, 0.2, 0, 1))
+        ks.append(min(inst.k, 50))
+    return insts, ks
+
+
+@pytest.mark.parametrize("theta", ["inf", "4", "1", "0.25"])
+def test_batch_theta_shapes_exact(kc, monkeypatch, theta):
+    monkeypatch.setenv("KC_BATCH_THETA", theta)
+    insts, ks = _heavy_batch()
+    res = kc.kc_gonzalez_batch([_dev(p) for p in insts], ks)
+    for p, k, r in zip(insts, ks, res):
+        _check_instance(p, k, r)
+
+
+def test_batch_bf16_groups_exact(kc, monkeypatch):
+    monkeypatch.setenv("KC_BATCH_THETA", "1")
+    insts, ks = _heavy_batch()
+    res = kc.kc_gonzalez_batch([_dev(p) for p in insts], ks, sweep="bf16")
+    for p, k, r in zip(insts, ks, res):
+        _check_instance(p, k, r)
+
+
+def test_batch_autotune_exact(kc):
+    insts, ks = _heavy_batch()
+    res = kc.kc_gonzalez_batch([_dev(p) for p in insts], ks, flags=kc.KC_AUTOTUNE)
+    for p, k, r in zip(insts, ks, res):
+        _check_instance(p, k, r)
+    again = kc.kc_gonzalez_batch([_dev(p) for p in insts], ks, flags=kc.KC_AUTOTUNE)   # cached shape
+    assert [a.centers.cpu().tolist() for a in again] == [a.centers.cpu().tolist() for a in res]
+
+
+def test_batch_plan_replays_current_points(kc, monkeypatch):
+    import torch
+    monkeypatch.setenv("KC_BATCH_THETA", "1")
+    insts, ks = _heavy_batch()
+    xs = [_dev(p) for p in insts]
+    plan = kc.kc_batch_plan_create(xs, ks)
+    theta, nheavy, gheavy, grid = kc.kc_batch_plan_info(plan)
+    assert theta == 1.0 and nheavy >= 1 and gheavy >= 2 * nheavy and grid >= gheavy
+    for _ in range(2):
+        kc.kc_batch_plan_run(plan)
+        res = kc.kc_batch_plan_wait(plan)
+        for p, k, r in zip(insts, ks, res):
+            _check_instance(p, k, r)
+    # new values in the bound buffers: the next replay solves them
+    new = [I.gauss_mixture(p.shape[0], p.shape[1], 500 + i, 7, 0.3, -1, 1) for i, p in enumerate(insts)]
+    for x, p in zip(xs, new):
+        x.copy_(torch.from_numpy(p))
+    kc.kc_batch_plan_run(plan)
+    res = kc.kc_batch_plan_wait(plan)
+    for p, k, r in zip(new, ks, res):
+        _check_instance(p, k, r)
+    kc.kc_batch_plan_destroy(plan)
+
+
+def test_batch_plan_autotune_and_stream(kc):
+    import torch
+    insts, ks = _heavy_batch()
+    xs = [_dev(p) for p in insts]
+    plan = kc.kc_batch_plan_create(xs, ks, flags=kc.KC_AUTOTUNE)
+    theta, nheavy, gheavy, grid = kc.kc_batch_plan_info(plan)
+    assert theta in (1e300, 4.0, 2.0, 1.0, 0.5) and grid >= 1
+    s = torch.cuda.Stream()
+    kc.kc_batch_plan_run(plan, stream=s)
+    res = kc.kc_batch_plan_wait(plan)
+    for p, k, r in zip(insts, ks, res):
+        _check_instance(p, k, r)
+    kc.kc_batch_plan_destroy(plan)
+
+
+def test_batch_plan_rejects_host_memory(kc):
+    L = kc.load()
+    import ctypes as ct
+    pts = np.zeros((10, 2), dtype=np.float32)
+    ptrs = (ct.c_void_p * 1)(pts.ctypes.data)
+    cen = np.zeros(2, dtype=np.int64)
+    cptrs = (ct.c_void_p * 1)(cen.ctypes.data)
+    n = np.array([10], dtype=np.int64)
+    d = np.array([2], dtype=np.int32)
+    k = np.array([2], dtype=np.int32)
+    ko = np.zeros(1, dtype=np.int32)
+    rr = np.zeros(1, dtype=np.float64)
+    h = ct.c_void_p()
+    st = L.kc_batch_plan_create(1, ptrs, n.ctypes.data, d.ctypes.data, k.ctypes.data, cptrs, ko.ctypes.data,
+                                rr.ctypes.data, None, ct.byref(h))
+    assert st == kc.KC_ERR_ARG and b"device memory" in L.kc_last_error()
