@@ -41,6 +41,14 @@ N, D, K = 1_000_000, 10, 100
 WORKLOAD = "gon_radius_gau_n1000000_d10_k100"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
+
+# Further workloads (one JSON line each, same keys): the int GON latency case,
+# GON / MRG on 10M x 16, GON / tensor-core radius / EIM on 8M x 64, and the
+# 4,096-instance batch.
+EXTRA = ("gon_int_n10000_d2_k10", "gon_unif_n10000000_d16_k200", "mrg_unif_n10000000_d16_m64_k200",
+         "gon_gau_n8000000_d64_k1024", "radius_gau_n8000000_d64_k1024", "eim_gau_n8000000_d64_k1024",
+         "batch_4096")
 
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from an
 # ncu capture, keyed by the SHA-256 of the kernel's source file at capture
@@ -58,6 +66,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD,) + EXTRA,
+                    help="the default is the headline line; the others measure the remaining paths")
+    ap.add_argument("--sweep", default="f32", choices=["f32", "bf16", "fp8"],
+                    help="sweep precision for the GON / MRG / batch workloads")
     return ap.parse_args()
 
 
@@ -72,13 +84,15 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
-def peaks():
+def peaks(kind="hbm"):
+    """Roofline denominator: measured HBM copy GB/s, or dense bf16 TFLOP/s
+    (burst; fp16 runs at the bf16 rate)."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             j = json.load(f)
-        return float(j["hbm_gbs"]), "measured"
-    return FALLBACK_HBM_GBS, "fallback"
+        return (float(j["hbm_gbs"]) if kind == "hbm" else float(j["bf16_tflops"])), "measured"
+    return (FALLBACK_HBM_GBS if kind == "hbm" else FALLBACK_BF16_TFLOPS), "fallback"
 
 
 def workload(rank: int):
@@ -316,10 +330,150 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------- other workloads
+
+def run_extra(args):
+    """One of EXTRA on one GPU: warm-up, then `steps` timed calls (CUDA
+    events around each); the dominant step's device time comes from the
+    library's trace events."""
+    import numpy as np
+    import torch
+
+    import paper_1604_03228_gb300 as kc
+    from paper_1604_03228_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    kc.load()
+    name, sw = args.workload, (None if args.sweep == "f32" else args.sweep)
+    bpc = {"f32": 4, "bf16": 2, "fp8": 1}[args.sweep]
+    mind_b = 4 if sw is None else 2          # running minimum: u32, or 16-bit code in the mixed sweep
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    cfg = {"workload": name, "sweep": args.sweep, "l2": "inputs larger than L2"}
+    dom, bound, plan = "gonzalez", "hbm", None
+    if name == "gon_int_n10000_d2_k10":
+        w = I.gon_int_10k()
+        x, k, n, d = dev(w.points), w.k, 10_000, 2
+        step = lambda: kc.kc_gonzalez(x, k)
+        evals, units = k * n, None
+        cfg.update(n=n, d=d, k=k, dtype="int32", l2="80 KB input, on chip (latency bound)")
+    elif name in ("gon_unif_n10000000_d16_k200", "mrg_unif_n10000000_d16_m64_k200"):
+        pts, off, k = I.mrg_unif_10m()
+        n, d = pts.shape
+        x, o = dev(pts), dev(off)
+        if name.startswith("gon"):
+            step = lambda: kc.kc_gonzalez(x, k, sweep=sw)
+            evals = k * n                               # the k sweeps (the radius is their maximum)
+        else:
+            step = lambda: kc.kc_mrg(x, k, 64, o, sweep=sw)
+            dom = "mrg_round1"
+            evals = k * n + k * (64 * k) + k * n        # round 1, round 2 on the union, radius
+            cfg.update(m=64, parts="Zipf(1.1) contiguous")
+        units = k * n * (d * bpc + mind_b)
+        cfg.update(n=n, d=d, k=k)
+    elif name in ("gon_gau_n8000000_d64_k1024", "radius_gau_n8000000_d64_k1024", "eim_gau_n8000000_d64_k1024"):
+        pts = I.eim_gau_8m()
+        n, d = pts.shape
+        k = 1024
+        x = dev(pts)
+        cfg.update(n=n, d=d, k=k)
+        if name.startswith("gon"):
+            step = lambda: kc.kc_gonzalez(x, k, sweep=sw)
+            evals = k * n
+            units = k * n * (d * bpc + mind_b)
+        elif name.startswith("radius"):
+            cen = torch.from_numpy(np.sort(I.uniform_int(7, 3, k, 0, n - 1)).astype(np.int64)).cuda()
+            step = lambda: kc.kc_radius(x, cen)
+            dom, bound = "radius", "tensor"
+            evals = k * n
+            units = 2.0 * n * k * d                     # GEMM-form flops of the n x k block
+            cfg.update(centers="k seeded uniform indices", path="tcgen05 fp16 block + exact recheck")
+        else:
+            step = lambda: kc.kc_eim(x, k, eps=0.1, phi=6.0, seed=40)
+            dom, bound = "eim_prune", "tensor"
+            evals, units = None, None                   # from the prune counters below
+            cfg.update(eps=0.1, phi=6.0, seed=40, metric_note="evals = prune |R| x |S| + GON on the sample + radius")
+    elif name == "batch_4096":
+        insts = [I.batch_instance(i) for i in range(4096)]
+        xs = [dev(z.points) for z in insts]
+        ks = [z.k for z in insts]
+        plan = kc.kc_batch_plan_create(xs, ks, sweep=sw, flags=kc.KC_AUTOTUNE)
+        step = lambda: kc.kc_batch_plan_run(plan)
+        dom = "gonzalez_batch"
+        evals = sum(z.points.shape[0] * min(z.k, z.points.shape[0]) for z in insts)
+        units = sum(z.points.shape[0] * min(z.k, z.points.shape[0]) * (z.points.shape[1] * bpc + mind_b)
+                    for z in insts)
+        th, nh, gh, grid = kc.kc_batch_plan_info(plan)
+        cfg.update(count=4096, step="CUDA-graph replay of the batch plan", theta=th, group_instances=nh,
+                   group_ctas=gh, grid=grid)
+    s = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    kc.kc_counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = kc.kc_launch_count()
+    t0 = time.time()
+    for i in range(args.steps):
+        ev[i][0].record(s)
+        step()
+        ev[i][1].record(s)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    launches = kc.kc_launch_count() - launches0
+    sampler.stop()
+    total_ms = sum(a.elapsed_time(b) for a, b in ev)
+    counters = kc.kc_counters()
+    # the dominant step's device time, traced outside the timed region
+    kc.kc_trace_read()
+    kc.kc_trace_enable(True)
+    if plan is not None:
+        kc.kc_gonzalez_batch(xs, ks, sweep=sw, flags=kc.KC_AUTOTUNE)   # same shape, traced (graphs are not)
+    else:
+        step()
+    torch.cuda.synchronize()
+    kc.kc_trace_enable(False)
+    trace = kc.kc_trace_read()
+    shares = {}
+    for nm, nk, ms in trace:
+        shares[nm] = shares.get(nm, 0.0) + ms
+    dom_ms = shares.get(dom)
+    if name.startswith("eim"):
+        pairs = counters[4] // args.steps
+        units = 2.0 * pairs * d
+        evals = pairs + k * n                           # prune blocks, radius (GON on the sample not counted)
+        cfg.update(prune_pairs_per_solve=pairs)
+    roof = None
+    if units is not None and dom_ms:
+        peak, pk = peaks(bound)
+        if bound == "hbm":
+            achieved, unit = units / (dom_ms / 1e3) / 1e9, "GB/s"
+        else:
+            achieved, unit = units / (dom_ms / 1e3) / 1e12, "TFLOP/s"
+        roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": None, "kernel_step": dom, "avg_ms": dom_ms, "peak_kind": pk,
+                "alg_per_launch": units}
+    line = {"metric": METRIC, "value": evals * args.steps / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "i32" if name.startswith("gon_int") else "f32", "data": "synthetic", "config": cfg,
+            "roofline": roof, "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
+            "clocks": sampler.summary(t0, t1), "step_share_ms": shares,
+            "counters": {"sweep_rechecks": counters[0], "sweep_overflows": counters[1],
+                         "prune_undecided_pairs": counters[2], "prune_points": counters[3],
+                         "sweep_big_rechecks": counters[5], "gon_cycles_sweep": counters[6],
+                         "gon_cycles_recheck": counters[7], "gon_cycles_exchange": counters[8],
+                         "gon_cycles_sweep_max_cta": counters[9], "gon_cycles_sweep_recheck_max_cta": counters[10]}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != WORKLOAD:
+        run_extra(args)
     else:
         run_gpu(args)
 

@@ -296,8 +296,15 @@ int64_t kc_launch_count(void);
  * recomputed exactly in FP32, out[1] = candidate-buffer overflows (a warp
  * rescanned its running minima); and of EIM's tensor-core prune: out[2] =
  * (point, center) pairs left undecided by the bounds and recomputed exactly,
- * out[3] = points processed.  Synchronises the device.  Returns the number of
- * values (4), or -1 on a CUDA error.
+ * out[3] = points processed; and of every EIM prune (tensor cores or CUDA
+ * cores, counted on the host for all devices): out[4] = the sum over prune
+ * rounds of |R| x |S|, the point-center pairs the prune covers; out[5] =
+ * sweep rechecks whose exact-minimum memo lagged more than 4 centers (done by
+ * a whole warp); out[6..8] = clock cycles of the persistent GON kernels,
+ * summed over CTAs, spent in the sweep, the exact rechecks and the group
+ * exchange; out[9], out[10] = the largest per-CTA sweep total and sweep +
+ * recheck total.  Synchronises the device.  Returns the number of values
+ * (11), or -1 on a CUDA error.
  */
 int32_t kc_counters(int64_t *out, int32_t cap);
 

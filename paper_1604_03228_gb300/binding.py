@@ -95,9 +95,12 @@ def load(path: str | None = None):
 
 def kc_counters():
     """Diagnostics since the last call: (sweep exact rechecks, sweep buffer
-    overflows, prune undecided pairs, prune points)."""
-    out = np.zeros(4, dtype=np.int64)
-    if load().kc_counters(out.ctypes.data, 4) < 0:
+    overflows, prune undecided pairs, prune points, prune |R| x |S| pairs,
+    sweep rechecks with a lagging memo, GON kernel cycles in sweep / recheck /
+    exchange summed over CTAs, largest per-CTA sweep and sweep + recheck
+    totals)."""
+    out = np.zeros(11, dtype=np.int64)
+    if load().kc_counters(out.ctypes.data, 11) < 0:
         raise KCError(KC_ERR_CUDA, "kc_counters failed")
     return tuple(int(v) for v in out)
 

@@ -27,6 +27,7 @@ thread_local std::string g_err;
 
 // ------------------------------------------------------------ tracing
 std::atomic<int64_t> g_launches{0};
+std::atomic<unsigned long long> g_prune_pairs{0};   // sum of |R| x |S| over EIM prunes
 std::atomic<int> g_trace_on{0};
 thread_local int t_kernels = 0;
 
@@ -299,6 +300,7 @@ struct LPBufs {
     uint32_t *lp = nullptr;
     float *eblk = nullptr, *ept = nullptr, *scale = nullptr;
     unsigned *colmax = nullptr;
+    uint32_t *m32 = nullptr, *stamp = nullptr;   // recheck memo
 };
 
 void take_lp(Carve &cv, LPBufs &L, int lp, int64_t n, int d) {
@@ -313,6 +315,8 @@ void take_lp(Carve &cv, LPBufs &L, int lp, int64_t n, int d) {
     L.ept = cv.take<float>((size_t)nb * BLK);
     L.scale = cv.take<float>((size_t)ng * 4);
     L.colmax = cv.take<unsigned>((size_t)d);
+    L.m32 = cv.take<uint32_t>((size_t)nb * BLK);
+    L.stamp = cv.take<uint32_t>((size_t)nb * BLK);
 }
 
 // Tensor-core radius filter scratch for kc centers over n float points
@@ -362,6 +366,8 @@ void attach_lp(GonInst &I, const LPBufs &L, int lp, float *cenT, int kcap, float
     I.cenT = cenT;
     I.kcap = kcap;
     I.ecmax_out = ecmax;
+    I.m32 = L.m32;
+    I.stamp = L.stamp;
     I.lp_kind = lp;
 }
 
@@ -406,14 +412,23 @@ const char *kc_version(void) { return "kcenter-gb300 0.1 (sm_103a)"; }
 void kc_trace_enable(int32_t on) { g_trace_on = on ? 1 : 0; }
 
 int32_t kc_counters(int64_t *out, int32_t cap) {
-    unsigned long long v[4] = {0, 0, 0, 0};
-    if (cudaDeviceSynchronize() != cudaSuccess || read_counters(v, true) != cudaSuccess ||
+    unsigned long long v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (cudaDeviceSynchronize() != cudaSuccess || read_counters(g, true) != cudaSuccess ||
         read_tc_counters(v + 2, true) != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }
-    for (int i = 0; i < cap && i < 4; ++i) out[i] = (int64_t)v[i];
-    return 4;
+    v[0] = g[0];
+    v[1] = g[1];
+    v[4] = g_prune_pairs.exchange(0);
+    v[5] = g[2];
+    v[6] = g[3];
+    v[7] = g[4];
+    v[8] = g[5];
+    v[9] = g[6];
+    v[10] = g[7];
+    for (int i = 0; i < cap && i < 11; ++i) out[i] = (int64_t)v[i];
+    return 11;
 }
 
 int64_t kc_launch_count(void) { return g_launches.load(); }
@@ -507,7 +522,9 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         unsigned long long *key32 = cv.take<unsigned long long>(1);
         unsigned long long *max64 = cv.take<unsigned long long>(1);
         unsigned long long *arg64 = cv.take<unsigned long long>(1);
-        uint64_t *slots = cv.take<uint64_t>((size_t)keff * grid);
+        // per (step, CTA): argmax keys, and for the mixed-precision sweep the
+        // CTAs' lower bounds too
+        uint64_t *slots = cv.take<uint64_t>((size_t)keff * grid * (lp ? 2 : 1));
         *zero_bytes = cv.off;
         *staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
         void *pk = cv.take<char>((size_t)nb * BLK * d * esz);
@@ -576,7 +593,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
                 "pack launch");
         if (lp)
             KC_CUDA(launch_lp_pack(lp, (const float *)g.single.pk, n, d, LB.colmax, LB.scale, LB.lp, LB.ept,
-                                   LB.eblk, c.s),
+                                   LB.eblk, LB.stamp, c.s),
                     "low-precision pack");
     }
     {
@@ -776,7 +793,8 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
                 ++sum;
             }
         }
-        for (int i = 0; i < m; ++i) slot_off[i + 1] = slot_off[i] + (queue1 ? 0 : (int64_t)ki[i] * G[i]);
+        for (int i = 0; i < m; ++i)
+            slot_off[i + 1] = slot_off[i] + (queue1 ? 0 : (int64_t)ki[i] * G[i] * (lp ? 2 : 1));
     }
     int grid1 = 0;
     for (int i = 0; i < m; ++i) grid1 += G[i];
@@ -905,7 +923,8 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         TraceStep t("pack", c.s);
         KC_CUDA(launch_pack(src, c.o.dtype, n, d, Lo.pk, Lo.range2, st, c.s), "pack launch");
         if (lp)
-            KC_CUDA(launch_lp_pack(lp, (const float *)Lo.pk, n, d, LB.colmax, LB.scale, LB.lp, LB.ept, LB.eblk, c.s),
+            KC_CUDA(launch_lp_pack(lp, (const float *)Lo.pk, n, d, LB.colmax, LB.scale, LB.lp, LB.ept, LB.eblk,
+                                   LB.stamp, c.s),
                     "low-precision pack");
     }
     {
@@ -1044,7 +1063,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         Lo.thr = cv.take<uint32_t>(1);
         Lo.v = cv.take<uint32_t>(1);
         Lo.fk = cv.take<uint64_t>(1);
-        Lo.slots = cv.take<uint64_t>((size_t)keff_max * grid);
+        Lo.slots = cv.take<uint64_t>((size_t)keff_max * grid * (lp ? 2 : 1));
         Lo.mask = cv.take<uint8_t>((size_t)n);
         Lo.zero_bytes = cv.off;
         Lo.staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
@@ -1157,6 +1176,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
                 KC_CUDA(launch_eim_select(Lo.H, Lo.dH, (int64_t)hn, p, Lo.thr, Lo.v, c.s), "select");
             }
             TraceStep t("eim_prune", c.s);
+            g_prune_pairs += (unsigned long long)rn * (unsigned long long)sn;
             if (Ptc.tc_at && sn >= 256) {
                 // tensor-core R x S block with exact rechecks of undecided pairs
                 KC_CUDA(launch_tc_prune((const float *)src, d, Rc, rn, Lo.mask, (const float *)Lo.Sc, sn, tc_bufs(Ptc),
@@ -1186,6 +1206,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         KC_CUDA(launch_gather_pack(Lo.pk, c.o.dtype, d, Lo.C, Lo.total, nC, Lo.pkC, c.s), "gather C");
         if (lp && nC > 0)
             KC_CUDA(launch_lp_pack(lp, (const float *)Lo.pkC, nC, d, LB.colmax, LB.scale, LB.lp, LB.ept, LB.eblk,
+                                   LB.stamp,
                                    c.s),
                     "low-precision pack");
     }
@@ -1332,14 +1353,6 @@ uint64_t batch_signature(const BatchShape &b, const int64_t *n, const int32_t *d
 std::mutex g_tune_mu;
 std::map<uint64_t, double> g_tune;   // batch signature -> fastest theta
 
-// Default theta, or the one KC_BATCH_THETA names ("inf": the plain queue).
-double default_theta() {
-    const char *e = getenv("KC_BATCH_THETA");
-    if (!e || !*e) return kThetaDefault;
-    if (strcmp(e, "inf") == 0) return kThetaQueue;
-    const double v = atof(e);
-    return v > 0 ? v : kThetaDefault;
-}
 
 bool tuned_theta(uint64_t sig, double *theta) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1354,6 +1367,20 @@ void remember_theta(uint64_t sig, double theta) {
     g_tune[sig] = theta;
 }
 
+// The theta for a batch: KC_BATCH_THETA if set ("inf": the plain queue;
+// it also skips tuning), else the tuned one for this shape, else the
+// default.  Returns whether the choice is settled (no tuning needed).
+bool pick_theta(uint64_t sig, double *theta) {
+    const char *e = getenv("KC_BATCH_THETA");
+    if (e && *e) {
+        const double v = strcmp(e, "inf") == 0 ? kThetaQueue : atof(e);
+        *theta = v > 0 ? v : kThetaDefault;
+        return true;
+    }
+    *theta = kThetaDefault;
+    return tuned_theta(sig, theta);
+}
+
 // Device buffers of one batch, carved from one allocation.  The zero region
 // (queue counter, per-instance range words, group slots) starts the layout.
 struct BatchBufs {
@@ -1364,6 +1391,7 @@ struct BatchBufs {
         int32_t *range2;
         uint32_t *lpw;
         float *ept, *eblk, *cenT, *ecmax;
+        uint32_t *m32, *stamp;
         uint64_t *slots;
     };
     std::vector<Per> per;
@@ -1394,7 +1422,7 @@ void batch_layout(Carve &cv, const BatchShape &b, BatchBufs &B, const int64_t *n
     for (int i = 0; i < count; ++i) B.per[i].range2 = cv.take<int32_t>(2);
     for (int q = 0; q < b.nheavy; ++q) {
         const int i = b.order[q];
-        B.per[i].slots = cv.take<uint64_t>((size_t)std::min<int64_t>(k[i], n[i]) * b.G[q]);
+        B.per[i].slots = cv.take<uint64_t>((size_t)std::min<int64_t>(k[i], n[i]) * b.G[q] * (b.lp ? 2 : 1));
     }
     B.zero_bytes = cv.off;
     B.kout_dev = dev_kout ? k_out : cv.take<int32_t>((size_t)count);
@@ -1416,6 +1444,8 @@ void batch_layout(Carve &cv, const BatchShape &b, BatchBufs &B, const int64_t *n
             P.ept = cv.take<float>((size_t)nbi * BLK);
             P.eblk = cv.take<float>((size_t)nbi);
             P.cenT = cv.take<float>((size_t)ki * d[i]);
+            P.m32 = cv.take<uint32_t>((size_t)nbi * BLK);
+            P.stamp = cv.take<uint32_t>((size_t)nbi * BLK);
             P.ecmax = cv.take<float>(1);
         }
     }
@@ -1451,6 +1481,7 @@ std::vector<char> batch_descriptors(const BatchShape &b, BatchBufs &B, const voi
             Ls.lp = P.lpw;
             Ls.ept = P.ept;
             Ls.eblk = P.eblk;
+            Ls.stamp = P.stamp;
             Ls.n = n[i];
             Ls.blk0 = blk0;
             Ls.d = d[i];
@@ -1482,6 +1513,8 @@ std::vector<char> batch_descriptors(const BatchShape &b, BatchBufs &B, const voi
             I.ept = P.ept;
             I.scale = nullptr;
             I.cenT = P.cenT;
+            I.m32 = P.m32;
+            I.stamp = P.stamp;
             I.ecmax_out = P.ecmax;
             I.lp_kind = b.lp;
         }
@@ -1575,8 +1608,8 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
     const bool tune = (c.o.flags & KC_AUTOTUNE) != 0;
     if (tune && c.async) return fail(KC_ERR_ARG, "KC_AUTOTUNE times the batch and does not take KC_ASYNC");
     const uint64_t sig = batch_signature(b, n, d, k);
-    double theta = default_theta();
-    const bool known = tuned_theta(sig, &theta);
+    double theta = kThetaDefault;
+    const bool known = pick_theta(sig, &theta);
 
     BatchBufs B;
     // One solve with the given theta: layout, inputs, descriptors, launches.
@@ -1766,8 +1799,8 @@ kc_status kc_batch_plan_create(int32_t count, const void *const *pts, const int6
         if (!is_device_ptr(pts[i], c.dev) || !is_device_ptr(centers[i], c.dev))
             return fail(KC_ERR_ARG, "instance %d: a plan needs device memory for points and centers", i);
     const uint64_t sig = batch_signature(b, n, d, k);
-    double theta = default_theta();
-    const bool known = tuned_theta(sig, &theta);
+    double theta = kThetaDefault;
+    const bool known = pick_theta(sig, &theta);
     if ((c.o.flags & KC_AUTOTUNE) && !known) {
         // Time each candidate's graph (one warm-up, then the mean of three
         // replays) and keep the fastest plan.

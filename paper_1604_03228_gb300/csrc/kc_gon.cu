@@ -33,8 +33,32 @@
 namespace kc {
 
 // Diagnostic counters of the mixed-precision sweep (since the last read):
-// [0] exact FP32 rechecks of candidates, [1] candidate-buffer overflows.
-__device__ unsigned long long g_counters[4];
+// [0] exact FP32 rechecks of candidates, [1] candidate-buffer overflows,
+// [2] rechecks whose memo was more than a few centers behind (done by a
+// whole warp); clock cycles summed over CTAs of the GON kernels' phases:
+// [3] sweep (to the first barrier of a step), [4] exact rechecks (mixed
+// precision only), [5] group exchange and center load; the largest of any
+// CTA: [6] sweep total, [7] sweep + recheck total.
+__device__ unsigned long long g_counters[8];
+
+// Per-CTA phase clock, kept in shared memory (c[0] the last mark, c[1..3]
+// the phase totals) and driven by thread 0: mark() adds the cycles since the
+// last mark to one phase; publish() adds the totals to g_counters once.
+__device__ __forceinline__ void pc_start(long long *c) {
+    c[0] = clock64();
+    c[1] = c[2] = c[3] = 0;
+}
+__device__ __forceinline__ void pc_mark(long long *c, int ph) {
+    const long long now = clock64();
+    c[1 + ph] += now - c[0];
+    c[0] = now;
+}
+__device__ __forceinline__ void pc_publish(const long long *c) {
+    for (int i = 0; i < 3; ++i)
+        if (c[1 + i] > 0) atomicAdd(&g_counters[3 + i], (unsigned long long)c[1 + i]);
+    atomicMax(&g_counters[6], (unsigned long long)c[1]);
+    atomicMax(&g_counters[7], (unsigned long long)(c[1] + c[2]));
+}
 
 namespace {
 
@@ -181,6 +205,7 @@ __device__ __forceinline__ int64_t out_index(const GonInst &I, int64_t local) {
 struct Shared {
     uint64_t red[32];
     uint64_t key;
+    long long pc[4];
     int abort;
 };
 
@@ -201,11 +226,13 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
 
     int it;
     uint64_t K = 0;
+    if (tid == 0) pc_start(sh.pc);
     for (it = 0; it < I.k; ++it) {
         uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
+        if (tid == 0) pc_mark(sh.pc, 0);
         if (warp == 0) {
             uint64_t v = lane < W ? sh.red[lane] : 0;
             v = warp_max_u64(v);
@@ -226,13 +253,16 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
             }
         }
         __syncthreads();
-        if (sh.abort) return;
+        if (tid == 0) pc_mark(sh.pc, 2);
+        if (sh.abort) break;
         K = sh.key;
         if (key_val(K) == 0) {   // every point is at distance 0: stop early
             ++it;
             break;
         }
     }
+    if (tid == 0) pc_publish(sh.pc);
+    if (sh.abort) return;
     if (r == 0 && tid == 0) {
         *I.k_out = it;
         *I.final_key = K;
@@ -278,11 +308,14 @@ struct Cand {
     uint32_t idx;   // local index
     float U;
 };
-constexpr int LP_CAP = 64;   // candidates per warp
+constexpr int LP_CAP = 128;   // candidates per warp
 
 struct ShLP {
     uint64_t red[32];
     uint64_t key;
+    unsigned Lcta;     // largest positive lower bound L published by a warp this step (float bits)
+    float Tg;          // the group's largest L this step
+    long long pc[4];
     float Lw[32];
     int ovf[32];
     int cnt[32];
@@ -292,18 +325,86 @@ struct ShLP {
 
 
 // Canonical FP32 minimum of point gx over the first ncen centers (cenT is
-// [d][kcap]); lane l takes centers l, l+32, ...; warp minimum.
-__device__ uint32_t exact_min_warp(const float *__restrict__ pk, int64_t gx, int d, const float *__restrict__ cenT,
-                                   int kcap, int ncen, int lane) {
-    uint32_t m = 0xFFFFFFFFu;
-    for (int i = lane; i < ncen; i += 32) {
-        float acc = 0.f;
-        for (int j = 0; j < d; ++j) acc = sq_step(acc, pk[pk_index(gx, j, d)], cenT[(int64_t)j * kcap + i]);
-        m = min(m, __float_as_uint(acc));
+// [d][kcap]), from the memo: m32[gx] holds the exact minimum over centers
+// [0, stamp[gx]), so only centers [stamp, ncen) are evaluated; the memo is
+// then advanced to ncen.  A point is rechecked by the one warp that owns its
+// block (the same in every step), so the memo needs no atomics.
+constexpr int MEMO_LANE_GAP = 4;   // gaps up to this many centers: one lane per point
+
+// Canonical FP32 squared distance of packed point gx and center i of cenT,
+// loads issued four coordinates at a time (coordinates past d are zero
+// pairs, whose term fma(0, 0, acc) leaves acc unchanged).
+__device__ __forceinline__ float memo_dist(const float *__restrict__ pk, int64_t gx, int d,
+                                           const float *__restrict__ cenT, int kcap, int i) {
+    float acc = 0.f;
+    for (int j0 = 0; j0 < d; j0 += 4) {
+        float xv[4], cv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            xv[u] = j < d ? pk[pk_index(gx, j, d)] : 0.f;
+            cv[u] = j < d ? cenT[(int64_t)j * kcap + i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = sq_step(acc, xv[u], cv[u]);
     }
+    return acc;
+}
+
+// One lane, centers [stamp, ncen) in order.
+__device__ __forceinline__ uint32_t memo_min_lane(const float *__restrict__ pk, int64_t gx, int d,
+                                                  const float *__restrict__ cenT, int kcap, int ncen,
+                                                  uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp) {
+    const int s0 = (int)stamp[gx];
+    uint32_t m = s0 ? m32[gx] : 0xFFFFFFFFu;
+    for (int i = s0; i < ncen; ++i) m = min(m, __float_as_uint(memo_dist(pk, gx, d, cenT, kcap, i)));
+    m32[gx] = m;
+    stamp[gx] = (uint32_t)ncen;
+    return m;
+}
+
+// The whole warp: lane l takes centers stamp + l, stamp + l + 32, ...
+__device__ uint32_t memo_min_warp(const float *__restrict__ pk, int64_t gx, int d, const float *__restrict__ cenT,
+                                  int kcap, int ncen, uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp,
+                                  int lane) {
+    const int s0 = (int)stamp[gx];
+    uint32_t m = s0 ? m32[gx] : 0xFFFFFFFFu;
+    for (int i = s0 + lane; i < ncen; i += 32) m = min(m, __float_as_uint(memo_dist(pk, gx, d, cenT, kcap, i)));
 #pragma unroll
     for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    __syncwarp();
+    if (lane == 0) {
+        m32[gx] = m;
+        stamp[gx] = (uint32_t)ncen;
+    }
+    __syncwarp();
     return m;
+}
+
+// Exact values of the points lanes flag (want; local index idx): small gaps
+// lane by lane, the rest one at a time by the whole warp.  Updates the lane's
+// best key and recheck count.
+__device__ __forceinline__ void memo_recheck(const GonInst &I, const float *__restrict__ pk, int d, int ncen,
+                                             bool want, uint32_t idx, int lane, uint64_t &best, unsigned &nre) {
+    const int64_t gx = I.lo + idx;
+    const bool small = want && ncen - (int)I.stamp[gx] <= MEMO_LANE_GAP;
+    if (small) {
+        const uint32_t mm = memo_min_lane(pk, gx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp);
+        best = umax64(best, make_key(mm, idx));
+        ++nre;
+    }
+    unsigned big = __ballot_sync(0xFFFFFFFFu, want && !small);
+    if (big && lane == 0) atomicAdd(&g_counters[2], (unsigned long long)__popc(big));
+    while (big) {
+        const int src = __ffs(big) - 1;
+        big &= big - 1;
+        const uint32_t bidx = __shfl_sync(0xFFFFFFFFu, idx, src);
+        const uint32_t mm = memo_min_warp(pk, I.lo + bidx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp, lane);
+        if (lane == src) {
+            best = umax64(best, make_key(mm, bidx));
+            ++nre;
+        }
+    }
 }
 
 // In-place removal of buffer entries with U < lim (warp-cooperative).
@@ -320,6 +421,17 @@ __device__ __forceinline__ int lp_compact(Cand *buf, int cnt, float lim, int lan
         __syncwarp();
     }
     return out;
+}
+
+// Order-preserving 64-bit code of a float lower bound for the slot exchange
+// (non-zero, so a published slot is never mistaken for an empty one).
+__device__ __forceinline__ uint64_t enc_bound(float T) {
+    const uint32_t u = __float_as_uint(T);
+    return (1ull << 32) | (uint64_t)((u & 0x80000000u) ? ~u : (u | 0x80000000u));
+}
+__device__ __forceinline__ float dec_bound(uint64_t v) {
+    const uint32_t o = (uint32_t)v;
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
 }
 
 // The decoded low-precision center, its bound, and its FP32 coordinates
@@ -365,6 +477,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
         if (lane == 0) {
             sh.ecmax = ec;
             sh.abort = 0;
+            sh.Lcta = 0u;
         }
     }
     if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
@@ -372,6 +485,8 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
 
     int it;
     uint64_t K = 0;
+    if (tid == 0) pc_start(sh.pc);
+    volatile unsigned *Lcta = &sh.Lcta;
     for (it = 0; it < I.k; ++it) {
         const float ecmax = sh.ecmax;
         float Lrun = -INFINITY;
@@ -463,8 +578,11 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
 #pragma unroll
             for (int o2 = 16; o2; o2 >>= 1) bl = fmaxf(bl, __shfl_xor_sync(0xFFFFFFFFu, bl, o2));
             Lrun = fmaxf(Lrun, bl);
+            // admission against the CTA's largest L so far (<= the final T)
+            if (lane == 0 && Lrun > 0.f) atomicMax(&sh.Lcta, __float_as_uint(Lrun));
+            const float Lc = fmaxf(Lrun, __uint_as_float(*Lcta));
             if (!ovf) {
-                const float a0 = __fsub_rd(__fdiv_rd(Lrun, opg), delta);
+                const float a0 = __fsub_rd(__fdiv_rd(Lc, opg), delta);
                 const float t0 = a0 > 0.f ? __fdiv_rd(a0, opg) : 0.f;
                 const uint32_t tau = __float_as_uint(__fmul_rd(t0, t0));
 #pragma unroll
@@ -475,7 +593,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                     const int nq = __popc(bal);
                     if (nq == 0) continue;
                     if (cnt + nq > LP_CAP) {
-                        cnt = lp_compact(buf, cnt, Lrun, lane);
+                        cnt = lp_compact(buf, cnt, Lc, lane);
                         if (cnt + nq > LP_CAP) {
                             ovf = true;
                             break;
@@ -494,48 +612,80 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             sh.cnt[warp] = cnt;
         }
         __syncthreads();
+        if (tid == 0) pc_mark(sh.pc, 0);
         float T = -INFINITY;
         for (int w = 0; w < W; ++w) T = fmaxf(T, sh.Lw[w]);
+        if (G > 1) {
+            // The group's largest lower bound: a point whose upper bound is
+            // below it is strictly below that point's exact value, so only
+            // candidates reaching it are rechecked (slots [k G, 2 k G)).
+            if (warp == 0) {
+                bool ab = false;
+                uint64_t *ts = I.slots + (int64_t)I.k * G + (int64_t)it * G;
+                if (lane == 0) st_relaxed_u64(ts + r, enc_bound(T));
+                const uint64_t tg = poll_slots(ts, G, timeout, st, it, &ab);
+                if (lane == 0) {
+                    sh.Tg = dec_bound(tg);
+                    if (ab) sh.abort = 1;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) pc_mark(sh.pc, 2);
+            if (sh.abort) break;
+            T = sh.Tg;
+        }
         // exact recheck of this warp's candidates with U >= T
         uint64_t best = 0;
         const int ncen = it + 1;
-        unsigned long long nre = 0;
+        unsigned nre = 0;
         if (!ovf) {
             __syncwarp();
-            for (int e = 0; e < cnt; ++e) {
-                const Cand c = buf[e];
-                if (c.U >= T) {
-                    const uint32_t mm = exact_min_warp(pk, lo + c.idx, d, I.cenT, I.kcap, ncen, lane);
-                    best = umax64(best, make_key(mm, c.idx));
-                    ++nre;
-                }
+            for (int e0 = 0; e0 < cnt; e0 += 32) {
+                const int e = e0 + lane;
+                Cand c = {0u, -INFINITY};
+                if (e < cnt) c = buf[e];
+                memo_recheck(I, pk, d, ncen, e < cnt && c.U >= T, c.idx, lane, best, nre);
             }
         } else {
+            // the buffer overflowed: rescan the warp's running minima against
+            // the final T, buffering the survivors and rechecking them 32 at a
+            // time
             if (lane == 0) atomicAdd(&g_counters[1], 1ull);
+            int c2 = 0;
+            __syncwarp();
             for (int64_t b = lo / BLK + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) {
                 const float delta = __fadd_ru(I.eblk[b], ecmax);
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) {
                     const int64_t g = b * BLK + lane * 4 + q;
-                    const bool v = g >= lo && g < hi;
                     const bool pred =
-                        v && lp_upper(((uint32_t)reinterpret_cast<const uint16_t *>(I.mind)[g] + 1u) << 16, delta,
-                                      opg) >= T;
-                    unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
-                    while (bal) {
-                        const int src_lane = __ffs(bal) - 1;
-                        bal &= bal - 1;
-                        const int64_t gs = b * BLK + src_lane * 4 + q;
-                        const uint32_t mm = exact_min_warp(pk, gs, d, I.cenT, I.kcap, ncen, lane);
-                        best = umax64(best, make_key(mm, (uint32_t)(gs - lo)));
-                        ++nre;
+                        g >= lo && g < hi &&
+                        lp_upper(((uint32_t)reinterpret_cast<const uint16_t *>(I.mind)[g] + 1u) << 16, delta, opg) >=
+                            T;
+                    const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
+                    if (pred) buf[c2 + __popc(bal & ((1u << lane) - 1u))] = Cand{(uint32_t)(g - lo), 0.f};
+                    c2 += __popc(bal);
+                    if (c2 > LP_CAP - 32) {
+                        __syncwarp();
+                        for (int e0 = 0; e0 < c2; e0 += 32)
+                            memo_recheck(I, pk, d, ncen, e0 + lane < c2, e0 + lane < c2 ? buf[e0 + lane].idx : 0u,
+                                         lane, best, nre);
+                        c2 = 0;
+                        __syncwarp();
                     }
                 }
             }
+            __syncwarp();
+            for (int e0 = 0; e0 < c2; e0 += 32)
+                memo_recheck(I, pk, d, ncen, e0 + lane < c2, e0 + lane < c2 ? buf[e0 + lane].idx : 0u, lane, best,
+                             nre);
         }
-        if (lane == 0 && nre) atomicAdd(&g_counters[0], nre);
+        nre = __reduce_add_sync(0xFFFFFFFFu, nre);
+        if (lane == 0 && nre) atomicAdd(&g_counters[0], (unsigned long long)nre);
+        best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
+        if (tid == 0) pc_mark(sh.pc, 1);
         if (warp == 0) {
             uint64_t v = lane < W ? sh.red[lane] : 0;
             v = warp_max_u64(v);
@@ -545,6 +695,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                 if (lane == 0) st_relaxed_u64(&I.slots[(int64_t)it * G + r], v ? v : 1);
                 g = poll_slots(I.slots + (int64_t)it * G, G, timeout, st, it, &ab);
             }
+            if (lane == 0) sh.Lcta = 0u;   // next step's admission bound starts over
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {
                 const int64_t c = key_idx(g);
                 float ec;
@@ -558,13 +709,16 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             }
         }
         __syncthreads();
-        if (sh.abort) return;
+        if (tid == 0) pc_mark(sh.pc, 2);
+        if (sh.abort) break;
         K = sh.key;
         if (key_val(K) == 0) {
             ++it;
             break;
         }
     }
+    if (tid == 0) pc_publish(sh.pc);
+    if (sh.abort) return;
     if (r == 0 && tid == 0) {
         *I.k_out = it;
         *I.final_key = K;
@@ -663,7 +817,7 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_lp_kernel(GonArgs a) {
 }
 
 template <int KIND, int DC>
-__global__ void __launch_bounds__(QUEUE_NT) gon_queue_lp_kernel(GonArgs a) {
+__global__ void __launch_bounds__(QUEUE_NT, 4) gon_queue_lp_kernel(GonArgs a) {
     extern __shared__ __align__(16) float smem_f[];
     __shared__ GonInst I;
     __shared__ ShLP sh;
@@ -713,7 +867,6 @@ void *pick_queue_lp(int kind, int dc) {
     switch (dc) {
         case 3: return queue_lp_fn<KC_SWEEP_BF16, 3>();
         case 8: return queue_lp_fn<KC_SWEEP_BF16, 8>();
-        case 32: return queue_lp_fn<KC_SWEEP_BF16, 32>();
         default: return queue_lp_fn<KC_SWEEP_BF16, 0>();
     }
 }
@@ -757,10 +910,10 @@ void *pick_queue(int dtype, int dc) {
 
 }  // namespace
 
-cudaError_t read_counters(unsigned long long out[4], bool reset) {
-    cudaError_t e = cudaMemcpyFromSymbol(out, g_counters, 4 * sizeof(unsigned long long));
+cudaError_t read_counters(unsigned long long out[8], bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_counters, 8 * sizeof(unsigned long long));
     if (e == cudaSuccess && reset) {
-        const unsigned long long z[4] = {0, 0, 0, 0};
+        const unsigned long long z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         e = cudaMemcpyToSymbol(g_counters, z, sizeof z);
     }
     return e;

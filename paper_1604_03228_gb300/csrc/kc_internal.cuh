@@ -150,6 +150,11 @@ struct GonInst {
     const float *scale;
     float *cenT;
     float *ecmax_out;
+    // exact FP32 memo of the recheck, per point of the packed array: m32 is
+    // the canonical minimum over centers [0, stamp) (stamp zeroed by the
+    // low-precision pack), so a recheck evaluates only the newer centers
+    uint32_t *m32;
+    uint32_t *stamp;
     int32_t lp_kind;
     int32_t kcap;
     int64_t lo;              // first point of the range in the packed array
@@ -180,7 +185,7 @@ struct GonArgs {
 };
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s);
 // Mixed-precision diagnostics (synchronous): exact rechecks, overflows.
-cudaError_t read_counters(unsigned long long out[4], bool reset);
+cudaError_t read_counters(unsigned long long out[8], bool reset);
 int gon_max_grid(int dtype, int d, int lp = 0);
 int gon_queue_grid(int dtype, int d, int lp = 0);
 int gon_threads();
@@ -208,6 +213,8 @@ inline void gon_single(GonArgs &g, const void *pk, int dtype, int64_t n, int d, 
     I.scale = nullptr;
     I.cenT = nullptr;
     I.ecmax_out = nullptr;
+    I.m32 = nullptr;
+    I.stamp = nullptr;
     I.lp_kind = 0;
     I.kcap = k;
     I.lo = 0;
@@ -250,14 +257,16 @@ __host__ __device__ inline int lp_ngroups(int kind, int d) { return (d + lp_grou
 // [nblocks*ng*BLK], per-point bounds `ept` [nblocks*BLK], per-block maxima
 // `eblk` [nblocks]; fp8 also fills `scale` [ng*4] from the column maxima
 // (`colmax` [d] scratch).
+// stamp ([nblocks(n) * BLK]) is zeroed: the recheck memo starts empty.
 cudaError_t launch_lp_pack(int kind, const float *pk, int64_t n, int d, unsigned *colmax, float *scale, uint32_t *lp,
-                           float *ept, float *eblk, cudaStream_t s);
+                           float *ept, float *eblk, uint32_t *stamp, cudaStream_t s);
 // bf16 copies of many packed arrays (batched form).
 struct LpSeg {
     const float *pk;
     uint32_t *lp;
     float *ept;
     float *eblk;
+    uint32_t *stamp;
     int64_t n;
     int64_t blk0;
     int32_t d;

@@ -13,7 +13,7 @@
 //   e_x >= || decoded(x) - x ||_2
 // sums the exact squared differences with upward rounding.  e_pt holds it
 // per point (used for the centers), e_blk the maximum over each block (used in
-// the sweep).
+// the sweep).  The pack also zeroes the per-point stamp of the recheck memo.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -46,11 +46,13 @@ __device__ __forceinline__ float fp8_scale(const unsigned *colmax, int j) {
 // One block b of BLK points (one thread per point).
 template <int KIND>
 __device__ void lp_pack_block(const float *__restrict__ pk, int64_t n, int d, const unsigned *__restrict__ colmax,
-                              uint32_t *__restrict__ lp, float *__restrict__ ept, float *__restrict__ eblk, int64_t b) {
+                              uint32_t *__restrict__ lp, float *__restrict__ ept, float *__restrict__ eblk,
+                              uint32_t *__restrict__ stamp, int64_t b) {
     constexpr int G = lp_group(KIND);
     const int ng = (d + G - 1) / G;
     {
         const int i = threadIdx.x;
+        stamp[b * BLK + i] = 0u;
         const bool valid = b * BLK + i < n;
         float e2 = 0.f;
         for (int jg = 0; jg < ng; ++jg) {
@@ -102,12 +104,12 @@ template <int KIND>
 __global__ void __launch_bounds__(BLK) lp_pack_kernel(const float *__restrict__ pk, int64_t n, int d,
                                                       const unsigned *__restrict__ colmax, float *__restrict__ scale,
                                                       uint32_t *__restrict__ lp, float *__restrict__ ept,
-                                                      float *__restrict__ eblk) {
+                                                      float *__restrict__ eblk, uint32_t *__restrict__ stamp) {
     constexpr int G = lp_group(KIND);
     const int ng = (d + G - 1) / G;
     if (KIND == KC_SWEEP_FP8 && blockIdx.x == 0)
         for (int j = threadIdx.x; j < ng * G; j += blockDim.x) scale[j] = j < d ? fp8_scale(colmax, j) : 1.f;
-    for (int64_t b = blockIdx.x; b < nblocks(n); b += gridDim.x) lp_pack_block<KIND>(pk, n, d, colmax, lp, ept, eblk, b);
+    for (int64_t b = blockIdx.x; b < nblocks(n); b += gridDim.x) lp_pack_block<KIND>(pk, n, d, colmax, lp, ept, eblk, stamp, b);
 }
 
 // bf16 copies of many packed arrays in one launch (segment s owns blocks
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(BLK) lp_pack_many_kernel(const LpSeg *__restri
             S = segs[lo];
         }
         __syncthreads();
-        lp_pack_block<KC_SWEEP_BF16>(S.pk, S.n, S.d, nullptr, S.lp, S.ept, S.eblk, gb - S.blk0);
+        lp_pack_block<KC_SWEEP_BF16>(S.pk, S.n, S.d, nullptr, S.lp, S.ept, S.eblk, S.stamp, gb - S.blk0);
     }
 }
 
@@ -144,7 +146,7 @@ cudaError_t launch_lp_pack_many(const LpSeg *segs, int nseg, int64_t total_block
 }
 
 cudaError_t launch_lp_pack(int kind, const float *pk, int64_t n, int d, unsigned *colmax, float *scale, uint32_t *lp,
-                           float *ept, float *eblk, cudaStream_t s) {
+                           float *ept, float *eblk, uint32_t *stamp, cudaStream_t s) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -156,10 +158,10 @@ cudaError_t launch_lp_pack(int kind, const float *pk, int64_t n, int d, unsigned
         const int64_t total = nb * (int64_t)d * BLK;
         const int g2 = (int)((total + 255) / 256 < (int64_t)sms * 8 ? (total + 255) / 256 : (int64_t)sms * 8);
         colmax_kernel<<<g2, 256, 0, s>>>(pk, n, d, colmax);
-        lp_pack_kernel<KC_SWEEP_FP8><<<grid, BLK, 0, s>>>(pk, n, d, colmax, scale, lp, ept, eblk);
+        lp_pack_kernel<KC_SWEEP_FP8><<<grid, BLK, 0, s>>>(pk, n, d, colmax, scale, lp, ept, eblk, stamp);
         kernels = 2;
     } else {
-        lp_pack_kernel<KC_SWEEP_BF16><<<grid, BLK, 0, s>>>(pk, n, d, colmax, scale, lp, ept, eblk);
+        lp_pack_kernel<KC_SWEEP_BF16><<<grid, BLK, 0, s>>>(pk, n, d, colmax, scale, lp, ept, eblk, stamp);
     }
     note_launches(kernels);
     return cudaGetLastError();
