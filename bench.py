@@ -70,6 +70,9 @@ def parse():
                     help="the default is the headline line; the others measure the remaining paths")
     ap.add_argument("--sweep", default="f32", choices=["f32", "bf16", "fp8"],
                     help="sweep precision for the GON / MRG / batch workloads")
+    ap.add_argument("--n", type=int, default=0,
+                    help="other workloads: fewer points than the configuration's (small profiling cases)")
+    ap.add_argument("--k", type=int, default=0, help="8M x 64 workloads: another k (small profiling cases)")
     return ap.parse_args()
 
 
@@ -349,6 +352,8 @@ def run_extra(args):
     mind_b = 4 if sw is None else 2          # running minimum: u32, or 16-bit code in the mixed sweep
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     cfg = {"workload": name, "sweep": args.sweep, "l2": "inputs larger than L2"}
+    if args.n:
+        cfg["n_override"] = args.n
     dom, bound, plan = "gonzalez", "hbm", None
     if name == "gon_int_n10000_d2_k10":
         w = I.gon_int_10k()
@@ -357,7 +362,7 @@ def run_extra(args):
         evals, units = k * n, None
         cfg.update(n=n, d=d, k=k, dtype="int32", l2="80 KB input, on chip (latency bound)")
     elif name in ("gon_unif_n10000000_d16_k200", "mrg_unif_n10000000_d16_m64_k200"):
-        pts, off, k = I.mrg_unif_10m()
+        pts, off, k = I.mrg_unif_10m(**({"n": args.n} if args.n else {}))
         n, d = pts.shape
         x, o = dev(pts), dev(off)
         if name.startswith("gon"):
@@ -371,9 +376,9 @@ def run_extra(args):
         units = k * n * (d * bpc + mind_b)
         cfg.update(n=n, d=d, k=k)
     elif name in ("gon_gau_n8000000_d64_k1024", "radius_gau_n8000000_d64_k1024", "eim_gau_n8000000_d64_k1024"):
-        pts = I.eim_gau_8m()
+        pts = I.eim_gau_8m(**({"n": args.n} if args.n else {}))
         n, d = pts.shape
-        k = 1024
+        k = args.k or 1024
         x = dev(pts)
         cfg.update(n=n, d=d, k=k)
         if name.startswith("gon"):

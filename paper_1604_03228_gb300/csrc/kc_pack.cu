@@ -8,21 +8,40 @@ namespace kc {
 
 namespace {
 
-constexpr int PACK_DC = 32;   // coordinates staged per pass through shared memory
+constexpr int PACK_NT = 256;   // threads per CTA
+constexpr int PACK_DC = 64;    // coordinates staged per pass through shared memory
 
 __device__ __forceinline__ uint32_t bias_i32(int32_t v) { return (uint32_t)v ^ 0x80000000u; }
 
-// One CTA of BLK threads handles one block of BLK points at a time: the
-// block's rows (contiguous in the source) are read coalesced into shared
-// memory, then written out coordinate-major, also coalesced.  Rows past n are
-// zero.  Floats are checked for NaN/Inf; int32 coordinates feed the global
-// range [min, max] kept as two order-preserving unsigned maxima:
-// range2[0] = max of ~bias(v) (so min v), range2[1] = max of bias(v).
+// Checks of one source value: floats for NaN/Inf and magnitude, int32 into
+// the running biased range.
 template <typename T>
-__global__ void __launch_bounds__(BLK) pack_kernel(const T *__restrict__ src, int64_t n, int d,
-                                                   T *__restrict__ dst, uint32_t *range2,
-                                                   DevStatus *st) {
-    __shared__ T tile[BLK][PACK_DC + 1];
+__device__ __forceinline__ void pack_check(T v, bool &bad, bool &nonfin, uint32_t &lo, uint32_t &hi) {
+    if constexpr (std::is_same<T, float>::value) {
+        // NaN fails the comparison; |v| <= 2^54 keeps every squared distance
+        // far below FLT_MAX (see the header).
+        if (!(fabsf(v) <= 0x1p54f)) bad = true;
+        if (!isfinite(v)) nonfin = true;
+    } else {
+        const uint32_t bv = bias_i32(v);
+        lo = max(lo, 0xFFFFFFFFu - bv);
+        hi = max(hi, bv);
+    }
+}
+
+// One CTA handles one block of BLK points at a time.  The block's rows are
+// one contiguous span of the source; a pass stages up to PACK_DC coordinates
+// of every row in shared memory (row stride dc + 1, so both phases are free
+// of bank conflicts) and writes them out coordinate-major, coalesced.  When
+// the pass covers whole rows the span is read with 16-byte loads (vec).
+// Rows past n are zero.  Floats are checked for NaN/Inf; int32 coordinates
+// feed the global range [min, max] kept as two order-preserving unsigned
+// maxima: range2[0] = max of ~bias(v) (so min v), range2[1] = max of bias(v).
+template <typename T>
+__global__ void __launch_bounds__(PACK_NT) pack_kernel(const T *__restrict__ src, int64_t n, int d, bool vec,
+                                                       T *__restrict__ dst, uint32_t *range2, DevStatus *st) {
+    using V4 = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
+    __shared__ T tile[BLK * (PACK_DC + 1)];
     const int64_t nb = nblocks(n);
     bool bad = false, nonfin = false;
     uint32_t lo = 0, hi = 0;   // as biased maxima (0 = identity)
@@ -31,29 +50,52 @@ __global__ void __launch_bounds__(BLK) pack_kernel(const T *__restrict__ src, in
         const int rows = (int)((n - p0) < BLK ? (n - p0) : BLK);
         for (int j0 = 0; j0 < d; j0 += PACK_DC) {
             const int dc = (d - j0) < PACK_DC ? (d - j0) : PACK_DC;
+            const int stride = dc + 1;
             __syncthreads();
-            for (int e = threadIdx.x; e < BLK * dc; e += BLK) {
-                const int r = e / dc, jj = e - r * dc;
-                T v = T(0);
-                if (r < rows) {
-                    v = src[(p0 + r) * (int64_t)d + j0 + jj];
-                    if constexpr (std::is_same<T, float>::value) {
-                        // NaN fails the comparison; |v| <= 2^54 keeps every
-                        // squared distance far below FLT_MAX (see the header).
-                        if (!(fabsf(v) <= 0x1p54f)) bad = true;
-                        if (!isfinite(v)) nonfin = true;
-                    } else {
-                        uint32_t bv = bias_i32(v);
-                        lo = max(lo, 0xFFFFFFFFu - bv);
-                        hi = max(hi, bv);
+            if (dc == d) {
+                // whole rows: elements f = r d + j of the span [p0 d, (p0 + rows) d)
+                const T *base = src + p0 * (int64_t)d;
+                const int total = rows * d;
+                const int nv = vec ? total / 4 : 0;
+                for (int q = threadIdx.x; q < nv; q += PACK_NT) {
+                    const V4 w = reinterpret_cast<const V4 *>(base)[q];
+                    const T vv[4] = {w.x, w.y, w.z, w.w};
+                    int f = 4 * q, r = f / d, j = f - r * d;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        pack_check(vv[u], bad, nonfin, lo, hi);
+                        tile[r * stride + j] = vv[u];
+                        if (++j == d) {
+                            j = 0;
+                            ++r;
+                        }
                     }
                 }
-                tile[r][jj] = v;
+                for (int f = 4 * nv + threadIdx.x; f < total; f += PACK_NT) {
+                    const int r = f / d, j = f - r * d;
+                    const T v = base[f];
+                    pack_check(v, bad, nonfin, lo, hi);
+                    tile[r * stride + j] = v;
+                }
+                for (int f = total + threadIdx.x; f < BLK * d; f += PACK_NT) {
+                    const int r = f / d, j = f - r * d;
+                    tile[r * stride + j] = T(0);
+                }
+            } else {
+                for (int e = threadIdx.x; e < BLK * dc; e += PACK_NT) {
+                    const int r = e / dc, j = e - r * dc;
+                    T v = T(0);
+                    if (r < rows) {
+                        v = src[(p0 + r) * (int64_t)d + j0 + j];
+                        pack_check(v, bad, nonfin, lo, hi);
+                    }
+                    tile[r * stride + j] = v;
+                }
             }
             __syncthreads();
-            for (int e = threadIdx.x; e < BLK * dc; e += BLK) {
-                const int jj = e / BLK, r = e - jj * BLK;
-                dst[(b * d + j0 + jj) * BLK + r] = tile[r][jj];
+            for (int e = threadIdx.x; e < BLK * dc; e += PACK_NT) {
+                const int j = e / BLK, r = e - j * BLK;
+                dst[(b * d + j0 + j) * BLK + r] = tile[r * stride + j];
             }
         }
     }
@@ -91,14 +133,15 @@ cudaError_t launch_pack(const void *src, int dtype, int64_t n, int d, void *dst,
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t cap = (int64_t)sms * 16;
+    const int64_t cap = (int64_t)sms * 8;
     const int grid = (int)(nb < cap ? nb : cap);
+    const bool vec = ((uintptr_t)src & 15) == 0;   // a block's span starts at p0 d, a multiple of 128 elements
     if (dtype == KC_F32)
-        pack_kernel<float><<<grid, BLK, 0, s>>>((const float *)src, n, d, (float *)dst,
-                                                (uint32_t *)range2, st);
+        pack_kernel<float><<<grid, PACK_NT, 0, s>>>((const float *)src, n, d, vec, (float *)dst,
+                                                    (uint32_t *)range2, st);
     else
-        pack_kernel<int32_t><<<grid, BLK, 0, s>>>((const int32_t *)src, n, d, (int32_t *)dst,
-                                                  (uint32_t *)range2, st);
+        pack_kernel<int32_t><<<grid, PACK_NT, 0, s>>>((const int32_t *)src, n, d, vec, (int32_t *)dst,
+                                                      (uint32_t *)range2, st);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -160,17 +160,34 @@ __device__ __forceinline__ bool can_reach(const uint32_t *mind, int64_t x, doubl
     return (double)U * (double)U >= thr;
 }
 
-// FP64 minimum over all centers of point x, computed by the whole warp: lane
-// l takes centers l, l+32, ... (each sum in coordinate order), then a warp
-// minimum.  FP64 is slow on this part, so the centers are spread over lanes
-// rather than chained in one thread.
+// FP64 minimum over all centers of point x, computed by the whole warp (lane
+// l takes centers l, l+32, ...).  FP64 is slow on this part, so a canonical
+// FP32 pass goes first: with g the FP32 bound (d+2)u/(1-(d+2)u) and m32 the
+// FP32 minimum, a center whose FP32 value exceeds m32 (1+g)/(1-g) (1+eps64)
+// has an exact distance above the FP32 argmin's by more than FP64's own
+// rounding (eps64 = 4 (d+2) 2^-53), so its FP64 value cannot be the minimum;
+// only the remaining centers (usually one or two) are evaluated in FP64,
+// each sum in coordinate order.
 __device__ double min64_warp(const float *__restrict__ pk, int64_t x, int d,
                              const float *__restrict__ cen, int kc, int lane) {
+    uint32_t m32 = 0xFFFFFFFFu;
+    for (int ci = lane; ci < kc; ci += 32) {
+        float s = 0.f;
+        for (int j = 0; j < d; ++j) s = sq_step(s, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
+        m32 = min(m32, __float_as_uint(s));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m32 = min(m32, __shfl_xor_sync(0xFFFFFFFFu, m32, o));
+    const double g = f32_gamma(d);
+    const double lim = (double)__uint_as_float(m32) * ((1.0 + g) / (1.0 - g)) * (1.0 + 4.0 * (d + 2) * 0x1p-53);
     double m = INFINITY;
     for (int ci = lane; ci < kc; ci += 32) {
-        double s = 0.0;
-        for (int j = 0; j < d; ++j) s = sq_step64(s, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
-        m = fmin(m, s);
+        float s = 0.f;
+        for (int j = 0; j < d; ++j) s = sq_step(s, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
+        if ((double)s > lim) continue;
+        double s64 = 0.0;
+        for (int j = 0; j < d; ++j) s64 = sq_step64(s64, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
+        m = fmin(m, s64);
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) m = fmin(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));

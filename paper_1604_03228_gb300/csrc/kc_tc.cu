@@ -10,16 +10,18 @@
 // per-row |x~|^2 and error bound e_x = ||x~ - 2^e x|| (FP32, rounded up).
 //
 // Kernel.  One persistent CTA per SM (it holds all 512 TMEM columns).  Warps:
-//   8    producer: cp.async.bulk of point tiles (2-stage ring) and center
-//        tiles (2-stage ring) into shared memory
+//   8    producer: cp.async.bulk of point tiles (2-stage ring), center tiles
+//        (2-stage ring) and each center tile's negated norms (a 2-stage ring
+//        tied to the accumulator stages) into shared memory
 //   9    MMA issuer (one thread): tcgen05.mma.kind::f16, M=128 x N=256,
 //        Kp/16 instructions per tile pair, FP32 accumulators double-buffered
 //        in TMEM (2 x 256 columns)
 //   0-7  epilogue: warps w and w+4 own point rows 32(w%4).. (their TMEM
-//        lanes) and split the 256 columns; per (point, center) they form
-//        v = 2 x~.c~ - |c~|^2 (one FMA) and keep its maximum (radius) or
-//        compare it with the point's two decision limits (prune), since
-//        s~ = |x~|^2 - v approximates ||x~ - c~||^2.
+//        lanes) and split the 256 columns; each thread software-pipelines its
+//        32-column TMEM loads and forms v = 2 x~.c~ - |c~|^2 two columns per
+//        packed FMA, folding v into a running maximum three values at a time
+//        (radius) or comparing it with the point's two decision limits
+//        (prune), since s~ = |x~|^2 - v approximates ||x~ - c~||^2.
 // Shared-memory operand layout: no swizzle, K-major, 8 x 16-byte core
 // matrices; core matrix (row block mi, column block ki) of an R-row tile at
 // byte ((ki * R/8) + mi) * 128: the descriptor's leading (K) byte offset is
@@ -47,8 +49,16 @@ namespace {
 
 constexpr int TC_M = 128;
 constexpr int TC_N = 256;
-constexpr int TC_THREADS = 320;   // warps 0-7 epilogue, 8 producer, 9 MMA
-constexpr int TC_EPI = 256;
+// 8 epilogue warps: with the producer and MMA warps the CTA has 10, at most 3
+// per SM sub-partition, which leaves up to 168 registers per thread.
+constexpr int TC_EPI_WARPS = 8;                     // epilogue warps 0-7
+constexpr int TC_GROUPS = TC_EPI_WARPS / 4;          // column groups per accumulator row
+constexpr int TC_COLS = TC_N / TC_GROUPS;            // columns of a tile per epilogue thread
+constexpr int TC_PROD = TC_EPI_WARPS;                // producer warp
+constexpr int TC_MMA = TC_EPI_WARPS + 1;             // MMA warp
+constexpr int TC_THREADS = (TC_EPI_WARPS + 2) * 32;
+constexpr int TC_EPI = TC_EPI_WARPS * 32;
+static_assert(TC_COLS % 32 == 0, "whole 32-column TMEM loads");
 constexpr int TC_KMAX = 128;
 constexpr long long TC_SPIN = 1ll << 32;   // wait budget in clock cycles (about two seconds)
 
@@ -112,8 +122,9 @@ __device__ __forceinline__ void umma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// 32 consecutive accumulator columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
+// 32 consecutive accumulator columns of this thread's TMEM lane; the
+// registers are valid after tmem_wait_ld on them.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -122,7 +133,34 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
           "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
           "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// Wait for this thread's outstanding TMEM loads; r is named as read and
+// written so that no use of it moves above the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// v = 2 acc - |c|^2 for two accumulator columns at once (c2n holds the
+// negated norms), each lane rounded like fma(2, acc, -|c|^2).
+__device__ __forceinline__ void fma2_acc(uint32_t r0, uint32_t r1, float2 c2n, float &v0, float &v1) {
+    unsigned long long a, c, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "r"(r0), "r"(r1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(c2n.x), "f"(c2n.y));
+    const unsigned long long two = 0x4000000040000000ull;   // (2.0f, 2.0f)
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(two), "l"(c));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v0), "=f"(v1) : "l"(d));
+}
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 // Element offset of (row r, coordinate k) in an R-row no-swizzle K-major tile.
@@ -154,7 +192,9 @@ __global__ void tc_absmax_kernel(const float *__restrict__ pk, int64_t n, int d,
 // packed array (pk) when pk != null, else row idx ? idx[i] : i of the
 // row-major array rm.  Rows past the count are zero with norm +inf (they
 // never win a minimum or pass a threshold).  maxes (optional) gets the
-// largest e and the largest norm.
+// largest e and the largest norm.  Center tiles (R = TC_N) store the norm
+// negated (-inf past the count), the form the epilogue's fused multiply-add
+// takes.
 template <int R>
 __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__restrict__ rm,
                                const uint32_t *__restrict__ idx, const int32_t *cnt_dev, int64_t cnt_max, int d,
@@ -171,18 +211,32 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
         int64_t g = 0;
         if (valid) g = pk ? i : (idx ? (int64_t)idx[i] : i);
         float nrm = 0.f, e2 = 0.f;
-        for (int k = 0; k < kp; ++k) {
-            float x = 0.f;
-            if (valid && k < d) x = __fmul_rn(pk ? pk[pk_index(g, k, d)] : rm[g * d + k], sc);   // exact
-            const __half q = __float2half_rn(x);
-            const float xq = __half2float(q);
-            const float df = fabsf(__fsub_rn(x, xq));   // exact (Sterbenz) or x itself
-            e2 = __fmaf_ru(df, df, e2);
-            nrm = __fmaf_rn(xq, xq, nrm);
-            tile[core_off(R, r, k)] = q;
+        // one 16-byte core-matrix row (8 coordinates) per store; consecutive
+        // rows of a warp store consecutive 16-byte chunks
+        for (int k0 = 0; k0 < kp; k0 += 8) {
+            uint32_t w[4];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                __half q2[2];
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const int k = k0 + u + v;
+                    float x = 0.f;
+                    if (valid && k < d) x = __fmul_rn(pk ? pk[pk_index(g, k, d)] : rm[g * d + k], sc);   // exact
+                    const __half q = __float2half_rn(x);
+                    const float xq = __half2float(q);
+                    const float df = fabsf(__fsub_rn(x, xq));   // exact (Sterbenz) or x itself
+                    e2 = __fmaf_ru(df, df, e2);
+                    nrm = __fmaf_rn(xq, xq, nrm);
+                    q2[v] = q;
+                }
+                w[u / 2] = (uint32_t)__half_as_ushort(q2[0]) | ((uint32_t)__half_as_ushort(q2[1]) << 16);
+            }
+            *reinterpret_cast<uint4 *>(tile + core_off(R, r, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         const float e = __fsqrt_ru(e2);
-        norm[i] = valid ? nrm : INFINITY;
+        const float nv = valid ? nrm : INFINITY;
+        norm[i] = R == TC_N ? -nv : nv;
         err[i] = valid ? e : 0.f;
         if (maxes && valid) {
             atomicMax(&maxes[0], __float_as_uint(e));
@@ -229,14 +283,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int kp = a.kp;
     const uint32_t a_bytes = (uint32_t)TC_M * kp * 2, b_bytes = (uint32_t)TC_N * kp * 2;
-    // point tiles at smem + stage * a_bytes, center tiles after them
+    // point tiles at smem + stage * a_bytes, center tiles after them, then
+    // the negated center norms of the two accumulator stages
     unsigned char *const sAb = smem, *const sBb = smem + 2 * a_bytes;
-    __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], t_full[2], t_empty[2];
+    float *const sCn = reinterpret_cast<float *>(smem + 2 * a_bytes + 2 * b_bytes);
+    __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], t_full[2], t_empty[2], c_full[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
-    __shared__ float s_part[TC_M];
+    __shared__ float s_part[TC_GROUPS][TC_M];
     __shared__ int s_gone[TC_M];   // prune: the row is surely within the threshold
-    __shared__ int s_pend[TC_M];   // prune: the row's other half deferred pairs (bit 0) or overflowed (bit 1)
+    __shared__ int s_pend[TC_M];   // prune: another group deferred pairs (bit 0) or overflowed (bit 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t ntile_pts = (a.npts + TC_M - 1) / TC_M;
     volatile int *abort = &s_abort;
@@ -249,6 +305,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
             mbar_init(&b_empty[s], 1);
             mbar_init(&t_full[s], 1);
             mbar_init(&t_empty[s], TC_EPI);
+            mbar_init(&c_full[s], 1);
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -267,52 +324,62 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
 
-    if (warp == 8) {
+    if (warp == TC_PROD) {
         // ------------------------------------------------ producer
         if (lane == 0) {
-            uint32_t afill[2] = {0, 0}, bfill[2] = {0, 0};
+            uint32_t afill = 0, bfill = 0, cfill = 0;   // bit s: parity of stage s's fills so far
             int64_t u = 0, p = 0;
             for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x, ++p) {
                 const int sa = (int)(p & 1);
-                if (!mbar_wait(&a_empty[sa], (afill[sa] & 1u) ^ 1u, abort)) {
+                if (!mbar_wait(&a_empty[sa], ((afill >> sa) & 1u) ^ 1u, abort)) {
                     *abort = 1;
                     set_status(a.st, KC_ERR_TIMEOUT, 6, 0);
                     break;
                 }
                 mbar_expect_tx(&a_full[sa], a_bytes);
                 bulk_g2s(sAb + sa * a_bytes, a.at + pt * (int64_t)TC_M * kp, a_bytes, &a_full[sa]);
-                ++afill[sa];
+                afill ^= 1u << sa;
                 for (int t = 0; t < a.ntiles; ++t, ++u) {
                     const int s = (int)(u & 1);
-                    if (!mbar_wait(&b_empty[s], (bfill[s] & 1u) ^ 1u, abort)) {
+                    if (!mbar_wait(&b_empty[s], ((bfill >> s) & 1u) ^ 1u, abort)) {
                         *abort = 1;
                         set_status(a.st, KC_ERR_TIMEOUT, 6, t);
                         break;
                     }
                     mbar_expect_tx(&b_full[s], b_bytes);
                     bulk_g2s(sBb + s * b_bytes, a.bt + (int64_t)t * TC_N * kp, b_bytes, &b_full[s]);
-                    ++bfill[s];
+                    bfill ^= 1u << s;
+                    // the norms of tile u go to ring stage s once the epilogue
+                    // has released that stage (tile u - 2)
+                    if (!mbar_wait(&t_empty[s], ((cfill >> s) & 1u) ^ 1u, abort)) {
+                        *abort = 1;
+                        set_status(a.st, KC_ERR_TIMEOUT, 6, t);
+                        break;
+                    }
+                    mbar_expect_tx(&c_full[s], TC_N * 4);
+                    bulk_g2s(sCn + s * TC_N, a.cn + (int64_t)t * TC_N, TC_N * 4, &c_full[s]);
+                    cfill ^= 1u << s;
                 }
             }
         }
-    } else if (warp == 9) {
+    } else if (warp == TC_MMA) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = umma_idesc_f16(TC_M, TC_N);
             const uint32_t a_lbo = (TC_M / 8) * 128, b_lbo = (TC_N / 8) * 128;
-            uint32_t ause[2] = {0, 0}, buse[2] = {0, 0}, tuse[2] = {0, 0};
+            uint32_t ause = 0, buse = 0, tuse = 0;   // bit s: parity of stage s's uses so far
             int64_t u = 0, p = 0;
             for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x, ++p) {
                 const int sa = (int)(p & 1);
-                if (!mbar_wait(&a_full[sa], ause[sa] & 1u, abort)) {
+                if (!mbar_wait(&a_full[sa], (ause >> sa) & 1u, abort)) {
                     *abort = 1;
                     set_status(a.st, KC_ERR_TIMEOUT, 7, 0);
                     break;
                 }
                 for (int t = 0; t < a.ntiles; ++t, ++u) {
                     const int s = (int)(u & 1);
-                    if (!mbar_wait(&t_empty[s], (tuse[s] & 1u) ^ 1u, abort) ||
-                        !mbar_wait(&b_full[s], buse[s] & 1u, abort)) {
+                    if (!mbar_wait(&t_empty[s], ((tuse >> s) & 1u) ^ 1u, abort) ||
+                        !mbar_wait(&b_full[s], (buse >> s) & 1u, abort)) {
                         *abort = 1;
                         set_status(a.st, KC_ERR_TIMEOUT, 8, t);
                         break;
@@ -326,17 +393,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                     }
                     umma_commit(&b_empty[s]);
                     umma_commit(&t_full[s]);
-                    ++buse[s];
-                    ++tuse[s];
+                    buse ^= 1u << s;
+                    tuse ^= 1u << s;
                 }
                 umma_commit(&a_empty[sa]);
-                ++ause[sa];
+                ause ^= 1u << sa;
             }
         }
     } else {
-        // ------------------------------------------------ epilogue warps 0-7
+        // ------------------------------------------------ epilogue warps
+        // warp w reads TMEM lanes 32 (w % 4) .. (its accumulator rows) and
+        // the columns of group w / 4; each thread owns one row and TC_COLS
+        // columns of every tile
         const int row = (warp & 3) * 32 + lane;
-        const int half = warp >> 2;
+        const int grp = warp >> 2;
         const float sc = tc_scale(a.absmax);
         const float sc2 = sc * sc;                  // exact power of two
         const float isc2 = 1.f / sc2;               // exact power of two
@@ -344,7 +414,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
         const float g = lp_slack(a.d);
         const float E = __uint_as_float(a.maxes[0]);
         const float cnmax = __uint_as_float(a.maxes[1]);
-        uint32_t tuse[2] = {0, 0};
+        uint32_t tuse = 0;   // bit s: parity of TMEM stage s's uses so far
         int64_t u = 0;
         for (int64_t pt = blockIdx.x; pt < ntile_pts; pt += gridDim.x) {
             const int64_t pi = pt * TC_M + row;
@@ -372,88 +442,115 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
             unsigned long long namb = 0;
             bool emitted = false, ovf = false;
             volatile int *s_gone_v = s_gone;
+            int cbase = 0;
+            const float *cns = sCn;   // negated norms of the current tile's columns (shared memory)
+            // One 32-column chunk of accumulators (columns cbase + c0 ..):
+            // v = 2 acc - |c|^2, two columns per packed FMA, folded into the
+            // running maxima three values at a time.
+            auto chunk = [&](const uint32_t(&r)[32], int c0) {
+                const float4 *cn4 = reinterpret_cast<const float4 *>(cns + c0);
+                if (MODE == 0) {
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 c = cn4[j / 4];
+                        float a0, a1, a2, a3;
+                        fma2_acc(r[j], r[j + 1], make_float2(c.x, c.y), a0, a1);
+                        fma2_acc(r[j + 2], r[j + 3], make_float2(c.z, c.w), a2, a3);
+                        if ((j & 4) == 0) {
+                            v0 = max3f(v0, a0, a1);
+                            v1 = max3f(v1, a2, a3);
+                        } else {
+                            v2 = max3f(v2, a0, a1);
+                            v3 = max3f(v3, a2, a3);
+                        }
+                    }
+                } else if (!removed) {
+                    // fast pass: the chunk's largest v; only a chunk that can
+                    // hold a pair within the threshold is rescanned
+                    float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+                    for (int j = 0; j < 32; j += 4) {
+                        const float4 c = cn4[j / 4];
+                        float a0, a1, a2, a3;
+                        fma2_acc(r[j], r[j + 1], make_float2(c.x, c.y), a0, a1);
+                        fma2_acc(r[j + 2], r[j + 3], make_float2(c.z, c.w), a2, a3);
+                        m0 = max3f(m0, a0, a1);
+                        m1 = max3f(m1, a2, a3);
+                    }
+                    if (fmaxf(m0, m1) >= vhi) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float v = __fmaf_rn(2.f, __uint_as_float(r[j]), cns[c0 + j]);
+                            if (v >= vhi && !removed) {
+                                if (v >= vlo) {
+                                    removed = true;
+                                } else if (!ovf) {
+                                    // undecided: deferred to the exact pair check
+                                    const int64_t ci = (int64_t)cbase + c0 + j;
+                                    if (ci < a.kc) {
+                                        const unsigned long long slot = atomicAdd(a.npairs, 1ull);
+                                        if (slot < (unsigned long long)a.pcap)
+                                            a.pairs[slot] = make_uint2((uint32_t)pi, (uint32_t)ci);
+                                        else
+                                            ovf = true;
+                                        emitted = true;
+                                        ++namb;
+                                    }
+                                }
+                            }
+                        }
+                        if (removed) s_gone_v[row] = 1;
+                    }
+                }
+            };
             for (int t = 0; t < a.ntiles; ++t, ++u) {
                 const int s = (int)(u & 1);
-                if (!mbar_wait(&t_full[s], tuse[s] & 1u, abort)) {
+                if (!mbar_wait(&t_full[s], (tuse >> s) & 1u, abort) || !mbar_wait(&c_full[s], (tuse >> s) & 1u, abort)) {
                     set_status(a.st, KC_ERR_TIMEOUT, 10, t);
                     *abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int cbase = t * TC_N + half * (TC_N / 2);
-                const float4 *cn4 = reinterpret_cast<const float4 *>(a.cn + cbase);
-                if (MODE == 1 && !removed && s_gone_v[row]) removed = true;   // the other half decided
-                for (int c0 = 0; c0 < TC_N / 2; c0 += 32) {
-                    if (MODE == 1 && __all_sync(0xFFFFFFFFu, removed)) break;   // nothing left to read
-                    uint32_t r[32];
-                    tmem_ld32(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(s * TC_N + half * (TC_N / 2) + c0),
-                              r);
-                    if (MODE == 0) {
+                cbase = t * TC_N + grp * TC_COLS;
+                cns = sCn + s * TC_N + grp * TC_COLS;
+                if (MODE == 1 && !removed && s_gone_v[row]) removed = true;   // another group decided
+                if (MODE == 0 || !__all_sync(0xFFFFFFFFu, removed)) {
+                    // the next chunk's TMEM load is in flight while this one is used
+                    const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(s * TC_N + grp * TC_COLS);
+                    uint32_t ra[32], rb[32];
+                    tmem_ld32(taddr, ra);
+                    tmem_wait_ld(ra);
 #pragma unroll
-                        for (int j = 0; j < 32; j += 4) {
-                            const float4 c = __ldg(cn4 + (c0 + j) / 4);
-                            v0 = fmaxf(v0, __fmaf_rn(2.f, __uint_as_float(r[j]), -c.x));
-                            v1 = fmaxf(v1, __fmaf_rn(2.f, __uint_as_float(r[j + 1]), -c.y));
-                            v2 = fmaxf(v2, __fmaf_rn(2.f, __uint_as_float(r[j + 2]), -c.z));
-                            v3 = fmaxf(v3, __fmaf_rn(2.f, __uint_as_float(r[j + 3]), -c.w));
-                        }
-                    } else if (!removed) {
-                        // fast pass: the chunk's largest v; only a chunk that
-                        // can hold a pair within the threshold is rescanned
-                        float m = -INFINITY;
-#pragma unroll
-                        for (int j = 0; j < 32; j += 4) {
-                            const float4 c = __ldg(cn4 + (c0 + j) / 4);
-                            m = fmaxf(m, fmaxf(fmaxf(__fmaf_rn(2.f, __uint_as_float(r[j]), -c.x),
-                                                     __fmaf_rn(2.f, __uint_as_float(r[j + 1]), -c.y)),
-                                               fmaxf(__fmaf_rn(2.f, __uint_as_float(r[j + 2]), -c.z),
-                                                     __fmaf_rn(2.f, __uint_as_float(r[j + 3]), -c.w))));
-                        }
-                        if (m >= vhi) {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const float v = __fmaf_rn(2.f, __uint_as_float(r[j]), -__ldg(a.cn + cbase + c0 + j));
-                                if (v >= vhi && !removed) {
-                                    if (v >= vlo) {
-                                        removed = true;
-                                    } else if (!ovf) {
-                                        // undecided: deferred to the exact pair check
-                                        const int64_t ci = (int64_t)cbase + c0 + j;
-                                        if (ci < a.kc) {
-                                            const unsigned long long slot = atomicAdd(a.npairs, 1ull);
-                                            if (slot < (unsigned long long)a.pcap)
-                                                a.pairs[slot] = make_uint2((uint32_t)pi, (uint32_t)ci);
-                                            else
-                                                ovf = true;
-                                            emitted = true;
-                                            ++namb;
-                                        }
-                                    }
-                                }
-                            }
-                            if (removed) s_gone_v[row] = 1;
-                        }
+                    for (int c0 = 0; c0 < TC_COLS; c0 += 64) {
+                        tmem_ld32(taddr + c0 + 32, rb);
+                        chunk(ra, c0);
+                        tmem_wait_ld(rb);
+                        if (c0 + 64 < TC_COLS) tmem_ld32(taddr + c0 + 64, ra);
+                        chunk(rb, c0 + 32);
+                        if (c0 + 64 < TC_COLS) tmem_wait_ld(ra);
                     }
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(&t_empty[s]);
-                ++tuse[s];
+                tuse ^= 1u << s;
             }
-            // combine the two column halves of every row
+            // combine the column groups of every row in group 0
             const float vmax = fmaxf(fmaxf(v0, v1), fmaxf(v2, v3));
-            if (half == 1) {
-                s_part[row] = vmax;
+            if (grp > 0) {
+                if (MODE == 0) s_part[grp][row] = vmax;
                 if (MODE == 1) {
                     if (removed) s_gone[row] = 1;
-                    s_pend[row] = (emitted ? 1 : 0) | (ovf ? 2 : 0);
+                    if (emitted || ovf) atomicOr(&s_pend[row], (emitted ? 1 : 0) | (ovf ? 2 : 0));
                 }
             }
             asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory");
-            if (half == 0 && valid) {
+            if (grp == 0 && valid) {
                 if (MODE == 0) {
                     // min over centers of s~ = xn - max v, then bounds on the
                     // canonical FP32 minimum (scaled units), then unscaled
-                    const float vm = fmaxf(vmax, s_part[row]);
+                    float vm = vmax;
+#pragma unroll
+                    for (int q = 1; q < TC_GROUPS; ++q) vm = fmaxf(vm, s_part[q][row]);
                     const float mm_hi = __fsub_ru(xn, vm), mm_lo = __fsub_rd(xn, vm);
                     const float lo_r = __fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(mm_lo, eps), 0.f)), sl);
                     const float lo = lo_r > 0.f ? __fmul_rd(__fmul_rd(lo_r, lo_r), __fsub_rd(1.f, g)) : 0.f;
@@ -474,12 +571,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                     }
                 }
             }
-            if (MODE == 1 && half == 0) {
+            if (MODE == 1 && grp == 0) {
                 s_gone[row] = 0;
                 s_pend[row] = 0;
             }
             if (MODE == 1 && namb) atomicAdd(&g_tc_counters[0], namb);
-            if (MODE == 1 && half == 0 && valid) atomicAdd(&g_tc_counters[1], 1ull);
+            if (MODE == 1 && grp == 0 && valid) atomicAdd(&g_tc_counters[1], 1ull);
             asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory");   // s_* reused by the next tile
         }
     }
@@ -603,10 +700,11 @@ int sms() {
 
 int kpad(int d) { return (d + 15) / 16 * 16; }
 
-// Dynamic shared memory: two point tiles and two center tiles, and at least
+// Dynamic shared memory: two point tiles, two center tiles and two stages of
+// center norms, and at least
 // 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM.
 size_t tc_smem(int kp) {
-    const size_t need = (size_t)2 * TC_M * kp * 2 + (size_t)2 * TC_N * kp * 2;
+    const size_t need = (size_t)2 * TC_M * kp * 2 + (size_t)2 * TC_N * kp * 2 + (size_t)2 * TC_N * 4;
     return need > 120 * 1024 ? need : 120 * 1024;
 }
 
