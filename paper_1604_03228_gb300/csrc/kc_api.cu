@@ -524,7 +524,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         unsigned long long *arg64 = cv.take<unsigned long long>(1);
         // per (step, CTA): argmax keys, and for the mixed-precision sweep the
         // CTAs' lower bounds too
-        uint64_t *slots = cv.take<uint64_t>((size_t)keff * grid * (lp ? 2 : 1));
+        uint64_t *slots = cv.take<uint64_t>((size_t)slot_words(keff, grid, lp != 0));
         *zero_bytes = cv.off;
         *staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
         void *pk = cv.take<char>((size_t)nb * BLK * d * esz);
@@ -794,7 +794,7 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
             }
         }
         for (int i = 0; i < m; ++i)
-            slot_off[i + 1] = slot_off[i] + (queue1 ? 0 : (int64_t)ki[i] * G[i] * (lp ? 2 : 1));
+            slot_off[i + 1] = slot_off[i] + (queue1 ? 0 : slot_words(ki[i], G[i], lp != 0));
     }
     int grid1 = 0;
     for (int i = 0; i < m; ++i) grid1 += G[i];
@@ -836,7 +836,7 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         Lo.nU = cv.take<int64_t>(1);
         Lo.counter = cv.take<int>(1);
         Lo.slots1 = cv.take<uint64_t>((size_t)std::max<int64_t>(1, slot_off[m]));
-        Lo.slots2 = cv.take<uint64_t>((size_t)k * G2);
+        Lo.slots2 = cv.take<uint64_t>((size_t)slot_words(k, G2, false));
         Lo.zero_bytes = cv.off;
         Lo.staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
         Lo.pk = cv.take<char>((size_t)nb * BLK * d * esz);
@@ -1063,7 +1063,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         Lo.thr = cv.take<uint32_t>(1);
         Lo.v = cv.take<uint32_t>(1);
         Lo.fk = cv.take<uint64_t>(1);
-        Lo.slots = cv.take<uint64_t>((size_t)keff_max * grid * (lp ? 2 : 1));
+        Lo.slots = cv.take<uint64_t>((size_t)slot_words(keff_max, grid, lp != 0));
         Lo.mask = cv.take<uint8_t>((size_t)n);
         Lo.zero_bytes = cv.off;
         Lo.staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
@@ -1422,7 +1422,7 @@ void batch_layout(Carve &cv, const BatchShape &b, BatchBufs &B, const int64_t *n
     for (int i = 0; i < count; ++i) B.per[i].range2 = cv.take<int32_t>(2);
     for (int q = 0; q < b.nheavy; ++q) {
         const int i = b.order[q];
-        B.per[i].slots = cv.take<uint64_t>((size_t)std::min<int64_t>(k[i], n[i]) * b.G[q] * (b.lp ? 2 : 1));
+        B.per[i].slots = cv.take<uint64_t>((size_t)slot_words(std::min<int64_t>(k[i], n[i]), b.G[q], b.lp != 0));
     }
     B.zero_bytes = cv.off;
     B.kout_dev = dev_kout ? k_out : cv.take<int32_t>((size_t)count);

@@ -77,6 +77,9 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
 __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+__device__ __forceinline__ void ld_relaxed_u64x2(const uint64_t *p, uint64_t &a, uint64_t &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
 
 template <typename T, int DC>
 __device__ __forceinline__ void dist4(const T *__restrict__ blk, int d, const T *cs, int lane,
@@ -164,28 +167,36 @@ __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__
     return best;
 }
 
-// Warp 0: wait for all G slots of this step and return their maximum.
-__device__ uint64_t poll_slots(const uint64_t *slots, int G, long long timeout, DevStatus *st,
-                               int step, bool *abort_out) {
+// Warp 0: wait for all G slots of one step (a row starting on 16 bytes) and
+// return their maximum.  Lane l polls slot pairs l, l + 32, ... with 16-byte
+// relaxed loads (all of its pending pairs in flight at once), bounded by the
+// cycle budget.
+__device__ uint64_t poll_slots(const uint64_t *slots, int G, long long timeout, DevStatus *st, int step,
+                               bool *abort_out) {
     const int lane = threadIdx.x & 31;
+    const int P = (G + 1) >> 1;   // pairs; the second word of the last pair is padding when G is odd
     uint64_t g = 0;
     bool ab = false;
-    for (int s0 = 0; s0 < G && !ab; s0 += 128) {
-        uint64_t v[4];
+    for (int p0 = 0; p0 < P && !ab; p0 += 64) {
         unsigned pend = 0;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (s0 + q * 32 + lane < G) pend |= 1u << q;
+        for (int q = 0; q < 2; ++q)
+            if (p0 + q * 32 + lane < P) pend |= 1u << q;
         const long long t0 = clock64();
         while (pend) {
+            uint64_t v[2][2];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (pend >> q & 1u) v[q] = ld_relaxed_u64(slots + s0 + q * 32 + lane);
+            for (int q = 0; q < 2; ++q)
+                if (pend >> q & 1u) ld_relaxed_u64x2(slots + 2 * (p0 + q * 32 + lane), v[q][0], v[q][1]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if ((pend >> q & 1u) && v[q] != 0) {
-                    g = umax64(g, v[q]);
-                    pend &= ~(1u << q);
+            for (int q = 0; q < 2; ++q)
+                if (pend >> q & 1u) {
+                    const int s1 = 2 * (p0 + q * 32 + lane) + 1;
+                    if (v[q][0] != 0 && (s1 >= G || v[q][1] != 0)) {
+                        g = umax64(g, v[q][0]);
+                        if (s1 < G) g = umax64(g, v[q][1]);
+                        pend &= ~(1u << q);
+                    }
                 }
             if (pend && (clock64() - t0 > timeout || ld_volatile_i32(&st->code) != 0)) {
                 set_status(st, KC_ERR_TIMEOUT, 3, step);
@@ -239,8 +250,9 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
             uint64_t g = v;
             bool ab = false;
             if (G > 1) {
-                if (lane == 0) st_relaxed_u64(&I.slots[(int64_t)it * G + r], v ? v : 1);
-                g = poll_slots(I.slots + (int64_t)it * G, G, timeout, st, it, &ab);
+                const int64_t row = (int64_t)it * slot_stride(G);
+                if (lane == 0) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
+                g = poll_slots(I.slots + row, G, timeout, st, it, &ab);
             }
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {
                 const int64_t c = key_idx(g);
@@ -621,7 +633,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             // candidates reaching it are rechecked (slots [k G, 2 k G)).
             if (warp == 0) {
                 bool ab = false;
-                uint64_t *ts = I.slots + (int64_t)I.k * G + (int64_t)it * G;
+                uint64_t *ts = I.slots + ((int64_t)I.k + it) * slot_stride(G);
                 if (lane == 0) st_relaxed_u64(ts + r, enc_bound(T));
                 const uint64_t tg = poll_slots(ts, G, timeout, st, it, &ab);
                 if (lane == 0) {
@@ -692,8 +704,9 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             uint64_t g = v;
             bool ab = false;
             if (G > 1) {
-                if (lane == 0) st_relaxed_u64(&I.slots[(int64_t)it * G + r], v ? v : 1);
-                g = poll_slots(I.slots + (int64_t)it * G, G, timeout, st, it, &ab);
+                const int64_t row = (int64_t)it * slot_stride(G);
+                if (lane == 0) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
+                g = poll_slots(I.slots + row, G, timeout, st, it, &ab);
             }
             if (lane == 0) sh.Lcta = 0u;   // next step's admission bound starts over
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {
@@ -933,22 +946,30 @@ static size_t smem_for(int dtype, int lp, int dmax, bool queue) {
     return (size_t)(dmax > 0 ? dmax : 1) * 4;
 }
 
+// Occupancy of a GON kernel with its dynamic shared memory (opted in first
+// when above the default 48 KB).
+static int gon_occupancy(void *fn, int nt, size_t smem) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, nt, smem) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 0;
+    }
+    return occ;
+}
+
 int gon_max_grid(int dtype, int d, int lp) {
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_fn(dtype, lp, d, false), GROUP_NT,
-                                                  smem_for(dtype, lp, d, false));
-    return occ * sms;
+    return gon_occupancy(pick_fn(dtype, lp, d, false), GROUP_NT, smem_for(dtype, lp, d, false)) * sms;
 }
 
 int gon_queue_grid(int dtype, int d, int lp) {
-    int dev = 0, sms = 0, occ = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pick_fn(dtype, lp, d, true), QUEUE_NT,
-                                                  smem_for(dtype, lp, d, true));
-    return occ * sms;
+    return gon_occupancy(pick_fn(dtype, lp, d, true), QUEUE_NT, smem_for(dtype, lp, d, true)) * sms;
 }
 
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s) {

@@ -151,7 +151,7 @@ extern "C" kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, 
     const size_t o_status = b.take(sizeof(DevStatus));
     const size_t o_range = b.take(2 * sizeof(int32_t));
     const size_t o_key32 = b.take(8), o_max64 = b.take(8), o_arg64 = b.take(8);
-    const size_t o_slots = b.take((size_t)keff * grid * 8);
+    const size_t o_slots = b.take((size_t)slot_words(keff, grid, false) * 8);
     const size_t zero_bytes = b.off;
     const size_t o_pk = b.take((size_t)nb * BLK * d * 4);
     const size_t o_mind = b.take((size_t)nb * BLK * 4);
