@@ -335,7 +335,7 @@ void take_tc(Carve &cv, RadiusArgs &ra, int dtype, int64_t n, int d, int kc) {
     ra.tc_bt = cv.take<char>(tc_center_bytes(kc, d));
     ra.tc_cn = cv.take<float>((size_t)tc_center_tiles(kc) * 256);
     ra.tc_ce = cv.take<float>((size_t)tc_center_tiles(kc) * 256);
-    ra.tc_maxes = cv.take<unsigned>(2);
+    ra.tc_maxes = cv.take<unsigned>(3);
     ra.tc_absmax = cv.take<unsigned>(1);
     ra.tc_mlo = cv.take<float>((size_t)n);
     ra.tc_mhi = cv.take<float>((size_t)n);
@@ -1099,7 +1099,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
             Ptc.tc_bt = cv.take<char>(tc_center_bytes(n, d));
             Ptc.tc_cn = cv.take<float>((size_t)tc_center_tiles(n) * 256);
             Ptc.tc_ce = cv.take<float>((size_t)tc_center_tiles(n) * 256);
-            Ptc.tc_maxes = cv.take<unsigned>(2);
+            Ptc.tc_maxes = cv.take<unsigned>(3);
             Ptc.tc_absmax = cv.take<unsigned>(1);
         }
         Lo.pb = PruneBufs{};

@@ -4,21 +4,17 @@
 // radius recheck.
 #include <type_traits>
 
-#include "kc_internal.cuh"
+#include "kc_pack.cuh"
 
 namespace kc {
 
 namespace {
 
-constexpr int PM_DC = 32;
-
-__device__ __forceinline__ uint32_t bias_i32(int32_t v) { return (uint32_t)v ^ 0x80000000u; }
-
 // Pack many row-major arrays: segment s covers blocks [blk0[s], blk0[s+1]).
 template <typename T>
-__global__ void __launch_bounds__(BLK) pack_many_kernel(const PackSeg *__restrict__ segs, int nseg,
-                                                        int64_t total_blocks, DevStatus *st) {
-    __shared__ T tile[BLK][PM_DC + 1];
+__global__ void __launch_bounds__(PACK_NT) pack_many_kernel(const PackSeg *__restrict__ segs, int nseg,
+                                                            int64_t total_blocks, DevStatus *st) {
+    __shared__ T tile[BLK * (PACK_DC + 1)];
     __shared__ PackSeg S;
     __shared__ int s_seg;
     for (int64_t gb = blockIdx.x; gb < total_blocks; gb += gridDim.x) {
@@ -34,39 +30,10 @@ __global__ void __launch_bounds__(BLK) pack_many_kernel(const PackSeg *__restric
             S = segs[lo];
         }
         __syncthreads();
-        const T *src = (const T *)S.src;
-        T *dst = (T *)S.dst;
-        const int d = S.d;
-        const int64_t b = gb - S.blk0;
-        const int64_t p0 = b * BLK;
-        const int rows = (int)((S.n - p0) < BLK ? (S.n - p0) : BLK);
         bool bad = false, nonfin = false;
         uint32_t lo_b = 0, hi_b = 0;
-        for (int j0 = 0; j0 < d; j0 += PM_DC) {
-            const int dc = (d - j0) < PM_DC ? (d - j0) : PM_DC;
-            __syncthreads();
-            for (int e = threadIdx.x; e < BLK * dc; e += BLK) {
-                const int r = e / dc, jj = e - r * dc;
-                T v = T(0);
-                if (r < rows) {
-                    v = src[(p0 + r) * (int64_t)d + j0 + jj];
-                    if constexpr (std::is_same<T, float>::value) {
-                        if (!(fabsf(v) <= 0x1p54f)) bad = true;
-                        if (!isfinite(v)) nonfin = true;
-                    } else {
-                        const uint32_t bv = bias_i32(v);
-                        lo_b = max(lo_b, 0xFFFFFFFFu - bv);
-                        hi_b = max(hi_b, bv);
-                    }
-                }
-                tile[r][jj] = v;
-            }
-            __syncthreads();
-            for (int e = threadIdx.x; e < BLK * dc; e += BLK) {
-                const int jj = e / BLK, r = e - jj * BLK;
-                dst[(b * d + j0 + jj) * BLK + r] = tile[r][jj];
-            }
-        }
+        pack_block<T>((const T *)S.src, S.n, S.d, ((uintptr_t)S.src & 15) == 0, (T *)S.dst, gb - S.blk0, tile, bad,
+                      nonfin, lo_b, hi_b);
         if constexpr (std::is_same<T, float>::value) {
             if (nonfin) set_status(st, KC_ERR_NONFINITE, 1, s_seg);
             else if (bad) set_status(st, KC_ERR_RANGE, 1, s_seg);
@@ -207,10 +174,10 @@ cudaError_t launch_pack_many(const PackSeg *segs, int nseg, int64_t total_blocks
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t cap = (int64_t)sms * 16;
+    const int64_t cap = (int64_t)sms * 8;
     const int grid = (int)(total_blocks < cap ? total_blocks : cap);
-    if (dtype == KC_F32) pack_many_kernel<float><<<grid, BLK, 0, s>>>(segs, nseg, total_blocks, st);
-    else pack_many_kernel<int32_t><<<grid, BLK, 0, s>>>(segs, nseg, total_blocks, st);
+    if (dtype == KC_F32) pack_many_kernel<float><<<grid, PACK_NT, 0, s>>>(segs, nseg, total_blocks, st);
+    else pack_many_kernel<int32_t><<<grid, PACK_NT, 0, s>>>(segs, nseg, total_blocks, st);
     note_launches(1);
     return cudaGetLastError();
 }

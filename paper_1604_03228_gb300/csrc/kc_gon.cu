@@ -32,10 +32,11 @@
 
 namespace kc {
 
-// Diagnostic counters of the mixed-precision sweep (since the last read):
+// Diagnostic counters (since the last read):
 // [0] exact FP32 rechecks of candidates, [1] candidate-buffer overflows,
 // [2] rechecks whose memo was more than a few centers behind (done by a
-// whole warp); clock cycles summed over CTAs of the GON kernels' phases:
+// whole warp); clock cycles of the mixed-precision GON kernels' phases (CTA
+// groups only), summed over CTAs:
 // [3] sweep (to the first barrier of a step), [4] exact rechecks (mixed
 // precision only), [5] group exchange and center load; the largest of any
 // CTA: [6] sweep total, [7] sweep + recheck total.
@@ -76,9 +77,6 @@ __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t *p) {
 }
 __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ void ld_relaxed_u64x2(const uint64_t *p, uint64_t &a, uint64_t &b) {
-    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
 template <typename T, int DC>
@@ -167,36 +165,28 @@ __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__
     return best;
 }
 
-// Warp 0: wait for all G slots of one step (a row starting on 16 bytes) and
-// return their maximum.  Lane l polls slot pairs l, l + 32, ... with 16-byte
-// relaxed loads (all of its pending pairs in flight at once), bounded by the
-// cycle budget.
-__device__ uint64_t poll_slots(const uint64_t *slots, int G, long long timeout, DevStatus *st, int step,
-                               bool *abort_out) {
+// Warp 0: wait for all G slots of this step and return their maximum.
+__device__ uint64_t poll_slots(const uint64_t *slots, int G, long long timeout, DevStatus *st,
+                               int step, bool *abort_out) {
     const int lane = threadIdx.x & 31;
-    const int P = (G + 1) >> 1;   // pairs; the second word of the last pair is padding when G is odd
     uint64_t g = 0;
     bool ab = false;
-    for (int p0 = 0; p0 < P && !ab; p0 += 64) {
+    for (int s0 = 0; s0 < G && !ab; s0 += 128) {
+        uint64_t v[4];
         unsigned pend = 0;
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
-            if (p0 + q * 32 + lane < P) pend |= 1u << q;
+        for (int q = 0; q < 4; ++q)
+            if (s0 + q * 32 + lane < G) pend |= 1u << q;
         const long long t0 = clock64();
         while (pend) {
-            uint64_t v[2][2];
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (pend >> q & 1u) ld_relaxed_u64x2(slots + 2 * (p0 + q * 32 + lane), v[q][0], v[q][1]);
+            for (int q = 0; q < 4; ++q)
+                if (pend >> q & 1u) v[q] = ld_relaxed_u64(slots + s0 + q * 32 + lane);
 #pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (pend >> q & 1u) {
-                    const int s1 = 2 * (p0 + q * 32 + lane) + 1;
-                    if (v[q][0] != 0 && (s1 >= G || v[q][1] != 0)) {
-                        g = umax64(g, v[q][0]);
-                        if (s1 < G) g = umax64(g, v[q][1]);
-                        pend &= ~(1u << q);
-                    }
+            for (int q = 0; q < 4; ++q)
+                if ((pend >> q & 1u) && v[q] != 0) {
+                    g = umax64(g, v[q]);
+                    pend &= ~(1u << q);
                 }
             if (pend && (clock64() - t0 > timeout || ld_volatile_i32(&st->code) != 0)) {
                 set_status(st, KC_ERR_TIMEOUT, 3, step);
@@ -216,7 +206,6 @@ __device__ __forceinline__ int64_t out_index(const GonInst &I, int64_t local) {
 struct Shared {
     uint64_t red[32];
     uint64_t key;
-    long long pc[4];
     int abort;
 };
 
@@ -237,13 +226,11 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
 
     int it;
     uint64_t K = 0;
-    if (tid == 0) pc_start(sh.pc);
     for (it = 0; it < I.k; ++it) {
         uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
-        if (tid == 0) pc_mark(sh.pc, 0);
         if (warp == 0) {
             uint64_t v = lane < W ? sh.red[lane] : 0;
             v = warp_max_u64(v);
@@ -265,16 +252,13 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
             }
         }
         __syncthreads();
-        if (tid == 0) pc_mark(sh.pc, 2);
-        if (sh.abort) break;
+        if (sh.abort) return;
         K = sh.key;
         if (key_val(K) == 0) {   // every point is at distance 0: stop early
             ++it;
             break;
         }
     }
-    if (tid == 0) pc_publish(sh.pc);
-    if (sh.abort) return;
     if (r == 0 && tid == 0) {
         *I.k_out = it;
         *I.final_key = K;
@@ -477,6 +461,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
     float *scs = smem + dp;                            // [dp] fp8 scales
     Cand *buf = reinterpret_cast<Cand *>(smem + 2 * ((dp + 1) & ~1)) + warp * LP_CAP;
     const float *pk = (const float *)I.pk;
+    const bool clk = G > 1;   // phase clocks for CTA groups (queue instances are too short to time)
     const float g1 = lp_slack(d);
     const float opg = __fadd_ru(1.f, g1), omg = __fsub_rd(1.f, g1);
     const int64_t lo = I.lo, hi = I.lo + I.n, b1 = (hi - 1) / BLK;
@@ -497,7 +482,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
 
     int it;
     uint64_t K = 0;
-    if (tid == 0) pc_start(sh.pc);
+    if (clk && tid == 0) pc_start(sh.pc);
     volatile unsigned *Lcta = &sh.Lcta;
     for (it = 0; it < I.k; ++it) {
         const float ecmax = sh.ecmax;
@@ -624,7 +609,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             sh.cnt[warp] = cnt;
         }
         __syncthreads();
-        if (tid == 0) pc_mark(sh.pc, 0);
+        if (clk && tid == 0) pc_mark(sh.pc, 0);
         float T = -INFINITY;
         for (int w = 0; w < W; ++w) T = fmaxf(T, sh.Lw[w]);
         if (G > 1) {
@@ -642,7 +627,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                 }
             }
             __syncthreads();
-            if (tid == 0) pc_mark(sh.pc, 2);
+            if (clk && tid == 0) pc_mark(sh.pc, 2);
             if (sh.abort) break;
             T = sh.Tg;
         }
@@ -697,7 +682,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
-        if (tid == 0) pc_mark(sh.pc, 1);
+        if (clk && tid == 0) pc_mark(sh.pc, 1);
         if (warp == 0) {
             uint64_t v = lane < W ? sh.red[lane] : 0;
             v = warp_max_u64(v);
@@ -722,7 +707,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             }
         }
         __syncthreads();
-        if (tid == 0) pc_mark(sh.pc, 2);
+        if (clk && tid == 0) pc_mark(sh.pc, 2);
         if (sh.abort) break;
         K = sh.key;
         if (key_val(K) == 0) {
@@ -730,7 +715,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             break;
         }
     }
-    if (tid == 0) pc_publish(sh.pc);
+    if (clk && tid == 0) pc_publish(sh.pc);
     if (sh.abort) return;
     if (r == 0 && tid == 0) {
         *I.k_out = it;

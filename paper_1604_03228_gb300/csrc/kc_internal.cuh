@@ -189,11 +189,10 @@ cudaError_t read_counters(unsigned long long out[8], bool reset);
 int gon_max_grid(int dtype, int d, int lp = 0);
 int gon_queue_grid(int dtype, int d, int lp = 0);
 int gon_threads();
-// Exchange slots: per step a row of slot_stride(G) 8-byte words (G rounded up
-// to even, so a row starts on 16 bytes and is polled two slots per load);
-// words for k steps, twice that for the mixed-precision sweep (keys, then
-// the CTAs' lower bounds).
-__host__ __device__ inline int64_t slot_stride(int G) { return (int64_t)((G + 1) & ~1); }
+// Exchange slots: per step a row of G 8-byte words (one per CTA of the
+// group); words for k steps, twice that for the mixed-precision sweep (keys,
+// then the CTAs' lower bounds).
+__host__ __device__ inline int64_t slot_stride(int G) { return (int64_t)G; }
 inline int64_t slot_words(int64_t k, int G, bool lp) { return k * slot_stride(G) * (lp ? 2 : 1); }
 int gon_queue_warps();
 int gon_warps_per_cta();

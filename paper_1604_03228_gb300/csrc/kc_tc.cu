@@ -3,33 +3,40 @@
 // EIM's prune of R against the sample S (Algorithm 2, the round Section 5.2
 // finds dominant).
 //
-// Operands.  Points and centers are scaled by 2^e (e chosen so that every
-// |coordinate| <= 2^14, an exact scaling) and rounded to fp16.  A prep pass
-// writes them once as MMA tiles (128 point rows or 256 center rows by Kp =
-// d rounded up to 16 coordinates) in the shared-memory operand layout, with
-// per-row |x~|^2 and error bound e_x = ||x~ - 2^e x|| (FP32, rounded up).
+// Operands.  Points and centers are scaled by 2^e (an exact scaling, e chosen
+// so that every |coordinate| <= 2^S with d 2^(2S) <= 2^30 and S <= 14) and
+// rounded to fp16: x~, c~.  A prep pass writes them once as MMA tiles (128
+// point rows or 256 center rows by Kp = d + 3 rounded up to 16) in the
+// shared-memory operand layout, with per-row |x~|^2 and error bound
+// e = ||x~ - 2^e x|| (FP32, rounded up).  The tiles carry the norm term too:
+// a point row is (x~, 2^15, 2^4, 2^-7, 0...), a center row (2 c~, p1, p2, p3,
+// 0...) with p1 2^15 + p2 2^4 + p3 2^-7 = -|c~|^2 up to a residual r_c
+// (fp16 pieces taken in turn from the FP32 norm, r_c computed exactly), so
+// the accumulator itself is v = 2 x~.c~ - |c~|^2 and s~ = |x~|^2 - v
+// approximates ||x~ - c~||^2.  Rows past the count are zero (points) or
+// carry -inf pieces (centers: v = -inf, never a maximum or within a limit).
 //
 // Kernel.  One persistent CTA per SM (it holds all 512 TMEM columns).  Warps:
-//   8    producer: cp.async.bulk of point tiles (2-stage ring), center tiles
-//        (2-stage ring) and each center tile's negated norms (a 2-stage ring
-//        tied to the accumulator stages) into shared memory
+//   8    producer: cp.async.bulk of point tiles (2-stage ring) and center
+//        tiles (2-stage ring) into shared memory
 //   9    MMA issuer (one thread): tcgen05.mma.kind::f16, M=128 x N=256,
 //        Kp/16 instructions per tile pair, FP32 accumulators double-buffered
 //        in TMEM (2 x 256 columns)
 //   0-7  epilogue: warps w and w+4 own point rows 32(w%4).. (their TMEM
 //        lanes) and split the 256 columns; each thread software-pipelines its
-//        32-column TMEM loads and forms v = 2 x~.c~ - |c~|^2 two columns per
-//        packed FMA, folding v into a running maximum three values at a time
-//        (radius) or comparing it with the point's two decision limits
-//        (prune), since s~ = |x~|^2 - v approximates ||x~ - c~||^2.
+//        32-column TMEM loads and folds v into a running maximum three values
+//        at a time (radius) or compares it with the point's two decision
+//        limits (prune).
 // Shared-memory operand layout: no swizzle, K-major, 8 x 16-byte core
 // matrices; core matrix (row block mi, column block ki) of an R-row tile at
 // byte ((ki * R/8) + mi) * 128: the descriptor's leading (K) byte offset is
 // R/8 * 128 and its stride (M/N) byte offset 128.
 //
-// Error bound.  fp16 products are exact; the FP32 accumulation, the norms and
-// the epilogue operations are covered by
-//   |s~ - ||x~ - c~||^2| <= eta (|x~|^2 + |c~|^2),  eta = g_d + (Kp+16) 2^-21 + 2^-21
+// Error bound.  fp16 products are exact; the FP32 accumulation (whose terms
+// sum in magnitude to at most |x~|^2 + 2 |c~|^2), the norms and the split
+// are covered by
+//   |s~ - ||x~ - c~||^2| <= eta (|x~|^2 + 2 |c~|^2) + max r_c,
+//   eta = g_d + (Kp+16) 2^-21 + 2^-21
 // (a deliberately loose model of the tensor core's accumulation).  With the
 // triangle inequality ||x - c|| in ||x~ - c~|| -+ (e_x + e_c) (scaled units)
 // and the canonical FP32 value within (1 +- g_d) of the exact one, every
@@ -147,16 +154,6 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
                  : "memory");
 }
 
-// v = 2 acc - |c|^2 for two accumulator columns at once (c2n holds the
-// negated norms), each lane rounded like fma(2, acc, -|c|^2).
-__device__ __forceinline__ void fma2_acc(uint32_t r0, uint32_t r1, float2 c2n, float &v0, float &v1) {
-    unsigned long long a, c, d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "r"(r0), "r"(r1));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(c) : "f"(c2n.x), "f"(c2n.y));
-    const unsigned long long two = 0x4000000040000000ull;   // (2.0f, 2.0f)
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(two), "l"(c));
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(v0), "=f"(v1) : "l"(d));
-}
 __device__ __forceinline__ float max3f(float a, float b, float c) {
     float r;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -168,13 +165,22 @@ __host__ __device__ __forceinline__ int core_off(int R, int r, int k) {
     return ((k >> 3) * (R >> 3) + (r >> 3)) * 64 + (r & 7) * 8 + (k & 7);
 }
 
-// Scale 2^e with max|coordinate| * 2^e <= 2^14 (1 for an all-zero input).
-__device__ __forceinline__ float tc_scale(const unsigned *absmax) {
+// Largest exponent S with d 2^(2S) <= 2^30 (so |c~|^2 <= 2^30 and its first
+// fp16 piece fits after the 2^-15 shift), and S <= 14 (2 c~ stays in fp16).
+__host__ __device__ __forceinline__ int tc_sexp(int d) {
+    int lg = 0;
+    while ((1 << lg) < d) ++lg;   // ceil(log2 d)
+    const int S = (30 - lg) / 2;
+    return S < 14 ? S : 14;
+}
+
+// Scale 2^e with max|coordinate| * 2^e <= 2^S (1 for an all-zero input).
+__device__ __forceinline__ float tc_scale(const unsigned *absmax, int d) {
     const float m = __uint_as_float(*absmax);
     if (!(m > 0.f)) return 1.f;
     int ex;
-    frexpf(m, &ex);               // m = f 2^ex, f in [0.5, 1): m < 2^ex
-    return ldexpf(1.f, 14 - ex);  // m 2^(14-ex) < 2^14
+    frexpf(m, &ex);                        // m = f 2^ex, f in [0.5, 1): m < 2^ex
+    return ldexpf(1.f, tc_sexp(d) - ex);   // m 2^(S-ex) < 2^S
 }
 
 // ------------------------------------------------------------------ prep
@@ -190,18 +196,19 @@ __global__ void tc_absmax_kernel(const float *__restrict__ pk, int64_t n, int d,
 
 // Rows -> fp16 MMA tiles of R rows.  Row i is a point or center: from the
 // packed array (pk) when pk != null, else row idx ? idx[i] : i of the
-// row-major array rm.  Rows past the count are zero with norm +inf (they
-// never win a minimum or pass a threshold).  maxes (optional) gets the
-// largest e and the largest norm.  Center tiles (R = TC_N) store the norm
-// negated (-inf past the count), the form the epilogue's fused multiply-add
-// takes.
+// row-major array rm.  Point tiles (R = TC_M) append the multipliers
+// (2^15, 2^4, 2^-7) at columns d, d+1, d+2; center tiles (R = TC_N) store
+// 2 c~ and the three fp16 pieces of -|c~|^2 there.  Rows past the count:
+// zero coordinates, -inf pieces (centers), norm +inf.  maxes (optional) gets
+// the largest e, the largest norm and the largest split residual r_c.
 template <int R>
 __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__restrict__ rm,
                                const uint32_t *__restrict__ idx, const int32_t *cnt_dev, int64_t cnt_max, int d,
                                int kp, int64_t ntiles, const unsigned *absmax, __half *__restrict__ tiles,
                                float *__restrict__ norm, float *__restrict__ err, unsigned *maxes) {
+    constexpr bool CENTER = R == TC_N;
     const int64_t cnt = cnt_dev ? (int64_t)*cnt_dev : cnt_max;
-    const float sc = tc_scale(absmax);
+    const float sc = tc_scale(absmax, d);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ntiles * R;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = i / R;
@@ -210,9 +217,38 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
         const bool valid = i < cnt;
         int64_t g = 0;
         if (valid) g = pk ? i : (idx ? (int64_t)idx[i] : i);
+        // coordinates first: norm and rounding bound
         float nrm = 0.f, e2 = 0.f;
-        // one 16-byte core-matrix row (8 coordinates) per store; consecutive
-        // rows of a warp store consecutive 16-byte chunks
+        for (int k = 0; k < d; ++k) {
+            const float x = valid ? __fmul_rn(pk ? pk[pk_index(g, k, d)] : rm[g * d + k], sc) : 0.f;   // exact
+            const float xq = __half2float(__float2half_rn(x));
+            const float df = fabsf(__fsub_rn(x, xq));   // exact (Sterbenz) or x itself
+            e2 = __fmaf_ru(df, df, e2);
+            nrm = __fmaf_rn(xq, xq, nrm);
+        }
+        // the norm columns
+        __half aug[3];
+        float resid = 0.f;
+        if (!CENTER) {
+            aug[0] = __float2half_rn(32768.f);
+            aug[1] = __float2half_rn(16.f);
+            aug[2] = __float2half_rn(0.0078125f);
+        } else if (!valid) {
+            aug[0] = aug[1] = aug[2] = __float2half_rn(-INFINITY);
+        } else {
+            // -|c~|^2 = p1 2^15 + p2 2^4 + p3 2^-7 + residual; each piece is the
+            // fp16 rounding of what is left (|c~|^2 <= 2^30, so no piece overflows)
+            const double v = -(double)nrm;
+            aug[0] = __float2half_rn((float)(v * 0x1p-15));
+            const double r1 = v - (double)__half2float(aug[0]) * 0x1p15;
+            aug[1] = __float2half_rn((float)(r1 * 0x1p-4));
+            const double r2 = r1 - (double)__half2float(aug[1]) * 0x1p4;
+            aug[2] = __float2half_rn((float)(r2 * 0x1p7));
+            const double r3 = r2 - (double)__half2float(aug[2]) * 0x1p-7;
+            resid = __double2float_ru(fabs(r3));
+        }
+        // one 16-byte core-matrix row (8 columns) per store; consecutive rows
+        // of a warp store consecutive 16-byte chunks
         for (int k0 = 0; k0 < kp; k0 += 8) {
             uint32_t w[4];
 #pragma unroll
@@ -221,13 +257,15 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
 #pragma unroll
                 for (int v = 0; v < 2; ++v) {
                     const int k = k0 + u + v;
-                    float x = 0.f;
-                    if (valid && k < d) x = __fmul_rn(pk ? pk[pk_index(g, k, d)] : rm[g * d + k], sc);   // exact
-                    const __half q = __float2half_rn(x);
-                    const float xq = __half2float(q);
-                    const float df = fabsf(__fsub_rn(x, xq));   // exact (Sterbenz) or x itself
-                    e2 = __fmaf_ru(df, df, e2);
-                    nrm = __fmaf_rn(xq, xq, nrm);
+                    __half q = __float2half_rn(0.f);
+                    if (k < d) {
+                        if (valid) {
+                            q = __float2half_rn(__fmul_rn(pk ? pk[pk_index(g, k, d)] : rm[g * d + k], sc));
+                            if (CENTER) q = __hadd(q, q);   // 2 c~, exact
+                        }
+                    } else if (k < d + 3) {
+                        q = aug[k - d];
+                    }
                     q2[v] = q;
                 }
                 w[u / 2] = (uint32_t)__half_as_ushort(q2[0]) | ((uint32_t)__half_as_ushort(q2[1]) << 16);
@@ -235,12 +273,12 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
             *reinterpret_cast<uint4 *>(tile + core_off(R, r, k0)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
         const float e = __fsqrt_ru(e2);
-        const float nv = valid ? nrm : INFINITY;
-        norm[i] = R == TC_N ? -nv : nv;
+        norm[i] = valid ? nrm : INFINITY;
         err[i] = valid ? e : 0.f;
         if (maxes && valid) {
             atomicMax(&maxes[0], __float_as_uint(e));
             atomicMax(&maxes[1], __float_as_uint(nrm));
+            atomicMax(&maxes[2], __float_as_uint(resid));
         }
     }
 }
@@ -252,7 +290,7 @@ struct TcArgs {
     const float *an, *ae;       // point norms and bounds
     const __half *bt;           // center tiles [ntiles][256 x kp]
     const float *cn;            // center norms [ntiles * 256]
-    const unsigned *maxes;      // [0] = E (max e_c), [1] = max |c~|^2 (float bits), scaled units
+    const unsigned *maxes;      // [0] = E (max e_c), [1] = max |c~|^2, [2] = max r_c (float bits), scaled units
     const unsigned *absmax;     // max |coordinate| (float bits), for the scale
     // radius
     float *mlo, *mhi;           // per-point bounds on the canonical minimum (unscaled)
@@ -283,11 +321,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int kp = a.kp;
     const uint32_t a_bytes = (uint32_t)TC_M * kp * 2, b_bytes = (uint32_t)TC_N * kp * 2;
-    // point tiles at smem + stage * a_bytes, center tiles after them, then
-    // the negated center norms of the two accumulator stages
+    // point tiles at smem + stage * a_bytes, center tiles after them
     unsigned char *const sAb = smem, *const sBb = smem + 2 * a_bytes;
-    float *const sCn = reinterpret_cast<float *>(smem + 2 * a_bytes + 2 * b_bytes);
-    __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], t_full[2], t_empty[2], c_full[2];
+    __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], t_full[2], t_empty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_abort;
     __shared__ float s_part[TC_GROUPS][TC_M];
@@ -305,7 +341,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
             mbar_init(&b_empty[s], 1);
             mbar_init(&t_full[s], 1);
             mbar_init(&t_empty[s], TC_EPI);
-            mbar_init(&c_full[s], 1);
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -327,7 +362,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
     if (warp == TC_PROD) {
         // ------------------------------------------------ producer
         if (lane == 0) {
-            uint32_t afill = 0, bfill = 0, cfill = 0;   // bit s: parity of stage s's fills so far
+            uint32_t afill = 0, bfill = 0;   // bit s: parity of stage s's fills so far
             int64_t u = 0, p = 0;
             for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x, ++p) {
                 const int sa = (int)(p & 1);
@@ -349,16 +384,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                     mbar_expect_tx(&b_full[s], b_bytes);
                     bulk_g2s(sBb + s * b_bytes, a.bt + (int64_t)t * TC_N * kp, b_bytes, &b_full[s]);
                     bfill ^= 1u << s;
-                    // the norms of tile u go to ring stage s once the epilogue
-                    // has released that stage (tile u - 2)
-                    if (!mbar_wait(&t_empty[s], ((cfill >> s) & 1u) ^ 1u, abort)) {
-                        *abort = 1;
-                        set_status(a.st, KC_ERR_TIMEOUT, 6, t);
-                        break;
-                    }
-                    mbar_expect_tx(&c_full[s], TC_N * 4);
-                    bulk_g2s(sCn + s * TC_N, a.cn + (int64_t)t * TC_N, TC_N * 4, &c_full[s]);
-                    cfill ^= 1u << s;
                 }
             }
         }
@@ -407,13 +432,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
         // columns of every tile
         const int row = (warp & 3) * 32 + lane;
         const int grp = warp >> 2;
-        const float sc = tc_scale(a.absmax);
+        const float sc = tc_scale(a.absmax, a.d);
         const float sc2 = sc * sc;                  // exact power of two
         const float isc2 = 1.f / sc2;               // exact power of two
         const float eta = tc_eta(a.d, kp);
         const float g = lp_slack(a.d);
         const float E = __uint_as_float(a.maxes[0]);
-        const float cnmax = __uint_as_float(a.maxes[1]);
+        const float cnmax2 = __fmul_ru(2.f, __uint_as_float(a.maxes[1]));
+        const float rmax = __uint_as_float(a.maxes[2]);
         uint32_t tuse = 0;   // bit s: parity of TMEM stage s's uses so far
         int64_t u = 0;
         for (int64_t pt = blockIdx.x; pt < ntile_pts; pt += gridDim.x) {
@@ -421,7 +447,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
             const bool valid = pi < a.npts;
             const float xn = valid ? a.an[pi] : 0.f;
             const float sl = __fadd_ru(valid ? a.ae[pi] : 0.f, E);
-            const float eps = __fmul_ru(eta, __fadd_ru(xn, cnmax));
+            const float eps = __fadd_ru(__fmul_ru(eta, __fadd_ru(xn, cnmax2)), rmax);
             int64_t gx = 0;
             bool removed = !valid;
             float vlo = INFINITY, vhi = INFINITY;
@@ -443,26 +469,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
             bool emitted = false, ovf = false;
             volatile int *s_gone_v = s_gone;
             int cbase = 0;
-            const float *cns = sCn;   // negated norms of the current tile's columns (shared memory)
-            // One 32-column chunk of accumulators (columns cbase + c0 ..):
-            // v = 2 acc - |c|^2, two columns per packed FMA, folded into the
-            // running maxima three values at a time.
+            // One 32-column chunk of accumulators v (columns cbase + c0 ..),
+            // folded into running maxima three values at a time.
             auto chunk = [&](const uint32_t(&r)[32], int c0) {
-                const float4 *cn4 = reinterpret_cast<const float4 *>(cns + c0);
                 if (MODE == 0) {
 #pragma unroll
-                    for (int j = 0; j < 32; j += 4) {
-                        const float4 c = cn4[j / 4];
-                        float a0, a1, a2, a3;
-                        fma2_acc(r[j], r[j + 1], make_float2(c.x, c.y), a0, a1);
-                        fma2_acc(r[j + 2], r[j + 3], make_float2(c.z, c.w), a2, a3);
-                        if ((j & 4) == 0) {
-                            v0 = max3f(v0, a0, a1);
-                            v1 = max3f(v1, a2, a3);
-                        } else {
-                            v2 = max3f(v2, a0, a1);
-                            v3 = max3f(v3, a2, a3);
-                        }
+                    for (int j = 0; j < 32; j += 8) {
+                        v0 = max3f(v0, __uint_as_float(r[j]), __uint_as_float(r[j + 1]));
+                        v1 = max3f(v1, __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                        v2 = max3f(v2, __uint_as_float(r[j + 4]), __uint_as_float(r[j + 5]));
+                        v3 = max3f(v3, __uint_as_float(r[j + 6]), __uint_as_float(r[j + 7]));
                     }
                 } else if (!removed) {
                     // fast pass: the chunk's largest v; only a chunk that can
@@ -470,17 +486,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                     float m0 = -INFINITY, m1 = -INFINITY;
 #pragma unroll
                     for (int j = 0; j < 32; j += 4) {
-                        const float4 c = cn4[j / 4];
-                        float a0, a1, a2, a3;
-                        fma2_acc(r[j], r[j + 1], make_float2(c.x, c.y), a0, a1);
-                        fma2_acc(r[j + 2], r[j + 3], make_float2(c.z, c.w), a2, a3);
-                        m0 = max3f(m0, a0, a1);
-                        m1 = max3f(m1, a2, a3);
+                        m0 = max3f(m0, __uint_as_float(r[j]), __uint_as_float(r[j + 1]));
+                        m1 = max3f(m1, __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
                     }
                     if (fmaxf(m0, m1) >= vhi) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) {
-                            const float v = __fmaf_rn(2.f, __uint_as_float(r[j]), cns[c0 + j]);
+                            const float v = __uint_as_float(r[j]);
                             if (v >= vhi && !removed) {
                                 if (v >= vlo) {
                                     removed = true;
@@ -505,14 +517,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
             };
             for (int t = 0; t < a.ntiles; ++t, ++u) {
                 const int s = (int)(u & 1);
-                if (!mbar_wait(&t_full[s], (tuse >> s) & 1u, abort) || !mbar_wait(&c_full[s], (tuse >> s) & 1u, abort)) {
+                if (!mbar_wait(&t_full[s], (tuse >> s) & 1u, abort)) {
                     set_status(a.st, KC_ERR_TIMEOUT, 10, t);
                     *abort = 1;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 cbase = t * TC_N + grp * TC_COLS;
-                cns = sCn + s * TC_N + grp * TC_COLS;
                 if (MODE == 1 && !removed && s_gone_v[row]) removed = true;   // another group decided
                 if (MODE == 0 || !__all_sync(0xFFFFFFFFu, removed)) {
                     // the next chunk's TMEM load is in flight while this one is used
@@ -698,13 +709,14 @@ int sms() {
     return s;
 }
 
-int kpad(int d) { return (d + 15) / 16 * 16; }
+// K of the MMA tiles: the d coordinates and the three norm columns, rounded
+// up to the MMA's K of 16.
+int kpad(int d) { return (d + 3 + 15) / 16 * 16; }
 
-// Dynamic shared memory: two point tiles, two center tiles and two stages of
-// center norms, and at least
+// Dynamic shared memory: two point tiles and two center tiles, and at least
 // 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM.
 size_t tc_smem(int kp) {
-    const size_t need = (size_t)2 * TC_M * kp * 2 + (size_t)2 * TC_N * kp * 2 + (size_t)2 * TC_N * 4;
+    const size_t need = (size_t)2 * TC_M * kp * 2 + (size_t)2 * TC_N * kp * 2;
     return need > 120 * 1024 ? need : 120 * 1024;
 }
 
@@ -750,7 +762,7 @@ cudaError_t launch_tc_absmax(const float *pk, int64_t n, int d, unsigned *absmax
 
 cudaError_t launch_tc_centers(const float *cen_rows, const int32_t *kc_dev, int64_t kc, int d, const unsigned *absmax,
                               void *bt, float *cn, float *ce, unsigned *maxes, cudaStream_t s) {
-    cudaMemsetAsync(maxes, 0, 2 * sizeof(unsigned), s);
+    cudaMemsetAsync(maxes, 0, 3 * sizeof(unsigned), s);
     return rows<TC_N>(nullptr, cen_rows, nullptr, kc_dev, kc, d, absmax, bt, cn, ce, maxes, s);
 }
 
