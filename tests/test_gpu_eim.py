@@ -55,7 +55,7 @@ def test_eim_float_phi_sweep(kc, phi):
     check_eim(kc, pts, 3, phi=phi, expect_loop=True)
 
 
-@pytest.mark.parametrize("n,d,k", [(40000, 16, 4), (30000, 64, 3), (12000, 70, 2)])
+@pytest.mark.parametrize("n,d,k", [(40000, 16, 4), (30000, 64, 3), (12000, 70, 2), (30000, 13, 4), (30000, 14, 4)])
 def test_eim_float_dims(kc, n, d, k):
     pts = I.gauss_mixture(n, d, 72 + d, 100, 0.5, -10, 10)
     check_eim(kc, pts, k, expect_loop=True)

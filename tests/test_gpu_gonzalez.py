@@ -192,7 +192,8 @@ def test_errors_are_status_codes(kc):
 # ------------------------------------------- tensor-core radius filter
 
 @pytest.mark.parametrize("n,d,kc_", [(1000, 3, 100), (40000, 10, 100), (20000, 16, 300), (9000, 17, 513),
-                                      (30000, 64, 1000), (5000, 100, 257), (4000, 128, 64), (3000, 129, 40)])
+                                      (30000, 64, 1000), (5000, 100, 257), (4000, 128, 64), (3000, 129, 40),
+                                      (6000, 1, 300), (7000, 13, 700), (7000, 14, 700)])
 def test_radius_tensor_core_matches_cuda_cores(kc, n, d, kc_, monkeypatch):
     pts = I.gauss_mixture(n, d, 200 + d, 11, 0.7, -15, 15)
     C = I.uniform_int(57, d, kc_, 0, n - 1)
@@ -213,3 +214,26 @@ def test_radius_tensor_core_ties_and_far_points(kc):
     rr = kc.kc_radius(_dev(pts), _dev(C))
     r64, am, _ = O.radius(pts, C, mode="f64")
     assert rr.radius == r64 and rr.argmax == am == 10000
+
+
+@pytest.mark.parametrize("d", [5, 64])
+def test_radius_tensor_core_large_offset(kc, monkeypatch, d):
+    # coordinates near 1e4 with unit spread: norms dwarf the distances, the
+    # hardest case for the norm term carried in the MMA
+    pts = (I.gauss_mixture(20000, d, 400 + d, 6, 1.0, -3, 3) + np.float32(1.0e4)).astype(np.float32)
+    C = I.uniform_int(59, d, 512, 0, 19999)
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    rr = kc.kc_radius(_dev(pts), _dev(C))
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    assert rr.radius == r64 and rr.argmax == am
+
+
+def test_radius_tensor_core_zero_norms_and_exact_hits(kc, monkeypatch):
+    # a center at the origin (norm 0), points equal to centers, all-zero rows
+    pts = I.gauss_mixture(8000, 9, 61, 5, 1.0, -1, 1)
+    pts[:50] = 0.0
+    C = np.concatenate([np.arange(0, 8000, 29), [0, 3]])
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    rr = kc.kc_radius(_dev(pts), _dev(C))
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    assert rr.radius == r64 and rr.argmax == am
