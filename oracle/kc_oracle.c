@@ -233,6 +233,68 @@ int64_t orc_mrg(const orc_metric *M, int64_t k, int64_t m, const int64_t *off,
 }
 
 /*
+ * MRG with a machine capacity c (Algorithm 1 with its while loop).  The first
+ * round runs GON on the m given parts (as orc_mrg).  While the union S of the
+ * returned centers, in ascending index, holds more than c points, S is split
+ * into m' = ceil(|S| / c) contiguous parts -- part i holds positions
+ * [floor(i |S| / m'), floor((i + 1) |S| / m')) of S, at most c points -- each
+ * part runs GON from its lowest index, and S becomes the union of their
+ * centers.  Finally GON on S from its lowest index.  Each extra round adds 2
+ * to the approximation factor (Lemma 3).  Needs c >= 2k, so that S shrinks
+ * (the machine count of inequality (1) falls below 2 only when 2k < c).
+ * sizes[r] (at most max_rounds entries) gets |S| after round r + 1;
+ * *rounds the number of rounds including the final one.  Returns k_out, or
+ * -1 when c < 2k or the rounds exceed max_rounds.
+ */
+int64_t orc_mrg_rounds(const orc_metric *M, int64_t k, int64_t m, const int64_t *off, int64_t c,
+                       int64_t max_rounds, int64_t *sizes, int64_t *rounds, int64_t *centers, double *radius2)
+{
+    if (c < 2 * k) return -1;
+    int64_t cap = m * k > 1 ? m * k : 1;
+    int64_t *subset = (int64_t *)malloc((size_t)M->n * sizeof(int64_t));
+    int64_t *S = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+    int64_t *T = (int64_t *)malloc((size_t)cap * sizeof(int64_t));
+    int64_t *Ci = (int64_t *)malloc((size_t)k * sizeof(int64_t));
+    int64_t sn = 0, r = 0, kout = -1;
+    double r2;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t lo = off[i], hi = off[i + 1];
+        for (int64_t p = lo; p < hi; ++p) subset[p - lo] = p;
+        int64_t ki = orc_gon(M, subset, hi - lo, k, 0, Ci, NULL, &r2);
+        for (int64_t j = 0; j < ki; ++j) S[sn++] = Ci[j];
+    }
+    qsort(S, (size_t)sn, sizeof(int64_t), cmp_i64);
+    if (r < max_rounds) sizes[r] = sn;
+    ++r;
+    while (sn > c) {
+        if (r >= max_rounds) goto done;
+        int64_t mp = (sn + c - 1) / c, tn = 0;
+        for (int64_t i = 0; i < mp; ++i) {
+            int64_t lo = (int64_t)((__int128)i * sn / mp), hi = (int64_t)((__int128)(i + 1) * sn / mp);
+            int64_t ki = orc_gon(M, S + lo, hi - lo, k, 0, Ci, NULL, &r2);
+            for (int64_t j = 0; j < ki; ++j) T[tn++] = Ci[j];
+        }
+        qsort(T, (size_t)tn, sizeof(int64_t), cmp_i64);
+        int64_t *tmp = S;
+        S = T;
+        T = tmp;
+        sn = tn;
+        sizes[r] = sn;
+        ++r;
+    }
+    kout = orc_gon(M, S, sn, k, 0, centers, NULL, &r2);
+    *radius2 = orc_radius(M, NULL, M->n, centers, kout, NULL);
+    ++r;
+done:
+    *rounds = r;
+    free(subset);
+    free(S);
+    free(T);
+    free(Ci);
+    return kout;
+}
+
+/*
  * Uniform draw U(seed, it, x, stream) in [0, 1) for EIM's Bernoulli samples.
  * The paper leaves the random source open; this is a counter-based
  * splitmix64 (Steele, Lea, Flood 2014): counter = it<<33 | x<<1 | stream,

@@ -45,6 +45,9 @@ def lib():
         L.orc_mrg.restype = ct.c_int64
         L.orc_mrg.argtypes = [P(_Metric), ct.c_int64, ct.c_int64, ct.c_void_p, ct.c_void_p,
                               ct.c_void_p, ct.c_void_p, P(ct.c_double)]
+        L.orc_mrg_rounds.restype = ct.c_int64
+        L.orc_mrg_rounds.argtypes = [P(_Metric), ct.c_int64, ct.c_int64, ct.c_void_p, ct.c_int64, ct.c_int64,
+                                     ct.c_void_p, P(ct.c_int64), ct.c_void_p, P(ct.c_double)]
         L.orc_uniform.restype = ct.c_double
         L.orc_uniform.argtypes = [ct.c_uint64, ct.c_uint64, ct.c_uint64, ct.c_uint64]
         L.orc_eim.restype = ct.c_int64
@@ -163,6 +166,37 @@ def mrg(pts: np.ndarray, k: int, offsets: np.ndarray, mode: str | None = None) -
     rounds = [r1[i * k:i * k + r1k[i]].copy() for i in range(m)]
     rad = radius(pts, C, mode="i64" if mode == "i64" else "f64")[0]
     return MrgResult(C, rounds, r2.value, rad)
+
+
+@dataclass
+class MrgRoundsResult:
+    centers: np.ndarray
+    rounds: int              # including the final GON
+    sizes: np.ndarray        # |S| after each round before the final one
+    radius2: float
+    radius: float
+
+
+def mrg_rounds(pts: np.ndarray, k: int, offsets: np.ndarray, capacity: int, mode: str | None = None,
+               max_rounds: int = 64) -> MrgRoundsResult:
+    """MRG with machine capacity c (Algorithm 1 with its while loop): round 1
+    on the given parts, further rounds on ceil(|S|/c) contiguous parts of the
+    union until |S| <= c, then GON on S."""
+    mode = mode or default_mode(pts)
+    P = _Points(pts, mode)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    m = len(off) - 1
+    C = np.zeros(k, dtype=np.int64)
+    sizes = np.zeros(max_rounds, dtype=np.int64)
+    rounds = ct.c_int64()
+    r2 = ct.c_double()
+    kout = lib().orc_mrg_rounds(ct.byref(P.m), k, m, _ptr(off), capacity, max_rounds, _ptr(sizes),
+                                ct.byref(rounds), _ptr(C), ct.byref(r2))
+    if kout < 0:
+        raise ValueError("capacity below 2k or too many rounds")
+    C = C[:kout].copy()
+    rad = radius(pts, C, mode="i64" if mode == "i64" else "f64")[0]
+    return MrgRoundsResult(C, rounds.value, sizes[:rounds.value - 1].copy(), r2.value, rad)
 
 
 def uniform(seed: int, it: int, x: int, stream: int) -> float:

@@ -178,6 +178,60 @@ def test_mrg_four_approximation_lemma2(idx, k):
             assert cover2(D, list(r.round1[i]), part) <= 4 * opt2 * (1 + 1e-12)
 
 
+# ------------------------------------------------ multi-round MRG (Lemma 3)
+
+@pytest.mark.parametrize("idx", range(12))
+def test_mrg_rounds_lemma3_bound(idx):
+    """With capacity c < m k, Algorithm 1 runs extra rounds; after L loop
+    rounds and the final GON the radius is at most 2 (L + 1) OPT (Lemma 3:
+    each extra round adds two to the factor)."""
+    pts = list(_tiny_sets())[idx]
+    n = len(pts)
+    D = brute_d2(pts)
+    mode = "i64" if np.issubdtype(pts.dtype, np.integer) else "f64"
+    k = 2
+    opt2 = brute_opt2(D, k)
+    seen_extra = False
+    for m, c in ((7, 4), (6, 5), (5, 4), (7, 6)):
+        if m > n:
+            continue
+        r = O.mrg_rounds(pts, k, I.even_offsets(n, m), c, mode=mode)
+        seen_extra |= r.rounds > 2
+        factor = 2 * r.rounds            # rounds counts the loop rounds and the final GON
+        assert cover2(D, list(r.centers)) <= factor * factor * opt2 * (1 + 1e-12)
+    assert seen_extra
+
+
+def test_mrg_rounds_machine_count_inequality():
+    """Machines per round obey inequality (1): m^(i) <= m (k/c)^i + (1 - (k/c)^i) / (1 - k/c),
+    and the union shrinks every round."""
+    pts = I.unif_points(60000, 3, 21)
+    k, m, c = 20, 300, 50
+    r = O.mrg_rounds(pts, k, I.even_offsets(len(pts), m), c)
+    assert r.rounds >= 5
+    q = k / c
+    for i, size in enumerate(r.sizes):   # |S| after round i + 1; the next round uses ceil(|S| / c) machines
+        if size <= c:
+            break
+        mi = -(-int(size) // c)
+        bound = m * q ** (i + 1) + (1 - q ** (i + 1)) / (1 - q)
+        assert mi <= bound + 1e-9
+    assert all(int(a) > int(b) for a, b in zip(r.sizes[:-1], r.sizes[1:]))
+    assert r.sizes[-1] <= c
+
+
+def test_mrg_rounds_capacity_cases():
+    pts = I.gauss_mixture(3000, 4, 22, 10, 0.5, -5, 5)
+    off = I.even_offsets(3000, 12)
+    # capacity for the whole union: exactly the two-round algorithm
+    two = O.mrg(pts, 15, off)
+    r = O.mrg_rounds(pts, 15, off, 12 * 15)
+    assert r.rounds == 2 and list(r.centers) == list(two.centers) and r.radius2 == two.radius2
+    # a capacity below 2k cannot make progress and is refused
+    with pytest.raises(ValueError):
+        O.mrg_rounds(pts, 15, off, 29)
+
+
 @pytest.mark.parametrize("seed", range(5))
 def test_farthest_point_property_brute_force(seed):
     """Each selection is the farthest point from the earlier centers, lowest
