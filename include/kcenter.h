@@ -144,6 +144,29 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
                  int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts);
 
 /*
+ * kc_mrg_rounds -- MRG with a machine capacity: Algorithm 1 with its while
+ * loop (Section 3.2, Lemma 3).  Round 1 is kc_mrg's (GON on the m parts);
+ * while the union S of the returned centers (in ascending index) holds more
+ * than `capacity` points, S is split into ceil(|S| / capacity) contiguous
+ * parts -- part i holds positions [floor(i |S| / m'), floor((i+1) |S| / m'))
+ * of S -- each part runs GON from its lowest index, and S becomes the union
+ * of their centers; finally GON on S from its lowest index.  Each round
+ * beyond the second adds 2 to the approximation factor.  With
+ * capacity >= m k this is kc_mrg.
+ *   capacity  points one machine holds; must be >= 2k (else KC_ERR_ARG: the
+ *             union could stop shrinking).
+ *   rounds    int32 out, host memory, may be NULL: rounds run, the final
+ *             GON included.
+ * Other arguments and errors as kc_mrg.  With more than two rounds the call
+ * reads |S| back after each round (a host loop) and does not take KC_ASYNC.
+ * Rounds after the first sweep in FP32 whatever opts->sweep says (same
+ * selections).
+ */
+kc_status kc_mrg_rounds(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, const int64_t *offsets,
+                        int64_t capacity, int64_t *centers, int32_t *k_out, double *radius, int32_t *rounds,
+                        const kc_opts *opts);
+
+/*
  * kc_eim -- EIM: the sampling scheme of Ene, Im and Moseley as generalised in
  * Section 4 (EIM-MapReduce-Sample, Algorithm 2, with Select, Algorithm 3, and
  * the parameter phi), followed by GON on the returned sample (Section 4.2).

@@ -63,6 +63,8 @@ def load(path: str | None = None):
     L.kc_gonzalez_noalloc.argtypes = [vp, i64, i32, i32, i64, vp, vp, vp, popts]
     L.kc_mrg.restype = ct.c_int
     L.kc_mrg.argtypes = [vp, i64, i32, i32, i32, vp, vp, vp, vp, popts]
+    L.kc_mrg_rounds.restype = ct.c_int
+    L.kc_mrg_rounds.argtypes = [vp, i64, i32, i32, i32, vp, i64, vp, vp, vp, vp, popts]
     L.kc_eim.restype = ct.c_int
     L.kc_eim.argtypes = [vp, i64, i32, i32, dbl, vp, vp, vp, popts]
     L.kc_gonzalez_batch.restype = ct.c_int
@@ -326,6 +328,29 @@ def kc_mrg(points, k: int, m: int, offsets=None, *, stream=None, flags: int = 0,
         return centers, k_out, radius
     kk = int(_item(k_out))
     return GonResult(centers[:kk], kk, float(_item(radius)))
+
+
+def kc_mrg_rounds(points, k: int, m: int, capacity: int, offsets=None, *, stream=None, timeout_ms: int = 0,
+                  sweep=None):
+    """MRG with a machine capacity (Algorithm 1 with its while loop) through
+    the C ABI.  Returns (GonResult, rounds)."""
+    L = load()
+    p, n, d, code = _points(points)
+    off = None
+    if offsets is not None:
+        off = offsets.to(_torch().int64).contiguous() if _is_torch(offsets) else np.ascontiguousarray(offsets, dtype=np.int64)
+        if int(off.shape[0]) != m + 1:
+            raise ValueError("offsets must have m+1 entries")
+    centers = _empty_like_place(p, k, np.int64)
+    k_out = _empty_like_place(p, 1, np.int32)
+    radius = _empty_like_place(p, 1, np.float64)
+    rounds = ct.c_int32(0)
+    o = _opts(code, p, stream, 0, timeout_ms, sweep=sweep)
+    st = L.kc_mrg_rounds(_ptr(p), n, d, k, m, _ptr(off), int(capacity), _ptr(centers), _ptr(k_out), _ptr(radius),
+                         ct.byref(rounds), ct.byref(o))
+    _check(L, st)
+    kk = int(_item(k_out))
+    return GonResult(centers[:kk], kk, float(_item(radius))), rounds.value
 
 
 def kc_eim(points, k: int, eps: float = 0.1, phi: float = 6.0, seed: int = 0, *, stream=None,

@@ -709,17 +709,75 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
     return finish(c.arena, c.s);
 }
 
-kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, const int64_t *offsets,
-                 int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts) {
+}  // extern "C"
+
+namespace {
+
+// Round-1-style CTA groups for parts of sizes sz (k centers each, at most
+// sz): proportional to each part's work n_i k_i, at least one CTA, at most
+// one per 32 blocks (one block per warp), within the co-resident grid maxg.
+// queue: more parts than CTAs, one CTA per part from a queue.
+void mrg_groups(const std::vector<int64_t> &sz, int k, int maxg, int W, std::vector<int> &G, bool &queue) {
+    const int m = (int)sz.size();
+    G.assign((size_t)m, 1);
+    queue = m > maxg;
+    if (queue) return;
+    double tot = 0;
+    std::vector<double> work((size_t)m);
+    for (int i = 0; i < m; ++i) {
+        work[i] = (double)sz[i] * (double)std::min<int64_t>(k, sz[i]);
+        tot += work[i];
+    }
+    std::vector<int> cap((size_t)m);
+    int sum = 0;
+    for (int i = 0; i < m; ++i) {
+        const int64_t nbi = nblocks(sz[i]) + 1;
+        cap[i] = (int)std::max<int64_t>(1, (nbi + W - 1) / W);
+        G[i] = (int)std::max(1.0, std::floor(maxg * work[i] / tot));
+        G[i] = std::min(G[i], cap[i]);
+        sum += G[i];
+    }
+    while (sum > maxg) {   // trim the largest groups
+        int j = 0;
+        for (int i = 1; i < m; ++i) if (G[i] > G[j]) j = i;
+        if (G[j] <= 1) break;
+        --G[j];
+        --sum;
+    }
+    while (sum < maxg) {   // hand out the rest to the most loaded CTAs
+        int j = -1;
+        double best = 0;
+        for (int i = 0; i < m; ++i)
+            if (G[i] < cap[i] && work[i] / G[i] > best) {
+                best = work[i] / G[i];
+                j = i;
+            }
+        if (j < 0) break;
+        ++G[j];
+        ++sum;
+    }
+}
+
+// MRG, Algorithm 1: round 1 on the m parts; while the union holds more than
+// capacity points (capacity < m k), further rounds on ceil(|S| / capacity)
+// contiguous parts of the ascending union (host loop); then GON on the
+// union.  rounds_out (host, may be null) gets the number of rounds.
+kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, const int64_t *offsets,
+                  int64_t capacity, int64_t *centers, int32_t *k_out, double *radius, int32_t *rounds_out,
+                  const kc_opts *opts) {
     g_err.clear();
     if (!pts || !centers || !k_out || !radius) return fail(KC_ERR_ARG, "null pointer argument");
     if (n < 1 || n > (int64_t)N_MAX) return fail(KC_ERR_ARG, "n=%lld outside [1, 2^32-2]", (long long)n);
     if (d < 1) return fail(KC_ERR_ARG, "d=%d must be >= 1", d);
     if (k < 1) return fail(KC_ERR_ARG, "k=%d must be >= 1", k);
     if (m < 1 || m > n) return fail(KC_ERR_ARG, "m=%d must be in [1, n]", m);
+    if (capacity < 2 * (int64_t)k)
+        return fail(KC_ERR_ARG, "capacity=%lld must be at least 2k=%lld", (long long)capacity, 2 * (long long)k);
+    const bool multi = capacity < (int64_t)m * k;
     CallCtx c;
     kc_status r = begin(opts, c);
     if (r != KC_OK) return r;
+    if (multi && c.async) return fail(KC_ERR_ARG, "more than two rounds run a host loop and do not take KC_ASYNC");
     const bool dev_pts = is_device_ptr(pts, c.dev);
     const bool dev_cen = is_device_ptr(centers, c.dev);
     const bool dev_kout = is_device_ptr(k_out, c.dev);
@@ -750,52 +808,18 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
     // co-resident grid.  More parts than CTAs: one CTA per part from a queue.
     const int lp = lp_of(c.o);
     const int maxg = gon_max_grid(c.o.dtype, d, lp);
+    const int maxg0 = lp ? gon_max_grid(c.o.dtype, d, 0) : maxg;   // later rounds sweep in FP32
     const int W = gon_warps_per_cta();
-    std::vector<int> G((size_t)m, 1), ki((size_t)m);
-    std::vector<int64_t> slot_off((size_t)m + 1, 0);
-    const bool queue1 = m > maxg;
-    {
-        double tot = 0;
-        std::vector<double> work((size_t)m);
-        for (int i = 0; i < m; ++i) {
-            const int64_t ni = off[i + 1] - off[i];
-            ki[i] = (int)(k < ni ? k : ni);
-            work[i] = (double)ni * ki[i];
-            tot += work[i];
-        }
-        if (!queue1) {
-            std::vector<int> cap((size_t)m);
-            int sum = 0;
-            for (int i = 0; i < m; ++i) {
-                const int64_t nbi = nblocks(off[i + 1] - off[i]) + 1;
-                cap[i] = (int)std::max<int64_t>(1, (nbi + W - 1) / W);
-                G[i] = (int)std::max(1.0, std::floor(maxg * work[i] / tot));
-                G[i] = std::min(G[i], cap[i]);
-                sum += G[i];
-            }
-            while (sum > maxg) {   // trim the largest groups
-                int j = 0;
-                for (int i = 1; i < m; ++i) if (G[i] > G[j]) j = i;
-                if (G[j] <= 1) break;
-                --G[j];
-                --sum;
-            }
-            while (sum < maxg) {   // hand out the rest to the most loaded CTAs
-                int j = -1;
-                double best = 0;
-                for (int i = 0; i < m; ++i)
-                    if (G[i] < cap[i] && work[i] / G[i] > best) {
-                        best = work[i] / G[i];
-                        j = i;
-                    }
-                if (j < 0) break;
-                ++G[j];
-                ++sum;
-            }
-        }
-        for (int i = 0; i < m; ++i)
-            slot_off[i + 1] = slot_off[i] + (queue1 ? 0 : slot_words(ki[i], G[i], lp != 0));
+    std::vector<int> G, ki((size_t)m);
+    std::vector<int64_t> slot_off((size_t)m + 1, 0), sz1((size_t)m);
+    bool queue1 = false;
+    for (int i = 0; i < m; ++i) {
+        sz1[i] = off[i + 1] - off[i];
+        ki[i] = (int)std::min<int64_t>(k, sz1[i]);
     }
+    mrg_groups(sz1, k, maxg, W, G, queue1);
+    for (int i = 0; i < m; ++i)
+        slot_off[i + 1] = slot_off[i] + (queue1 ? 0 : slot_words(ki[i], G[i], lp != 0));
     int grid1 = 0;
     for (int i = 0; i < m; ++i) grid1 += G[i];
     if (queue1) grid1 = gon_queue_grid(c.o.dtype, d, lp);
@@ -817,7 +841,9 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         int *counter;
         void *staging, *pk, *pkU, *cen;
         uint32_t *mind, *mindU;
-        int64_t *c1, *U;
+        int64_t *c1, *U, *U2;
+        void *pkU2;
+        uint64_t *slotsR;
         int32_t *k1;
         uint64_t *fk1;
         GonInst *insts1, *inst2;
@@ -853,6 +879,11 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         ecmax1 = lp ? cv.take<float>((size_t)m) : nullptr;
         take_tc(cv, Rtc, c.o.dtype, n, d, k);
         Lo.inst2 = cv.take<GonInst>(1);
+        if (multi) {   // later rounds: the other union buffers and per-round slots
+            Lo.U2 = cv.take<int64_t>((size_t)ucap);
+            Lo.pkU2 = cv.take<char>((size_t)nblocks(ucap) * BLK * d * esz);
+            Lo.slotsR = cv.take<uint64_t>((size_t)k * std::max(1, maxg0));
+        }
         Lo.cen = cv.take<char>((size_t)k * d * esz);
         Lo.m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
         Lo.cen_dev = dev_cen ? centers : cv.take<int64_t>((size_t)k);
@@ -947,8 +978,89 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         TraceStep t("mrg_union", c.s);
         KC_CUDA(launch_mrg_union(Lo.c1, Lo.k1, m, k, Lo.U, Lo.nU, c.s), "union launch");
         KC_CUDA(launch_gather_pack(Lo.pk, c.o.dtype, d, Lo.U, Lo.nU, ucap, Lo.pkU, c.s), "gather launch");
-        KC_CUDA(launch_mrg_round2_prep(Lo.inst2, proto, Lo.nU, k, c.s), "round 2 prep");
     }
+    int rounds = 1;
+    if (multi) {
+        // Further rounds while the union exceeds the capacity: parts are
+        // contiguous ranges of the ascending union (part i: positions
+        // [floor(i |S| / m'), floor((i + 1) |S| / m'))), solved with the FP32
+        // sweep on the gathered copy, their centers mapped back to global
+        // indices, united and gathered again.
+        int64_t *Ucur = Lo.U, *Unext = Lo.U2;
+        void *pkcur = Lo.pkU, *pknext = Lo.pkU2;
+        for (;;) {
+            int64_t nU = 0;
+            KC_CUDA(cudaMemcpyAsync(&nU, Lo.nU, sizeof nU, cudaMemcpyDeviceToHost, c.s), "count read-back");
+            KC_CUDA(cudaStreamSynchronize(c.s), "cudaStreamSynchronize");
+            {
+                DevStatus h;
+                KC_CUDA(cudaMemcpy(&h, st, sizeof h, cudaMemcpyDeviceToHost), "status read-back");
+                if (h.code != 0) return finish(c.arena, c.s);
+            }
+            if (nU <= capacity) break;
+            if (rounds >= 64) return fail(KC_ERR_ARG, "MRG did not fit the capacity within 64 rounds");
+            const int mp = (int)((nU + capacity - 1) / capacity);
+            std::vector<int64_t> offr((size_t)mp + 1), szr((size_t)mp);
+            for (int i = 0; i <= mp; ++i) offr[i] = (int64_t)((__int128)i * nU / mp);
+            for (int i = 0; i < mp; ++i) szr[i] = offr[i + 1] - offr[i];
+            std::vector<int> Gr;
+            bool queuer = false;
+            mrg_groups(szr, k, maxg0, W, Gr, queuer);
+            std::vector<GonInst> hr((size_t)mp);
+            int64_t soff = 0;
+            int cta = 0;
+            for (int i = 0; i < mp; ++i) {
+                GonInst &I = hr[i];
+                memset(&I, 0, sizeof I);
+                const int kr = (int)std::min<int64_t>(k, szr[i]);
+                I.pk = pkcur;
+                I.mind = Lo.mindU;
+                I.slots = queuer ? nullptr : Lo.slotsR + soff;
+                I.centers = Lo.c1 + (int64_t)i * k;
+                I.k_out = Lo.k1 + i;
+                I.final_key = Lo.fk1 + i;
+                I.map = Ucur + offr[i];
+                I.range2 = Lo.range2;
+                I.lo = offr[i];
+                I.n = szr[i];
+                I.first = 0;
+                I.d = d;
+                I.k = kr;
+                I.cta0 = queuer ? 0 : cta;
+                I.G = queuer ? 1 : Gr[i];
+                I.kcap = kr;
+                cta += I.G;
+                soff += queuer ? 0 : slot_words(kr, Gr[i], false);
+            }
+            KC_CUDA(cudaMemsetAsync(Lo.slotsR, 0, (size_t)std::max<int64_t>(1, soff) * sizeof(uint64_t), c.s),
+                    "slot clear");
+            KC_CUDA(cudaMemsetAsync(Lo.counter, 0, sizeof(int), c.s), "counter clear");
+            if ((r = upload(c.arena, c.s, hr.data(), hr.size() * sizeof(GonInst), Lo.insts1)) != KC_OK) return r;
+            {
+                TraceStep t("mrg_roundk", c.s);
+                GonArgs g{};
+                g.insts = Lo.insts1;
+                g.ninst = mp;
+                g.dtype = c.o.dtype;
+                g.dc = d;
+                g.dmax = d;
+                g.st = st;
+                g.timeout_cycles = tmo;
+                g.grid = queuer ? gon_queue_grid(c.o.dtype, d, 0) : cta;
+                g.queue = queuer ? 1 : 0;
+                g.counter = Lo.counter;
+                KC_CUDA(launch_gon(g, c.s), "mrg round launch");
+                KC_CUDA(launch_mrg_union(Lo.c1, Lo.k1, mp, k, Unext, Lo.nU, c.s), "union launch");
+                KC_CUDA(launch_gather_pack(Lo.pk, c.o.dtype, d, Unext, Lo.nU, ucap, pknext, c.s), "gather launch");
+            }
+            std::swap(Ucur, Unext);
+            std::swap(pkcur, pknext);
+            ++rounds;
+        }
+        proto.pk = pkcur;
+        proto.map = Ucur;
+    }
+    KC_CUDA(launch_mrg_round2_prep(Lo.inst2, proto, Lo.nU, k, c.s), "final round prep");
     {
         TraceStep t("mrg_round2", c.s);
         GonArgs g{};
@@ -962,6 +1074,8 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         g.grid = G2;
         KC_CUDA(launch_gon(g, c.s), "mrg round 2 launch");
     }
+    ++rounds;
+    if (rounds_out) *rounds_out = rounds;
     {
         TraceStep t("radius", c.s);
         RadiusArgs ra{};
@@ -994,6 +1108,21 @@ kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, co
         KC_CUDA(cudaMemcpyAsync(radius, Lo.rad_dev, sizeof(double), cudaMemcpyDeviceToHost, c.s), "copy radius");
     if (c.async) return KC_OK;
     return finish(c.arena, c.s);
+}
+
+}  // namespace
+
+extern "C" {
+
+kc_status kc_mrg(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, const int64_t *offsets,
+                 int64_t *centers, int32_t *k_out, double *radius, const kc_opts *opts) {
+    return mrg_run(pts, n, d, k, m, offsets, INT64_MAX, centers, k_out, radius, nullptr, opts);
+}
+
+kc_status kc_mrg_rounds(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, const int64_t *offsets,
+                        int64_t capacity, int64_t *centers, int32_t *k_out, double *radius, int32_t *rounds,
+                        const kc_opts *opts) {
+    return mrg_run(pts, n, d, k, m, offsets, capacity, centers, k_out, radius, rounds, opts);
 }
 
 kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, int64_t *centers, int32_t *k_out,

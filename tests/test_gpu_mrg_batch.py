@@ -241,3 +241,43 @@ def test_batch_plan_rejects_host_memory(kc):
     st = L.kc_batch_plan_create(1, ptrs, n.ctypes.data, d.ctypes.data, k.ctypes.data, cptrs, ko.ctypes.data,
                                 rr.ctypes.data, None, ct.byref(h))
     assert st == kc.KC_ERR_ARG and b"device memory" in L.kc_last_error()
+
+
+# ------------------------------------------------ MRG with a capacity
+
+@pytest.mark.parametrize("n,d,k,m,cap", [(30000, 3, 20, 60, 200), (20000, 8, 16, 40, 100), (9000, 5, 7, 90, 14)])
+def test_mrg_rounds_exact(kc, n, d, k, m, cap):
+    pts = I.gauss_mixture(n, d, 80 + d, 12, 0.4, -4, 4)
+    off = I.even_offsets(n, m)
+    ref = O.mrg_rounds(pts, k, off, cap, mode="f32")
+    got, rounds = kc.kc_mrg_rounds(_dev(pts), k, m, cap, _dev(off))
+    assert rounds == ref.rounds and rounds >= 3
+    assert got.centers.cpu().tolist() == ref.centers.tolist()
+    assert got.radius == O.radius(pts, ref.centers, mode="f64")[0]
+
+
+def test_mrg_rounds_int_zipf_and_two_round_case(kc):
+    pts = I.int_points(50000, 4, 81, 0, 200)
+    off = I.offsets_from_sizes(I.zipf_partition_sizes(50000, 32, 1.1))
+    ref = O.mrg_rounds(pts, 25, off, 120)
+    got, rounds = kc.kc_mrg_rounds(_dev(pts), 25, 32, 120, _dev(off))
+    assert rounds == ref.rounds and got.centers.cpu().tolist() == ref.centers.tolist()
+    assert got.radius == math.sqrt(ref.radius2)
+    # capacity for the whole union: the two-round kc_mrg
+    two, r2 = kc.kc_mrg_rounds(_dev(pts), 25, 32, 32 * 25, _dev(off))
+    m2 = kc.kc_mrg(_dev(pts), 25, 32, _dev(off))
+    assert r2 == 2 and two.centers.cpu().tolist() == m2.centers.cpu().tolist() and two.radius == m2.radius
+
+
+def test_mrg_rounds_rejects_small_capacity(kc):
+    pts = I.gauss_mixture(1000, 3, 82, 3, 1.0, 0, 1)
+    with pytest.raises(kc.KCError):
+        kc.kc_mrg_rounds(_dev(pts), 10, 4, 19)
+
+
+def test_mrg_rounds_bf16_first_round(kc):
+    pts = I.gauss_mixture(40000, 16, 83, 10, 0.5, -3, 3)
+    off = I.even_offsets(40000, 50)
+    ref = O.mrg_rounds(pts, 12, off, 100, mode="f32")
+    got, rounds = kc.kc_mrg_rounds(_dev(pts), 12, 50, 100, _dev(off), sweep="bf16")
+    assert rounds == ref.rounds and got.centers.cpu().tolist() == ref.centers.tolist()
