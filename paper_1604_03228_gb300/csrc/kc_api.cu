@@ -202,6 +202,18 @@ bool is_device_ptr(const void *p, int dev) {
     return false;
 }
 
+// The address at which the device reads a pinned (page-locked, mapped) host
+// buffer, or null for pageable or device memory.
+const void *pinned_device_ptr(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost) return nullptr;
+    return at.devicePointer;
+}
+
 kc_opts default_opts() {
     kc_opts o;
     memset(&o, 0, sizeof o);
@@ -211,9 +223,9 @@ kc_opts default_opts() {
 }
 
 long long timeout_cycles(const kc_opts &o) {
-    int dev = 0, khz = 0;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    int khz = device_clock_khz(dev);
     if (khz <= 0) khz = 2100000;
     const long long ms = o.timeout_ms > 0 ? o.timeout_ms : 2000;
     return ms * (long long)khz;
@@ -281,10 +293,17 @@ kc_status begin(const kc_opts *opts, CallCtx &c, uint32_t allowed = KC_ASYNC) {
 }
 
 // Input points: device pointer as is, else copied into `staging`.
+// The points as the pack kernel reads them: device memory as is; pinned host
+// memory in place (pin: its device address; the kernel reads it once over
+// the host link); pageable memory through the staging copy.
 kc_status stage_points(const CallCtx &c, const void *pts, size_t bytes, bool dev_in, void *staging,
-                       const void **out) {
+                       const void **out, const void *pin = nullptr) {
     if (dev_in) {
         *out = pts;
+        return KC_OK;
+    }
+    if (pin) {
+        *out = pin;
         return KC_OK;
     }
     KC_CUDA(cudaMemcpyAsync(staging, pts, bytes, cudaMemcpyHostToDevice, c.s), "copy points to device");
@@ -501,6 +520,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     if (r != KC_OK) return r;
 
     const bool dev_pts = is_device_ptr(pts, c.dev);
+    const void *pin_pts = dev_pts ? nullptr : pinned_device_ptr(pts);   // read in place by the pack
     const bool dev_cen = is_device_ptr(centers, c.dev);
     const bool dev_kout = is_device_ptr(k_out, c.dev);
     const bool dev_rad = is_device_ptr(radius, c.dev);
@@ -526,7 +546,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         // CTAs' lower bounds too
         uint64_t *slots = cv.take<uint64_t>((size_t)slot_words(keff, grid, lp != 0));
         *zero_bytes = cv.off;
-        *staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
+        *staging = (dev_pts || pin_pts) ? nullptr : cv.take<char>((size_t)n * d * esz);
         void *pk = cv.take<char>((size_t)nb * BLK * d * esz);
         uint32_t *mind = cv.take<uint32_t>((size_t)nb * BLK);
         void *cen = cv.take<char>((size_t)keff * d * esz);
@@ -584,7 +604,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
 
     KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
     const void *src;
-    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, staging, &src);
+    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, staging, &src, pin_pts);
     if (r != KC_OK) return r;
     {
         TraceStep t("pack", c.s);
@@ -628,6 +648,7 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
     if (r != KC_OK) return r;
 
     const bool dev_pts = is_device_ptr(pts, c.dev);
+    const void *pin_pts = dev_pts ? nullptr : pinned_device_ptr(pts);   // read in place by the pack
     const bool dev_cin = is_device_ptr(centers, c.dev);
     const bool dev_rad = is_device_ptr(radius, c.dev);
     const bool dev_arg = argmax_point ? is_device_ptr(argmax_point, c.dev) : true;
@@ -654,7 +675,7 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
         ra.max64 = cv.take<unsigned long long>(1);
         ra.arg64 = cv.take<unsigned long long>(1);
         zero_bytes = cv.off;
-        staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
+        staging = (dev_pts || pin_pts) ? nullptr : cv.take<char>((size_t)n * d * esz);
         ra.pk = cv.take<char>((size_t)nb * BLK * d * esz);
         ra.mind = cv.take<uint32_t>((size_t)nb * BLK);
         ra.cen = cv.take<char>((size_t)kc * d * esz);
@@ -686,7 +707,7 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
 
     KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
     const void *src;
-    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, staging, &src);
+    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, staging, &src, pin_pts);
     if (r != KC_OK) return r;
     if (!dev_cin)
         KC_CUDA(cudaMemcpyAsync((void *)cin_dev, centers, (size_t)kc * sizeof(int64_t), cudaMemcpyHostToDevice, c.s),
@@ -779,6 +800,7 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
     if (r != KC_OK) return r;
     if (multi && c.async) return fail(KC_ERR_ARG, "more than two rounds run a host loop and do not take KC_ASYNC");
     const bool dev_pts = is_device_ptr(pts, c.dev);
+    const void *pin_pts = dev_pts ? nullptr : pinned_device_ptr(pts);   // read in place by the pack
     const bool dev_cen = is_device_ptr(centers, c.dev);
     const bool dev_kout = is_device_ptr(k_out, c.dev);
     const bool dev_rad = is_device_ptr(radius, c.dev);
@@ -864,7 +886,7 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
         Lo.slots1 = cv.take<uint64_t>((size_t)std::max<int64_t>(1, slot_off[m]));
         Lo.slots2 = cv.take<uint64_t>((size_t)slot_words(k, G2, false));
         Lo.zero_bytes = cv.off;
-        Lo.staging = dev_pts ? nullptr : cv.take<char>((size_t)n * d * esz);
+        Lo.staging = (dev_pts || pin_pts) ? nullptr : cv.take<char>((size_t)n * d * esz);
         Lo.pk = cv.take<char>((size_t)nb * BLK * d * esz);
         Lo.mind = cv.take<uint32_t>((size_t)nb * BLK);
         Lo.c1 = cv.take<int64_t>((size_t)ucap);
@@ -945,7 +967,7 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
 
     KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, Lo.zero_bytes, c.s), "scratch clear");
     const void *src;
-    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, Lo.staging, &src);
+    r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, Lo.staging, &src, pin_pts);
     if (r != KC_OK) return r;
     r = upload(c.arena, c.s, h1.data(), h1.size() * sizeof(GonInst), Lo.insts1);
     if (r != KC_OK) return r;

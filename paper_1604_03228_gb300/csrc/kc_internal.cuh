@@ -189,6 +189,9 @@ cudaError_t read_counters(unsigned long long out[8], bool reset);
 int gon_max_grid(int dtype, int d, int lp = 0);
 int gon_queue_grid(int dtype, int d, int lp = 0);
 int gon_threads();
+// SM clock rate of a device in kHz (queried once per device: the query
+// costs a few hundred microseconds on some hosts).
+int device_clock_khz(int dev);
 // Exchange slots: per step a row of G 8-byte words (one per CTA of the
 // group); words for k steps, twice that for the mixed-precision sweep (keys,
 // then the CTAs' lower bounds).

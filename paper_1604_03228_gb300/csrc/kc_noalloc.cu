@@ -174,8 +174,7 @@ extern "C" kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, 
                centers, k_out, (uint64_t *)(p + o_key32), (const int32_t *)(p + o_range), grid);
     g.st = st;
     {
-        int khz = 0;
-        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        int khz = device_clock_khz(dev);
         if (khz <= 0) khz = 2100000;
         g.timeout_cycles = (o.timeout_ms > 0 ? o.timeout_ms : 2000) * (long long)khz;
     }

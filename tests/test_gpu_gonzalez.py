@@ -237,3 +237,23 @@ def test_radius_tensor_core_zero_norms_and_exact_hits(kc, monkeypatch):
     rr = kc.kc_radius(_dev(pts), _dev(C))
     r64, am, _ = O.radius(pts, C, mode="f64")
     assert rr.radius == r64 and rr.argmax == am
+
+
+def test_pinned_host_points_read_in_place(kc):
+    # page-locked host memory is read by the pack kernel directly (no staging copy)
+    import torch
+    pts = I.gauss_mixture(50000, 10, 63, 25, 1.0, -50, 50)
+    hp = torch.from_numpy(pts).pin_memory()
+    g = kc.kc_gonzalez(hp, 40)
+    ref = O.gonzalez(pts, 40, mode="f32")
+    assert g.centers.tolist() == ref.centers.tolist()
+    assert g.radius == O.radius(pts, ref.centers, mode="f64")[0]
+    rr = kc.kc_radius(hp, g.centers)
+    assert rr.radius == g.radius
+    m = kc.kc_mrg(hp, 20, 8)
+    mref = O.mrg(pts, 20, I.even_offsets(50000, 8), mode="f32")
+    assert m.centers.tolist() == mref.centers.tolist()
+    # an unaligned view into a pinned buffer (row offset 1: 40-byte shift)
+    hv = torch.from_numpy(np.concatenate([pts[:1], pts])).pin_memory()[1:]
+    g2 = kc.kc_gonzalez(hv, 40)
+    assert g2.centers.tolist() == ref.centers.tolist()
