@@ -422,6 +422,22 @@ void note_launches(int kernels) {
     t_kernels += kernels;
 }
 void set_last_error(const char *text) { g_err = text ? text : ""; }
+
+int device_clock_khz(int dev) {
+    static std::atomic<int> cache[64];
+    int khz = 0;
+    if (dev < 0 || dev >= 64) {
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        return khz;
+    }
+    khz = cache[dev].load(std::memory_order_relaxed);
+    if (khz == 0) {
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+        if (khz <= 0) khz = -1;
+        cache[dev].store(khz, std::memory_order_relaxed);
+    }
+    return khz;
+}
 }  // namespace kc
 
 extern "C" {

@@ -26,7 +26,6 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
-#include <atomic>
 #include <type_traits>
 
 #include "kc_internal.cuh"
@@ -919,22 +918,6 @@ cudaError_t read_counters(unsigned long long out[8], bool reset) {
 }
 
 int gon_threads() { return GROUP_NT; }
-
-int device_clock_khz(int dev) {
-    static std::atomic<int> cache[64];
-    if (dev < 0 || dev >= 64) {
-        int khz = 0;
-        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-        return khz;
-    }
-    int khz = cache[dev].load(std::memory_order_relaxed);
-    if (khz == 0) {
-        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-        if (khz <= 0) khz = -1;
-        cache[dev].store(khz, std::memory_order_relaxed);
-    }
-    return khz;
-}
 int gon_queue_warps() { return QUEUE_NT / 32; }
 int gon_warps_per_cta() { return GROUP_NT / 32; }
 
