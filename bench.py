@@ -87,6 +87,28 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def workload_seed(rank: int) -> int:
+    """Seed of rank r's replica of the workload (independent instances)."""
+    return 1 + 1000 * rank
+
+
+def job_reduce(x: float, op: str, device) -> float:
+    """x reduced over the ranks of the default process group ("max" or
+    "min"); x itself without one (a single process)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.MIN)
+    return float(t.item())
+
+
+def job_throughput(units_per_step: float, steps: int, world: int, job_ms: float) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return units_per_step * steps * world / (job_ms / 1e3)
+
+
 def peaks(kind="hbm"):
     """Roofline denominator: measured HBM copy GB/s, or dense bf16 TFLOP/s
     (burst; fp16 runs at the bf16 rate)."""
@@ -100,8 +122,7 @@ def peaks(kind="hbm"):
 
 def workload(rank: int):
     from paper_1604_03228_gb300 import inputs as I
-    seed = 1 + 1000 * rank
-    return I.gauss_mixture(N, D, seed, 25, 1.0, -50.0, 50.0)
+    return I.gauss_mixture(N, D, workload_seed(rank), 25, 1.0, -50.0, 50.0)
 
 
 # ------------------------------------------------------------------ clocks
@@ -263,16 +284,12 @@ def run_gpu(args):
     trace = kc.kc_trace_read()
     kc.kc_sync(s)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_reduce(sum(step_ms), "max", "cuda")
     sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
 
     evals_step = N * K + N * K
-    value = evals_step * args.steps * world / (total_ms / 1e3)
+    value = job_throughput(evals_step, args.steps, world, total_ms)
 
     # dominant kernel: the persistent GON kernel (one launch per step)
     gon_ms = [ms for (name, nk, ms) in trace if name == "gonzalez"]
@@ -301,11 +318,8 @@ def run_gpu(args):
             r = kc.kc_radius(hp, g.centers)
             _ = (g.radius, r.radius)
         t1 = time.perf_counter()
-        e2e_val = evals_step * reps / (t1 - t0)
-        if world > 1:
-            t = torch.tensor([e2e_val * world], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MIN)
-            e2e_val = float(t.item())
+        # whole job: every rank's rate no better than the slowest rank's
+        e2e_val = job_reduce(evals_step * reps / (t1 - t0), "min", "cuda") * world
         h2d = 2 * N * D * 4 + K * 8
         d2h = K * 8 + 4 + 8 + 8 + 8
         e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
