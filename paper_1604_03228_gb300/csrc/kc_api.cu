@@ -750,10 +750,13 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
 
 namespace {
 
-// Round-1-style CTA groups for parts of sizes sz (k centers each, at most
-// sz): proportional to each part's work n_i k_i, at least one CTA, at most
-// one per 32 blocks (one block per warp), within the co-resident grid maxg.
-// queue: more parts than CTAs, one CTA per part from a queue.
+// CTA groups for parts of sizes sz (k centers each, at most sz):
+// proportional to each part's work n_i k_i, at least one CTA, at most one
+// per W blocks (one block per warp), within maxg co-resident CTAs.  queue:
+// more parts than CTAs, one CTA per part from a queue.  The parts run on the
+// queue kernel's 256-thread CTAs (four per SM) with every part a group
+// ("heavy"): the finer CTA granularity balances uneven parts (Zipf round 1
+// on 10M x 16: 0.83 -> 1.00 of HBM against one 1024-thread CTA per SM).
 void mrg_groups(const std::vector<int64_t> &sz, int k, int maxg, int W, std::vector<int> &G, bool &queue) {
     const int m = (int)sz.size();
     G.assign((size_t)m, 1);
@@ -841,12 +844,10 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
     for (int i = 0; i < m; ++i)
         if (off[i + 1] <= off[i]) return fail(KC_ERR_ARG, "part %d is empty or offsets decrease", i);
 
-    // Round-1 CTA groups: proportional to each part's work n_i * k_i, at least
-    // one CTA, at most one per 32 blocks (one block per warp), within the
-    // co-resident grid.  More parts than CTAs: one CTA per part from a queue.
+    // Round-1 CTA groups on the queue kernel's CTAs (mrg_groups).
     const int lp = lp_of(c.o);
     const int maxg = gon_max_grid(c.o.dtype, d, lp);
-    const int maxg0 = lp ? gon_max_grid(c.o.dtype, d, 0) : maxg;   // later rounds sweep in FP32
+    const int qslots0 = gon_queue_grid(c.o.dtype, d, 0);   // later rounds sweep in FP32
     const int W = gon_warps_per_cta();
     std::vector<int> G, ki((size_t)m);
     std::vector<int64_t> slot_off((size_t)m + 1, 0), sz1((size_t)m);
@@ -855,12 +856,13 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
         sz1[i] = off[i + 1] - off[i];
         ki[i] = (int)std::min<int64_t>(k, sz1[i]);
     }
-    mrg_groups(sz1, k, maxg, W, G, queue1);
+    const int qslots = gon_queue_grid(c.o.dtype, d, lp), Wq = gon_queue_warps();
+    mrg_groups(sz1, k, qslots, Wq, G, queue1);
     for (int i = 0; i < m; ++i)
         slot_off[i + 1] = slot_off[i] + (queue1 ? 0 : slot_words(ki[i], G[i], lp != 0));
     int grid1 = 0;
     for (int i = 0; i < m; ++i) grid1 += G[i];
-    if (queue1) grid1 = gon_queue_grid(c.o.dtype, d, lp);
+    if (queue1) grid1 = qslots;
     std::vector<int64_t> cen_off((size_t)m + 1, 0);
     for (int i = 0; i < m; ++i) cen_off[i + 1] = cen_off[i] + ki[i];
     LPBufs LB;
@@ -920,7 +922,7 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
         if (multi) {   // later rounds: the other union buffers and per-round slots
             Lo.U2 = cv.take<int64_t>((size_t)ucap);
             Lo.pkU2 = cv.take<char>((size_t)nblocks(ucap) * BLK * d * esz);
-            Lo.slotsR = cv.take<uint64_t>((size_t)k * std::max(1, maxg0));
+            Lo.slotsR = cv.take<uint64_t>((size_t)k * std::max(1, qslots0));
         }
         Lo.cen = cv.take<char>((size_t)k * d * esz);
         Lo.m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
@@ -1007,9 +1009,13 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
         g.st = st;
         g.timeout_cycles = tmo;
         g.grid = grid1;
-        g.queue = queue1 ? 1 : 0;
         g.counter = Lo.counter;
         g.lp_kind = lp;
+        g.queue = 1;   // queue kernel: every part a CTA group, or one CTA per part from the queue
+        if (!queue1) {
+            g.nheavy = m;
+            g.gheavy = grid1;
+        }
         KC_CUDA(launch_gon(g, c.s), "mrg round 1 launch");
     }
     {
@@ -1043,7 +1049,7 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
             for (int i = 0; i < mp; ++i) szr[i] = offr[i + 1] - offr[i];
             std::vector<int> Gr;
             bool queuer = false;
-            mrg_groups(szr, k, maxg0, W, Gr, queuer);
+            mrg_groups(szr, k, qslots0, Wq, Gr, queuer);
             std::vector<GonInst> hr((size_t)mp);
             int64_t soff = 0;
             int cta = 0;
@@ -1084,8 +1090,12 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
                 g.dmax = d;
                 g.st = st;
                 g.timeout_cycles = tmo;
-                g.grid = queuer ? gon_queue_grid(c.o.dtype, d, 0) : cta;
-                g.queue = queuer ? 1 : 0;
+                g.grid = queuer ? qslots0 : cta;
+                g.queue = 1;
+                if (!queuer) {
+                    g.nheavy = mp;
+                    g.gheavy = cta;
+                }
                 g.counter = Lo.counter;
                 KC_CUDA(launch_gon(g, c.s), "mrg round launch");
                 KC_CUDA(launch_mrg_union(Lo.c1, Lo.k1, mp, k, Unext, Lo.nU, c.s), "union launch");

@@ -899,6 +899,7 @@ void *pick_queue(int dtype, int dc) {
         switch (dc) {
             case 3: return queue_fn<float, 3>();
             case 8: return queue_fn<float, 8>();
+            case 16: return queue_fn<float, 16>();
             case 32: return queue_fn<float, 32>();
             default: return queue_fn<float, 0>();
         }
