@@ -341,10 +341,14 @@ void take_lp(Carve &cv, LPBufs &L, int lp, int64_t n, int d) {
 // Tensor-core radius filter scratch for kc centers over n float points
 // (left null, i.e. CUDA cores, for int32 points, d > 128, tiny center sets,
 // or KC_RADIUS_TC=0 in the environment).
-void take_tc(Carve &cv, RadiusArgs &ra, int dtype, int64_t n, int d, int kc) {
+bool tc_radius_wanted(int dtype, int d, int kc) {
     bool use = dtype == KC_F32 && tc_supported(d) && (int64_t)kc * d >= 8192;
     if (const char *env = getenv("KC_RADIUS_TC")) use = dtype == KC_F32 && tc_supported(d) && atoi(env) != 0;
-    if (!use) {
+    return use;
+}
+
+void take_tc(Carve &cv, RadiusArgs &ra, int dtype, int64_t n, int d, int kc) {
+    if (!tc_radius_wanted(dtype, d, kc)) {
         ra.tc_at = nullptr;
         return;
     }
@@ -663,8 +667,12 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
     kc_status r = begin(opts, c);
     if (r != KC_OK) return r;
 
+    // On the tensor-core path the row-major points are read where they are
+    // (device memory, else a device copy): no pack.  Otherwise the pack reads
+    // pinned host memory in place.
+    const bool rowmajor = tc_radius_wanted(c.o.dtype, d, kc);
     const bool dev_pts = is_device_ptr(pts, c.dev);
-    const void *pin_pts = dev_pts ? nullptr : pinned_device_ptr(pts);   // read in place by the pack
+    const void *pin_pts = (dev_pts || rowmajor) ? nullptr : pinned_device_ptr(pts);
     const bool dev_cin = is_device_ptr(centers, c.dev);
     const bool dev_rad = is_device_ptr(radius, c.dev);
     const bool dev_arg = argmax_point ? is_device_ptr(argmax_point, c.dev) : true;
@@ -692,7 +700,7 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
         ra.arg64 = cv.take<unsigned long long>(1);
         zero_bytes = cv.off;
         staging = (dev_pts || pin_pts) ? nullptr : cv.take<char>((size_t)n * d * esz);
-        ra.pk = cv.take<char>((size_t)nb * BLK * d * esz);
+        ra.pk = rowmajor ? nullptr : cv.take<char>((size_t)nb * BLK * d * esz);
         ra.mind = cv.take<uint32_t>((size_t)nb * BLK);
         ra.cen = cv.take<char>((size_t)kc * d * esz);
         ra.m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
@@ -728,7 +736,9 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
     if (!dev_cin)
         KC_CUDA(cudaMemcpyAsync((void *)cin_dev, centers, (size_t)kc * sizeof(int64_t), cudaMemcpyHostToDevice, c.s),
                 "copy centers in");
-    {
+    if (rowmajor) {
+        ra.rm = (const float *)src;   // checked by the tensor-core prep
+    } else {
         TraceStep t("pack", c.s);
         KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)ra.pk, range2, c.arena->status, c.s), "pack launch");
         if (c.o.dtype == KC_I32) KC_CUDA(launch_range_check(range2, d, c.arena->status, c.s), "range check");

@@ -21,6 +21,13 @@ __host__ __device__ inline int64_t nblocks(int64_t n) { return (n + BLK - 1) / B
 __host__ __device__ inline int64_t pk_index(int64_t i, int64_t j, int d) {
     return ((i / BLK) * d + j) * BLK + (i % BLK);
 }
+// Coordinate j of float point i: from the packed array, or the row-major
+// one when pk is null.
+__device__ __forceinline__ float point_at(const float *__restrict__ pk, const float *__restrict__ rm, int64_t i, int j,
+                                          int d) {
+    return pk ? pk[pk_index(i, j, d)] : rm[i * d + j];
+}
+
 
 // Device status word (first error wins).
 struct DevStatus {
@@ -82,6 +89,39 @@ __device__ __forceinline__ uint32_t sq_step(uint32_t acc, int32_t x, int32_t c) 
     uint32_t t = (uint32_t)(x - c);
     return acc + t * t;
 }
+
+// Canonical FP32 squared distance of float point i (packed, or row-major when
+// pk is null) and the center row c.  v4: d % 4 == 0, c 16-byte aligned and
+// (row-major) rm too; the center row, which differs between the lanes of a
+// warp, is then read with 16-byte loads (a quarter of the L1 wavefronts).
+__device__ __forceinline__ float point_row_dist(const float *__restrict__ pk, const float *__restrict__ rm, int64_t i,
+                                                int d, const float *__restrict__ c, bool v4) {
+    float acc = 0.f;
+    if (v4) {
+        const float4 *c4 = reinterpret_cast<const float4 *>(c);
+        const float4 *x4 = pk ? nullptr : reinterpret_cast<const float4 *>(rm + i * d);
+        for (int q = 0; q < d / 4; ++q) {
+            const float4 cc = c4[q];
+            float4 xx;
+            if (x4) {
+                xx = x4[q];
+            } else {
+                xx.x = pk[pk_index(i, 4 * q, d)];
+                xx.y = pk[pk_index(i, 4 * q + 1, d)];
+                xx.z = pk[pk_index(i, 4 * q + 2, d)];
+                xx.w = pk[pk_index(i, 4 * q + 3, d)];
+            }
+            acc = sq_step(acc, xx.x, cc.x);
+            acc = sq_step(acc, xx.y, cc.y);
+            acc = sq_step(acc, xx.z, cc.z);
+            acc = sq_step(acc, xx.w, cc.w);
+        }
+    } else {
+        for (int j = 0; j < d; ++j) acc = sq_step(acc, point_at(pk, rm, i, j, d), c[j]);
+    }
+    return acc;
+}
+
 template <typename T> struct AccOf;
 template <> struct AccOf<float> { using type = float; };
 template <> struct AccOf<int32_t> { using type = uint32_t; };
@@ -327,13 +367,16 @@ cudaError_t launch_compact(const uint8_t *mask, int64_t n, int *counts, int64_t 
 
 struct RadiusArgs {
     const void *pk;
+    // float points on the tensor-core path may come row-major instead
+    // ([n][d], pk null): nothing is packed, the coordinates are read in place
+    const float *rm;
     int dtype;
     int64_t n;
     int d;
     const int64_t *centers;  // [kc_max] device indices
     const int32_t *kc_dev;   // device count (nullptr: use kc_max)
     int kc_max;
-    void *cen;               // scratch [kc_max * d] gathered center coordinates
+    void *cen;               // scratch [kc_max * d] gathered center coordinates (16-byte aligned)
     uint32_t *mind;          // [nblocks*BLK] values (input if have_mind)
     unsigned long long *key32;   // argmax key of mind (input if have_mind)
     unsigned long long *max64;   // scratch
@@ -375,9 +418,11 @@ size_t tc_center_bytes(int64_t kc, int d);
 size_t tc_point_bytes(int64_t n, int d);
 int64_t tc_point_rows(int64_t n);
 cudaError_t launch_tc_absmax(const float *pk, int64_t n, int d, unsigned *absmax, cudaStream_t s);
-cudaError_t launch_tc_radius(const float *pk, int64_t n, int d, const float *cen, const int32_t *kc_dev, int kc,
-                             const TcBufs &B, uint32_t *mind, unsigned long long *key32, DevStatus *st,
-                             cudaStream_t s);
+// Points from the packed array pk, or (pk null) from the row-major array rm,
+// which is then also checked as the pack would (NaN/Inf, magnitude).
+cudaError_t launch_tc_radius(const float *pk, const float *rm, int64_t n, int d, const float *cen,
+                             const int32_t *kc_dev, int kc, const TcBufs &B, uint32_t *mind,
+                             unsigned long long *key32, DevStatus *st, cudaStream_t s);
 // Deferred exact checks of the tensor-core prune: the (row, center) pairs
 // its bounds leave undecided, per-row flags, the rows they decide, and the
 // counters of both lists.  pairs holds pcap entries; rows beyond it get a

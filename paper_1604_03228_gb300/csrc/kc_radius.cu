@@ -26,8 +26,9 @@ constexpr int RAD_NT = 256;
 constexpr int RAD_W = RAD_NT / 32;
 constexpr int RAD_TILE_BYTES = 32 * 1024;
 
+// Center rows from the packed array, or (float, pk null) the row-major one.
 template <typename T>
-__global__ void gather_kernel(const T *__restrict__ pk, int64_t n, int d,
+__global__ void gather_kernel(const T *__restrict__ pk, const T *__restrict__ rm, int64_t n, int d,
                               const int64_t *__restrict__ centers, const int32_t *kc_dev, int kc_max,
                               T *__restrict__ cen, DevStatus *st) {
     const int kc = kc_dev ? *kc_dev : kc_max;
@@ -41,7 +42,7 @@ __global__ void gather_kernel(const T *__restrict__ pk, int64_t n, int d,
             cen[e] = T(0);
             continue;
         }
-        cen[e] = pk[pk_index(c, j, d)];
+        cen[e] = pk ? pk[pk_index(c, j, d)] : rm[c * d + j];
     }
 }
 
@@ -167,26 +168,25 @@ __device__ __forceinline__ bool can_reach(const uint32_t *mind, int64_t x, doubl
 // has an exact distance above the FP32 argmin's by more than FP64's own
 // rounding (eps64 = 4 (d+2) 2^-53), so its FP64 value cannot be the minimum;
 // only the remaining centers (usually one or two) are evaluated in FP64,
-// each sum in coordinate order.
-__device__ double min64_warp(const float *__restrict__ pk, int64_t x, int d,
-                             const float *__restrict__ cen, int kc, int lane) {
-    uint32_t m32 = 0xFFFFFFFFu;
-    for (int ci = lane; ci < kc; ci += 32) {
-        float s = 0.f;
-        for (int j = 0; j < d; ++j) s = sq_step(s, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
-        m32 = min(m32, __float_as_uint(s));
-    }
+// each sum in coordinate order.  m32: the canonical FP32 minimum when the
+// caller holds it (0xFFFFFFFF: computed here first).
+__device__ double min64_warp(const float *__restrict__ pk, const float *__restrict__ rm, int64_t x, int d,
+                             const float *__restrict__ cen, int kc, int lane, uint32_t m32) {
+    const bool v4 = (d & 3) == 0 && ((uintptr_t)cen & 15) == 0 && (pk || ((uintptr_t)rm & 15) == 0);
+    if (m32 == 0xFFFFFFFFu) {
+        for (int ci = lane; ci < kc; ci += 32)
+            m32 = min(m32, __float_as_uint(point_row_dist(pk, rm, x, d, cen + (int64_t)ci * d, v4)));
 #pragma unroll
-    for (int o = 16; o; o >>= 1) m32 = min(m32, __shfl_xor_sync(0xFFFFFFFFu, m32, o));
+        for (int o = 16; o; o >>= 1) m32 = min(m32, __shfl_xor_sync(0xFFFFFFFFu, m32, o));
+    }
     const double g = f32_gamma(d);
     const double lim = (double)__uint_as_float(m32) * ((1.0 + g) / (1.0 - g)) * (1.0 + 4.0 * (d + 2) * 0x1p-53);
     double m = INFINITY;
     for (int ci = lane; ci < kc; ci += 32) {
-        float s = 0.f;
-        for (int j = 0; j < d; ++j) s = sq_step(s, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
+        const float s = point_row_dist(pk, rm, x, d, cen + (int64_t)ci * d, v4);
         if ((double)s > lim) continue;
         double s64 = 0.0;
-        for (int j = 0; j < d; ++j) s64 = sq_step64(s64, pk[pk_index(x, j, d)], cen[(int64_t)ci * d + j]);
+        for (int j = 0; j < d; ++j) s64 = sq_step64(s64, point_at(pk, rm, x, j, d), cen[(int64_t)ci * d + j]);
         m = fmin(m, s64);
     }
 #pragma unroll
@@ -196,7 +196,7 @@ __device__ double min64_warp(const float *__restrict__ pk, int64_t x, int d,
 
 // Each warp scans 32 points at a time; the flagged ones (ballot) are
 // recomputed one after another by the whole warp.
-__global__ void recheck_max_kernel(const float *__restrict__ pk, int64_t n, int d,
+__global__ void recheck_max_kernel(const float *__restrict__ pk, const float *__restrict__ rm, int64_t n, int d,
                                    const float *__restrict__ cen, const int32_t *kc_dev, int kc_max,
                                    const uint32_t *__restrict__ mind, const unsigned long long *key32,
                                    unsigned long long *max64, double *m64, const DevStatus *st,
@@ -217,7 +217,8 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, int64_t n, int 
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
             const int64_t xs = base + src;
-            const double v = min64_warp(pk, xs, d, cen, kc, lane);
+            // FP32 minima: mind holds the canonical one; mixed precision: not
+            const double v = min64_warp(pk, rm, xs, d, cen, kc, lane, eblk ? 0xFFFFFFFFu : mind[xs]);
             if (lane == src) {
                 m64[xs] = v;
                 atomicMax(max64, (unsigned long long)__double_as_longlong(v));
@@ -299,20 +300,23 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
         const int64_t g = (total + 255) / 256;
         const int grid = (int)(g < 1 ? 1 : (g > sms * 4 ? sms * 4 : g));
         if (a.dtype == KC_F32)
-            gather_kernel<float><<<grid, 256, 0, s>>>((const float *)a.pk, a.n, a.d, a.centers,
+            gather_kernel<float><<<grid, 256, 0, s>>>((const float *)a.pk, a.rm, a.n, a.d, a.centers,
                                                       a.kc_dev, a.kc_max, (float *)a.cen, a.st);
         else
-            gather_kernel<int32_t><<<grid, 256, 0, s>>>((const int32_t *)a.pk, a.n, a.d, a.centers,
+            gather_kernel<int32_t><<<grid, 256, 0, s>>>((const int32_t *)a.pk, nullptr, a.n, a.d, a.centers,
                                                         a.kc_dev, a.kc_max, (int32_t *)a.cen, a.st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    // row-major points are read only by the tensor-core path
+    if (a.rm && (a.pk || a.have_mind || a.dtype != KC_F32 || !a.tc_at || !tc_supported(a.d)))
+        return cudaErrorInvalidValue;
     if (!a.have_mind) {
         if (a.dtype == KC_F32 && a.tc_at && tc_supported(a.d)) {
             // tensor-core filter: fp16 dot products bound every point's
             // canonical minimum; only points that can reach the maximum get
             // their exact canonical FP32 minimum (the rest get 0)
-            e = launch_tc_radius((const float *)a.pk, a.n, a.d, (const float *)a.cen, a.kc_dev, a.kc_max, tc_bufs(a),
-                                 a.mind, a.key32, a.st, s);
+            e = launch_tc_radius((const float *)a.pk, a.rm, a.n, a.d, (const float *)a.cen, a.kc_dev, a.kc_max,
+                                 tc_bufs(a), a.mind, a.key32, a.st, s);
         } else {
             e = a.dtype == KC_F32 ? dispatch_min<float>(a, s, sms) : dispatch_min<int32_t>(a, s, sms);
         }
@@ -321,7 +325,7 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
     if (a.dtype == KC_F32) {
         const int64_t g = (a.n + 255) / 256;
         const int grid = (int)(g > sms * 8 ? sms * 8 : g);
-        recheck_max_kernel<<<grid, 256, 0, s>>>((const float *)a.pk, a.n, a.d, (const float *)a.cen,
+        recheck_max_kernel<<<grid, 256, 0, s>>>((const float *)a.pk, a.rm, a.n, a.d, (const float *)a.cen,
                                                 a.kc_dev, a.kc_max, a.mind, a.key32, a.max64, a.m64,
                                                 a.st, a.eblk, a.ecmax);
         recheck_arg_kernel<<<grid, 256, 0, s>>>(a.n, a.d, a.mind, a.key32, a.max64, a.m64, a.arg64,

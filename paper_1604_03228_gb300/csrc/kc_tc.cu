@@ -194,6 +194,137 @@ __global__ void tc_absmax_kernel(const float *__restrict__ pk, int64_t n, int d,
     if ((threadIdx.x & 31) == 0) atomicMax(absmax, __float_as_uint(m));
 }
 
+// The same maximum over a row-major array of total values, which it also
+// checks as the pack does: NaN/Inf (KC_ERR_NONFINITE), else |v| > 2^54
+// (KC_ERR_RANGE; squared distances then stay far below FLT_MAX).  vec: rm is
+// 16-byte aligned.
+__device__ __forceinline__ void absmax_check(float v, float &m, bool &bad, bool &nonfin) {
+    m = fmaxf(m, fabsf(v));
+    if (!(fabsf(v) <= 0x1p54f)) bad = true;   // NaN fails the comparison
+    if (!isfinite(v)) nonfin = true;
+}
+__global__ void tc_absmax_rm_kernel(const float *__restrict__ rm, int64_t total, bool vec, unsigned *absmax,
+                                    DevStatus *st) {
+    float m = 0.f;
+    bool bad = false, nonfin = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nv = vec ? total / 4 : 0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += stride) {
+        const float4 w = __ldg(reinterpret_cast<const float4 *>(rm) + q);
+        absmax_check(w.x, m, bad, nonfin);
+        absmax_check(w.y, m, bad, nonfin);
+        absmax_check(w.z, m, bad, nonfin);
+        absmax_check(w.w, m, bad, nonfin);
+    }
+    for (int64_t e = 4 * nv + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride)
+        absmax_check(rm[e], m, bad, nonfin);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(absmax, __float_as_uint(m));
+    if (nonfin) set_status(st, KC_ERR_NONFINITE, 1, 0);
+    else if (bad) set_status(st, KC_ERR_RANGE, 1, 0);
+}
+
+// Point tiles straight from the row-major array (the pack's work folded in):
+// a CTA stages a tile's rows, one contiguous span of rm, in shared memory
+// (scaled, row stride ld = d | 1, so the per-row reads below are free of bank
+// conflicts), then threads 0..127 compute their row's norm and rounding bound
+// and all threads write the fp16 tile, one 16-byte core-matrix row per store.
+// Values and rounding are those of tc_rows_kernel<TC_M> on the same points.
+constexpr int TC_RM_NT = 256;
+constexpr int TC_RM_V = 8;   // a 128 x 64 FP32 tile is 8 loads per thread
+__global__ void __launch_bounds__(TC_RM_NT) tc_points_rm_kernel(const float *__restrict__ rm, int64_t n, int d,
+                                                                 bool vec, int kp, int64_t ntiles,
+                                                                 const unsigned *absmax, __half *__restrict__ tiles,
+                                                                 float *__restrict__ norm, float *__restrict__ err) {
+    extern __shared__ float sx[];   // [TC_M][ld]
+    const int ld = d | 1;
+    const float sc = tc_scale(absmax, d);
+    const int tid = threadIdx.x;
+    // f / d as a multiply-high: exact for f < 2^14 (a tile's TC_M * d <= 2^14
+    // elements) and d <= 2^7
+    const uint64_t dmag = 0xFFFFFFFFull / (uint64_t)d + 1;
+    auto row_of = [&](int f) { return (int)(((uint64_t)(uint32_t)f * dmag) >> 32); };
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t p0 = t * TC_M;
+        const int rows = (int)((n - p0) < TC_M ? (n - p0) : TC_M);
+        const float *base = rm + p0 * (int64_t)d;
+        const int total = rows * d;
+        const int nv = vec ? total / 4 : 0;
+        __syncthreads();   // the previous tile's reads are done
+        // TC_RM_V 16-byte loads per thread in flight before any is stored
+        for (int q0 = 0; q0 < nv; q0 += TC_RM_V * TC_RM_NT) {
+            float4 w[TC_RM_V];
+#pragma unroll
+            for (int v = 0; v < TC_RM_V; ++v) {
+                const int q = q0 + v * TC_RM_NT + tid;
+                if (q < nv) w[v] = __ldg(reinterpret_cast<const float4 *>(base) + q);
+            }
+#pragma unroll
+            for (int v = 0; v < TC_RM_V; ++v) {
+                const int q = q0 + v * TC_RM_NT + tid;
+                if (q >= nv) break;
+                const float vv[4] = {w[v].x, w[v].y, w[v].z, w[v].w};
+                const int f = 4 * q;
+                int r = row_of(f), j = f - r * d;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    sx[r * ld + j] = __fmul_rn(vv[u], sc);   // exact
+                    if (++j == d) {
+                        j = 0;
+                        ++r;
+                    }
+                }
+            }
+        }
+        for (int f = 4 * nv + tid; f < total; f += TC_RM_NT) {
+            const int r = row_of(f), j = f - r * d;
+            sx[r * ld + j] = __fmul_rn(__ldg(base + f), sc);
+        }
+        for (int f = total + tid; f < TC_M * d; f += TC_RM_NT) {
+            const int r = row_of(f), j = f - r * d;
+            sx[r * ld + j] = 0.f;
+        }
+        __syncthreads();
+        if (tid < TC_M) {
+            const bool valid = tid < rows;
+            float nrm = 0.f, e2 = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < d; ++k) {
+                const float x = sx[tid * ld + k];
+                const float xq = __half2float(__float2half_rn(x));
+                const float df = fabsf(__fsub_rn(x, xq));   // exact (Sterbenz) or x itself
+                e2 = __fmaf_ru(df, df, e2);
+                nrm = __fmaf_rn(xq, xq, nrm);
+            }
+            norm[p0 + tid] = valid ? nrm : INFINITY;
+            err[p0 + tid] = valid ? __fsqrt_ru(e2) : 0.f;
+        }
+        __half *tile = tiles + t * (int64_t)TC_M * kp;
+        const int chunks = TC_M * (kp / 8);
+        for (int c = tid; c < chunks; c += TC_RM_NT) {
+            const int r = c % TC_M, k0 = (c / TC_M) * 8;
+            uint32_t h[4];
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                __half q2[2];
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    const int k = k0 + u + v;
+                    float x = 0.f;
+                    if (k < d) x = sx[r * ld + k];
+                    else if (k == d) x = 32768.f;
+                    else if (k == d + 1) x = 16.f;
+                    else if (k == d + 2) x = 0.0078125f;
+                    q2[v] = __float2half_rn(x);
+                }
+                h[u / 2] = (uint32_t)__half_as_ushort(q2[0]) | ((uint32_t)__half_as_ushort(q2[1]) << 16);
+            }
+            *reinterpret_cast<uint4 *>(tile + core_off(TC_M, r, k0)) = make_uint4(h[0], h[1], h[2], h[3]);
+        }
+    }
+}
+
 // Rows -> fp16 MMA tiles of R rows.  Row i is a point or center: from the
 // packed array (pk) when pk != null, else row idx ? idx[i] : i of the
 // row-major array rm.  Point tiles (R = TC_M) append the multipliers
@@ -603,12 +734,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
 // the FP32-to-FP64 margin) get their exact canonical FP32 minimum (one warp
 // per point, lanes over centers); everyone else gets 0.  The key of the
 // maximum then equals the one the CUDA-core path produces.
-__global__ void tc_exact_kernel(const float *__restrict__ pk, int64_t n, int d, const float *__restrict__ cen,
+__global__ void tc_exact_kernel(const float *__restrict__ pk, const float *__restrict__ rm, int64_t n, int d,
+                                const float *__restrict__ cen,
                                 const int32_t *kc_dev, int kc_max, const float *__restrict__ mhi,
                                 const unsigned *mlo_max, uint32_t *__restrict__ mind, unsigned long long *key32,
                                 const DevStatus *st) {
     if (ld_volatile_i32(&st->code) != 0) return;
     const int kc = kc_dev ? *kc_dev : kc_max;
+    const bool v4 = (d & 3) == 0 && ((uintptr_t)cen & 15) == 0 && (pk || ((uintptr_t)rm & 15) == 0);
     const double T = (double)__uint_as_float(*mlo_max) * (1.0 - 3.0 * f32_gamma(d));
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -624,11 +757,8 @@ __global__ void tc_exact_kernel(const float *__restrict__ pk, int64_t n, int d, 
             todo &= todo - 1;
             const int64_t xs = base + srcl;
             uint32_t m = 0xFFFFFFFFu;
-            for (int ci = lane; ci < kc; ci += 32) {
-                float acc = 0.f;
-                for (int j = 0; j < d; ++j) acc = sq_step(acc, pk[pk_index(xs, j, d)], cen[(int64_t)ci * d + j]);
-                m = min(m, __float_as_uint(acc));
-            }
+            for (int ci = lane; ci < kc; ci += 32)
+                m = min(m, __float_as_uint(point_row_dist(pk, rm, xs, d, cen + (int64_t)ci * d, v4)));
 #pragma unroll
             for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
             if (lane == srcl) {
@@ -771,12 +901,31 @@ cudaError_t launch_tc_points(const float *pk, const float *rm, const uint32_t *i
     return rows<TC_M>(pk, rm, idx, nullptr, n, d, absmax, at, an, ae, nullptr, s);
 }
 
-cudaError_t launch_tc_radius(const float *pk, int64_t n, int d, const float *cen, const int32_t *kc_dev, int kc,
-                             const TcBufs &B, uint32_t *mind, unsigned long long *key32, DevStatus *st,
-                             cudaStream_t s) {
+cudaError_t launch_tc_radius(const float *pk, const float *rm, int64_t n, int d, const float *cen,
+                             const int32_t *kc_dev, int kc, const TcBufs &B, uint32_t *mind,
+                             unsigned long long *key32, DevStatus *st, cudaStream_t s) {
     cudaError_t e;
-    if ((e = launch_tc_absmax(pk, n, d, B.absmax, s)) != cudaSuccess) return e;
-    if ((e = launch_tc_points(pk, nullptr, nullptr, n, d, B.absmax, B.at, B.an, B.ae, s)) != cudaSuccess) return e;
+    if (pk) {
+        if ((e = launch_tc_absmax(pk, n, d, B.absmax, s)) != cudaSuccess) return e;
+        if ((e = launch_tc_points(pk, nullptr, nullptr, n, d, B.absmax, B.at, B.an, B.ae, s)) != cudaSuccess)
+            return e;
+    } else {
+        const bool vec = ((uintptr_t)rm & 15) == 0;
+        cudaMemsetAsync(B.absmax, 0, sizeof(unsigned), s);
+        const int64_t total = n * (int64_t)d;
+        const int ga = (int)std::min<int64_t>(std::max<int64_t>(1, (total / 4 + 255) / 256), (int64_t)sms() * 8);
+        tc_absmax_rm_kernel<<<ga, 256, 0, s>>>(rm, total, vec, B.absmax, st);
+        const int64_t nt = (n + TC_M - 1) / TC_M;
+        const size_t sm = (size_t)TC_M * (d | 1) * sizeof(float);
+        if ((e = cudaFuncSetAttribute(tc_points_rm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
+            cudaSuccess)
+            return e;
+        const int gp = (int)std::min<int64_t>(nt, (int64_t)sms() * 8);
+        tc_points_rm_kernel<<<gp, TC_RM_NT, sm, s>>>(rm, n, d, vec, kpad(d), nt, B.absmax, (__half *)B.at, B.an,
+                                                      B.ae);
+        note_launches(2);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if ((e = launch_tc_centers(cen, kc_dev, kc, d, B.absmax, B.bt, B.cn, B.ce, B.maxes, s)) != cudaSuccess) return e;
     TcArgs a{};
     a.d = d;
@@ -804,7 +953,7 @@ cudaError_t launch_tc_radius(const float *pk, int64_t n, int d, const float *cen
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms());
     tc_dmin_kernel<0><<<grid, TC_THREADS, smem, s>>>(a);
     const int g2 = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms() * 8);
-    tc_exact_kernel<<<g2, 256, 0, s>>>(pk, n, d, cen, kc_dev, kc, B.mhi, B.mlomax, mind, key32, st);
+    tc_exact_kernel<<<g2, 256, 0, s>>>(pk, rm, n, d, cen, kc_dev, kc, B.mhi, B.mlomax, mind, key32, st);
     note_launches(2);
     return cudaGetLastError();
 }

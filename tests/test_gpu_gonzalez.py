@@ -239,6 +239,39 @@ def test_radius_tensor_core_zero_norms_and_exact_hits(kc, monkeypatch):
     assert rr.radius == r64 and rr.argmax == am
 
 
+@pytest.mark.parametrize("d", [7, 64])
+def test_radius_tensor_core_row_major_sources(kc, monkeypatch, d):
+    # the tensor-core radius reads row-major points without a pack: an
+    # unaligned device view (4-byte shift), host memory (pageable and pinned)
+    import torch
+    n = 3 * 128 + 77
+    pts = I.gauss_mixture(n, d, 500 + d, 9, 1.0, -4, 4)
+    C = I.uniform_int(64, d, 300, 0, n - 1)
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    flat = torch.from_numpy(np.concatenate([np.zeros(1, np.float32), pts.ravel()])).cuda()
+    view = flat[1:].view(n, d)
+    assert view.data_ptr() % 16 != 0
+    for src in (view, pts, torch.from_numpy(pts).pin_memory()):
+        rr = kc.kc_radius(src, _dev(C))
+        assert rr.radius == r64 and rr.argmax == am
+
+
+@pytest.mark.parametrize("bad,status", [(np.nan, "KC_ERR_NONFINITE"), (np.inf, "KC_ERR_NONFINITE"),
+                                        (1.0e30, "KC_ERR_RANGE")])
+def test_radius_tensor_core_checks_inputs(kc, monkeypatch, bad, status):
+    # without a pack the tensor-core prep performs the pack's checks
+    pts = I.gauss_mixture(1000, 16, 65, 4, 1.0, -1, 1)
+    pts[777, 5] = bad
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    with pytest.raises(kc.KCError) as e:
+        kc.kc_radius(_dev(pts), _dev(np.arange(0, 1000, 3)))
+    assert e.value.status == getattr(kc, status)
+    ok = I.gauss_mixture(1000, 16, 66, 4, 1.0, -1, 1)
+    C = np.arange(0, 1000, 3)
+    assert kc.kc_radius(_dev(ok), _dev(C)).radius == O.radius(ok, C, mode="f64")[0]
+
+
 def test_pinned_host_points_read_in_place(kc):
     # page-locked host memory is read by the pack kernel directly (no staging copy)
     import torch
