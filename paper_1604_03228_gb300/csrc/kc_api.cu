@@ -1283,6 +1283,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
             Ptc.tc_at = cv.take<char>(tc_point_bytes(n, d));
             Ptc.tc_an = cv.take<float>((size_t)tc_point_rows(n));
             Ptc.tc_ae = cv.take<float>((size_t)tc_point_rows(n));
+            Ptc.tc_rin = cv.take<uint8_t>((size_t)tc_point_rows(n));
             Ptc.tc_bt = cv.take<char>(tc_center_bytes(n, d));
             Ptc.tc_cn = cv.take<float>((size_t)tc_center_tiles(n) * 256);
             Ptc.tc_ce = cv.take<float>((size_t)tc_center_tiles(n) * 256);

@@ -394,6 +394,7 @@ struct RadiusArgs {
     void *tc_at, *tc_bt;
     float *tc_an, *tc_ae, *tc_cn, *tc_ce, *tc_mlo, *tc_mhi;
     unsigned *tc_maxes, *tc_absmax, *tc_mlomax;
+    uint8_t *tc_rin;         // prune only: per point row, 1 when the point is in S
 };
 
 // ------------------------------------------------- tensor-core blocks
@@ -406,10 +407,11 @@ struct TcBufs {
     unsigned *maxes, *absmax;
     float *mlo, *mhi;
     unsigned *mlomax;
+    uint8_t *rin;   // prune: per point row, 1 when the point is in S (null for the radius)
 };
 inline TcBufs tc_bufs(const RadiusArgs &a) {
     return TcBufs{a.tc_at, a.tc_bt, a.tc_an, a.tc_ae, a.tc_cn, a.tc_ce, a.tc_maxes, a.tc_absmax, a.tc_mlo, a.tc_mhi,
-                  a.tc_mlomax};
+                  a.tc_mlomax, a.tc_rin};
 }
 bool tc_supported(int d);
 cudaError_t read_tc_counters(unsigned long long out[2], bool reset);

@@ -18,15 +18,17 @@
 //
 // Kernel.  One persistent CTA per SM (it holds all 512 TMEM columns).  Warps:
 //   8    producer: cp.async.bulk of point tiles (2-stage ring) and center
-//        tiles (2-stage ring) into shared memory
+//        tiles (all of them once when they fit, else a 2-stage ring) into
+//        shared memory
 //   9    MMA issuer (one thread): tcgen05.mma.kind::f16, M=128 x N=256,
 //        Kp/16 instructions per tile pair, FP32 accumulators double-buffered
 //        in TMEM (2 x 256 columns)
 //   0-7  epilogue: warps w and w+4 own point rows 32(w%4).. (their TMEM
-//        lanes) and split the 256 columns; each thread software-pipelines its
-//        32-column TMEM loads and folds v into a running maximum three values
-//        at a time (radius) or compares it with the point's two decision
-//        limits (prune).
+//        lanes) and split the 256 columns; each thread loads its 128 columns
+//        as three 32-column loads behind one wait and a fourth in flight
+//        while those are used, releases the accumulator, and folds v into a
+//        running maximum three values at a time (radius) or compares it with
+//        the point's two decision limits (prune).
 // Shared-memory operand layout: no swizzle, K-major, 8 x 16-byte core
 // matrices; core matrix (row block mi, column block ki) of an R-row tile at
 // byte ((ki * R/8) + mi) * 128: the descriptor's leading (K) byte offset is
@@ -154,6 +156,17 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&r)[32]) {
                  : "memory");
 }
 
+// After tmem_wait_ld on another array: keeps every use of r below that wait
+// (volatile asm statements keep their order).
+__device__ __forceinline__ void tmem_pin(uint32_t (&r)[32]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31]));
+}
+
 __device__ __forceinline__ float max3f(float a, float b, float c) {
     float r;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -267,12 +280,18 @@ __global__ void __launch_bounds__(TC_RM_NT) tc_points_rm_kernel(const float *__r
                 const float vv[4] = {w[v].x, w[v].y, w[v].z, w[v].w};
                 const int f = 4 * q;
                 int r = row_of(f), j = f - r * d;
+                if ((d & 3) == 0) {   // the four values share a row
+                    float *dst = sx + r * ld + j;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    sx[r * ld + j] = __fmul_rn(vv[u], sc);   // exact
-                    if (++j == d) {
-                        j = 0;
-                        ++r;
+                    for (int u = 0; u < 4; ++u) dst[u] = __fmul_rn(vv[u], sc);   // exact
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        sx[r * ld + j] = __fmul_rn(vv[u], sc);
+                        if (++j == d) {
+                            j = 0;
+                            ++r;
+                        }
                     }
                 }
             }
@@ -305,6 +324,16 @@ __global__ void __launch_bounds__(TC_RM_NT) tc_points_rm_kernel(const float *__r
         for (int c = tid; c < chunks; c += TC_RM_NT) {
             const int r = c % TC_M, k0 = (c / TC_M) * 8;
             uint32_t h[4];
+            if (k0 + 8 <= d) {   // coordinates only
+                const float *row = sx + r * ld + k0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const __half2 q = __floats2half2_rn(row[2 * u], row[2 * u + 1]);
+                    h[u] = *reinterpret_cast<const uint32_t *>(&q);
+                }
+                *reinterpret_cast<uint4 *>(tile + core_off(TC_M, r, k0)) = make_uint4(h[0], h[1], h[2], h[3]);
+                continue;
+            }
 #pragma unroll
             for (int u = 0; u < 8; u += 2) {
                 __half q2[2];
@@ -331,12 +360,14 @@ __global__ void __launch_bounds__(TC_RM_NT) tc_points_rm_kernel(const float *__r
 // (2^15, 2^4, 2^-7) at columns d, d+1, d+2; center tiles (R = TC_N) store
 // 2 c~ and the three fp16 pieces of -|c~|^2 there.  Rows past the count:
 // zero coordinates, -inf pieces (centers), norm +inf.  maxes (optional) gets
-// the largest e, the largest norm and the largest split residual r_c.
+// the largest e, the largest norm and the largest split residual r_c.  rin
+// (optional, with idx and inS): per row, inS[idx[i]] (0 past the count).
 template <int R>
 __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__restrict__ rm,
                                const uint32_t *__restrict__ idx, const int32_t *cnt_dev, int64_t cnt_max, int d,
                                int kp, int64_t ntiles, const unsigned *absmax, __half *__restrict__ tiles,
-                               float *__restrict__ norm, float *__restrict__ err, unsigned *maxes) {
+                               float *__restrict__ norm, float *__restrict__ err, unsigned *maxes,
+                               const uint8_t *__restrict__ inS, uint8_t *__restrict__ rin) {
     constexpr bool CENTER = R == TC_N;
     const int64_t cnt = cnt_dev ? (int64_t)*cnt_dev : cnt_max;
     const float sc = tc_scale(absmax, d);
@@ -406,6 +437,7 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
         const float e = __fsqrt_ru(e2);
         norm[i] = valid ? nrm : INFINITY;
         err[i] = valid ? e : 0.f;
+        if (rin) rin[i] = valid && inS[g] != 0 ? 1 : 0;
         if (maxes && valid) {
             atomicMax(&maxes[0], __float_as_uint(e));
             atomicMax(&maxes[1], __float_as_uint(nrm));
@@ -416,6 +448,7 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
 
 struct TcArgs {
     int d, kp, kc, ntiles;      // centers: kc real of ntiles * TC_N rows
+    int resident;               // all center tiles stay in shared memory (loaded once)
     int64_t npts;               // points (rows of the A tiles)
     const __half *at;           // point tiles [ceil(npts/128)][128 x kp]
     const float *an, *ae;       // point norms and bounds
@@ -429,7 +462,7 @@ struct TcArgs {
     // prune
     const float *src;           // row-major FP32 points
     const uint32_t *R;          // point indices of the rows
-    const uint8_t *inS;         // sampled points (always removed)
+    const uint8_t *rin;         // per point row: the point is sampled (always removed)
     const float *cen;           // FP32 center rows (exact rechecks)
     const uint32_t *thr;        // threshold (canonical FP32 bits)
     uint32_t *Rn;               // kept points
@@ -447,8 +480,11 @@ __device__ __forceinline__ float tc_eta(int d, int kp) {
     return (float)(f32_gamma(d) + (double)(kp + 16) * 0x1p-21 + 0x1p-21);
 }
 
+// Launch bounds of 384 threads for a 320-thread launch: they cap the
+// registers at 168 per thread, so that the SM sub-partition holding three of
+// the ten warps has room for them (3 x 32 x 168 <= 16384).
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
+__global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int kp = a.kp;
     const uint32_t a_bytes = (uint32_t)TC_M * kp * 2, b_bytes = (uint32_t)TC_N * kp * 2;
@@ -505,6 +541,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                 mbar_expect_tx(&a_full[sa], a_bytes);
                 bulk_g2s(sAb + sa * a_bytes, a.at + pt * (int64_t)TC_M * kp, a_bytes, &a_full[sa]);
                 afill ^= 1u << sa;
+                if (a.resident) {
+                    if (p == 0) {   // every center tile, once, behind the first point tile
+                        mbar_expect_tx(&b_full[0], (uint32_t)a.ntiles * b_bytes);
+                        for (int t = 0; t < a.ntiles; ++t)
+                            bulk_g2s(sBb + t * b_bytes, a.bt + (int64_t)t * TC_N * kp, b_bytes, &b_full[0]);
+                    }
+                    continue;
+                }
                 for (int t = 0; t < a.ntiles; ++t, ++u) {
                     const int s = (int)(u & 1);
                     if (!mbar_wait(&b_empty[s], ((bfill >> s) & 1u) ^ 1u, abort)) {
@@ -534,20 +578,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                 }
                 for (int t = 0; t < a.ntiles; ++t, ++u) {
                     const int s = (int)(u & 1);
-                    if (!mbar_wait(&t_empty[s], ((tuse >> s) & 1u) ^ 1u, abort) ||
-                        !mbar_wait(&b_full[s], (buse >> s) & 1u, abort)) {
+                    // resident center tiles: one barrier phase, completed once
+                    const bool bok = a.resident ? (p > 0 || t > 0 || mbar_wait(&b_full[0], 0u, abort))
+                                                : mbar_wait(&b_full[s], (buse >> s) & 1u, abort);
+                    if (!mbar_wait(&t_empty[s], ((tuse >> s) & 1u) ^ 1u, abort) || !bok) {
                         *abort = 1;
                         set_status(a.st, KC_ERR_TIMEOUT, 8, t);
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t abase = smem_u32(sAb + sa * a_bytes), bbase = smem_u32(sBb + s * b_bytes);
+                    const uint32_t abase = smem_u32(sAb + sa * a_bytes);
+                    const uint32_t bbase = smem_u32(sBb + (a.resident ? t : s) * b_bytes);
                     for (int kk = 0; kk < kp / 16; ++kk) {
                         const uint64_t ad = umma_desc(abase + kk * 2 * a_lbo, a_lbo, 128);
                         const uint64_t bd = umma_desc(bbase + kk * 2 * b_lbo, b_lbo, 128);
                         umma_f16(tmem + (uint32_t)(s * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
                     }
-                    umma_commit(&b_empty[s]);
+                    if (!a.resident) umma_commit(&b_empty[s]);
                     umma_commit(&t_full[s]);
                     buse ^= 1u << s;
                     tuse ^= 1u << s;
@@ -573,18 +620,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
         const float rmax = __uint_as_float(a.maxes[2]);
         uint32_t tuse = 0;   // bit s: parity of TMEM stage s's uses so far
         int64_t u = 0;
+        // the row's norm, bound, index and sample flag are loaded one point
+        // tile ahead, so that no global load waits at the top of a tile
+        float nx_n = 0.f, ae_n = 0.f;
+        uint32_t gx_n = 0, in_n = 0;
+        auto fetch = [&](int64_t pt) {
+            const int64_t pi = pt * TC_M + row;
+            if (pt < ntile_pts && pi < a.npts) {
+                nx_n = a.an[pi];
+                ae_n = a.ae[pi];
+                if (MODE == 1) {
+                    gx_n = a.R[pi];
+                    in_n = a.rin[pi];
+                }
+            }
+        };
+        fetch(blockIdx.x);
+        float lomax = 0.f;              // radius: largest lower bound of this thread's rows
+        unsigned long long nrows = 0;   // prune: rows processed (diagnostics)
         for (int64_t pt = blockIdx.x; pt < ntile_pts; pt += gridDim.x) {
             const int64_t pi = pt * TC_M + row;
             const bool valid = pi < a.npts;
-            const float xn = valid ? a.an[pi] : 0.f;
-            const float sl = __fadd_ru(valid ? a.ae[pi] : 0.f, E);
+            const float xn = valid ? nx_n : 0.f;
+            const float sl = __fadd_ru(valid ? ae_n : 0.f, E);
             const float eps = __fadd_ru(__fmul_ru(eta, __fadd_ru(xn, cnmax2)), rmax);
             int64_t gx = 0;
             bool removed = !valid;
+            if (MODE == 1 && valid) {
+                gx = (int64_t)gx_n;
+                removed = in_n != 0;
+            }
+            fetch(pt + gridDim.x);
             float vlo = INFINITY, vhi = INFINITY;
             if (MODE == 1 && valid) {
-                gx = (int64_t)a.R[pi];
-                removed = a.inS[gx] != 0;
                 // s~ = xn - v; v >= vlo: s~ small enough that d(x,c) <= thr
                 // surely; v < vhi: d(x,c) > thr surely; between: exact check
                 const float thr = __fmul_rn(__uint_as_float(*a.thr), sc2);   // scaled, exact
@@ -656,24 +724,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 cbase = t * TC_N + grp * TC_COLS;
                 if (MODE == 1 && !removed && s_gone_v[row]) removed = true;   // another group decided
+                bool released = false;
                 if (MODE == 0 || !__all_sync(0xFFFFFFFFu, removed)) {
-                    // the next chunk's TMEM load is in flight while this one is used
+                    // three 32-column loads behind one wait, the fourth in
+                    // flight while they are used; the accumulator buffer is
+                    // released as soon as the last load has landed
+                    static_assert(TC_COLS == 128, "four 32-column chunks per thread");
                     const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(s * TC_N + grp * TC_COLS);
-                    uint32_t ra[32], rb[32];
+                    uint32_t ra[32], rb[32], rc[32];
                     tmem_ld32(taddr, ra);
+                    tmem_ld32(taddr + 32, rb);
+                    tmem_ld32(taddr + 64, rc);
                     tmem_wait_ld(ra);
-#pragma unroll
-                    for (int c0 = 0; c0 < TC_COLS; c0 += 64) {
-                        tmem_ld32(taddr + c0 + 32, rb);
-                        chunk(ra, c0);
-                        tmem_wait_ld(rb);
-                        if (c0 + 64 < TC_COLS) tmem_ld32(taddr + c0 + 64, ra);
-                        chunk(rb, c0 + 32);
-                        if (c0 + 64 < TC_COLS) tmem_wait_ld(ra);
-                    }
+                    tmem_pin(rb);
+                    tmem_pin(rc);
+                    chunk(ra, 0);
+                    tmem_ld32(taddr + 96, ra);
+                    chunk(rb, 32);
+                    chunk(rc, 64);
+                    tmem_wait_ld(ra);
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(&t_empty[s]);
+                    released = true;
+                    chunk(ra, 96);
                 }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                mbar_arrive(&t_empty[s]);
+                if (!released) {
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(&t_empty[s]);
+                }
                 tuse ^= 1u << s;
             }
             // combine the column groups of every row in group 0
@@ -701,7 +779,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                     const float lo_u = __fmul_rd(lo, isc2), hi_u = __fmul_ru(hi, isc2);
                     a.mlo[pi] = lo_u;
                     a.mhi[pi] = hi_u;
-                    atomicMax(a.mlo_max, __float_as_uint(lo_u));
+                    lomax = fmaxf(lomax, lo_u);
                 } else if (!(removed || s_gone[row] != 0)) {
                     const int pf = s_pend[row] | (emitted ? 1 : 0) | (ovf ? 2 : 0);
                     if (pf) {
@@ -718,8 +796,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_dmin_kernel(TcArgs a) {
                 s_pend[row] = 0;
             }
             if (MODE == 1 && namb) atomicAdd(&g_tc_counters[0], namb);
-            if (MODE == 1 && grp == 0 && valid) atomicAdd(&g_tc_counters[1], 1ull);
+            if (MODE == 1 && grp == 0 && valid) ++nrows;
             asm volatile("bar.sync 1, %0;" ::"n"(TC_EPI) : "memory");   // s_* reused by the next tile
+        }
+        // one atomic per warp (the lower bounds are non-negative: their bits order as the values)
+        if (MODE == 0) {
+            const unsigned m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(lomax));
+            if (lane == 0 && grp == 0) atomicMax(a.mlo_max, m);
+        } else {
+            const unsigned long long r = __reduce_add_sync(0xFFFFFFFFu, (unsigned)nrows);
+            if (lane == 0 && r) atomicAdd(&g_tc_counters[1], r);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -845,20 +931,32 @@ int kpad(int d) { return (d + 3 + 15) / 16 * 16; }
 
 // Dynamic shared memory: two point tiles and two center tiles, and at least
 // 120 KB so that one CTA (holding all 512 TMEM columns) runs per SM.
-size_t tc_smem(int kp) {
-    const size_t need = (size_t)2 * TC_M * kp * 2 + (size_t)2 * TC_N * kp * 2;
-    return need > 120 * 1024 ? need : 120 * 1024;
+// Dynamic shared memory of a launch over ntiles center tiles: a two-stage
+// point-tile ring and either every center tile (resident, loaded once) or a
+// two-stage center ring; at least 120 KB, so that one CTA holds the SM (and
+// all 512 TMEM columns).  A third point stage (when it fits beside resident
+// centers) measured slower: the larger shared-memory carve-out leaves less
+// L1.
+constexpr size_t TC_SMEM_MAX = 220 * 1024;
+size_t tc_smem_for(TcArgs &a) {
+    const size_t A = (size_t)TC_M * a.kp * 2, B = (size_t)TC_N * a.kp * 2;
+    const size_t centers = (size_t)a.ntiles * B;
+    a.resident = 2 * A + centers <= TC_SMEM_MAX && !getenv("KC_TC_STREAM_CENTERS") ? 1 : 0;
+    const size_t need = 2 * A + (a.resident ? centers : 2 * B);
+    const size_t floor1 = 120 * 1024;   // one CTA per SM
+    return need > floor1 ? need : floor1;
 }
 
 template <int R>
 cudaError_t rows(const float *pk, const float *rm, const uint32_t *idx, const int32_t *cnt_dev, int64_t cnt, int d,
-                 const unsigned *absmax, void *tiles, float *norm, float *err, unsigned *maxes, cudaStream_t s) {
+                 const unsigned *absmax, void *tiles, float *norm, float *err, unsigned *maxes, cudaStream_t s,
+                 const uint8_t *inS = nullptr, uint8_t *rin = nullptr) {
     const int64_t nt = (cnt + R - 1) / R;
     if (nt == 0) return cudaSuccess;
     const int64_t rowsn = nt * R;
     const int grid = (int)std::min<int64_t>((rowsn + 255) / 256, (int64_t)sms() * 8);
     tc_rows_kernel<R><<<grid, 256, 0, s>>>(pk, rm, idx, cnt_dev, cnt, d, kpad(d), nt, absmax, (__half *)tiles, norm, err,
-                                           maxes);
+                                           maxes, inS, rin);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -897,8 +995,9 @@ cudaError_t launch_tc_centers(const float *cen_rows, const int32_t *kc_dev, int6
 }
 
 cudaError_t launch_tc_points(const float *pk, const float *rm, const uint32_t *idx, int64_t n, int d,
-                             const unsigned *absmax, void *at, float *an, float *ae, cudaStream_t s) {
-    return rows<TC_M>(pk, rm, idx, nullptr, n, d, absmax, at, an, ae, nullptr, s);
+                             const unsigned *absmax, void *at, float *an, float *ae, cudaStream_t s,
+                             const uint8_t *inS = nullptr, uint8_t *rin = nullptr) {
+    return rows<TC_M>(pk, rm, idx, nullptr, n, d, absmax, at, an, ae, nullptr, s, inS, rin);
 }
 
 cudaError_t launch_tc_radius(const float *pk, const float *rm, int64_t n, int d, const float *cen,
@@ -944,7 +1043,7 @@ cudaError_t launch_tc_radius(const float *pk, const float *rm, int64_t n, int d,
     a.mhi = B.mhi;
     a.mlo_max = B.mlomax;
     a.st = st;
-    const size_t smem = tc_smem(a.kp);
+    const size_t smem = tc_smem_for(a);
     if ((e = cudaFuncSetAttribute(tc_dmin_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
@@ -962,7 +1061,8 @@ cudaError_t launch_tc_prune(const float *src, int d, const uint32_t *R, int64_t 
                             int64_t sn, const TcBufs &B, const PruneBufs &P, const uint32_t *thr, uint32_t *Rn,
                             unsigned long long *rnn, DevStatus *st, cudaStream_t s) {
     cudaError_t e;
-    if ((e = launch_tc_points(nullptr, src, R, rn, d, B.absmax, B.at, B.an, B.ae, s)) != cudaSuccess) return e;
+    if ((e = launch_tc_points(nullptr, src, R, rn, d, B.absmax, B.at, B.an, B.ae, s, inS, B.rin)) != cudaSuccess)
+        return e;
     if ((e = launch_tc_centers(Scen, nullptr, sn, d, B.absmax, B.bt, B.cn, B.ce, B.maxes, s)) != cudaSuccess) return e;
     cudaMemsetAsync(P.npairs, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(P.npend, 0, sizeof(unsigned long long), s);
@@ -982,7 +1082,7 @@ cudaError_t launch_tc_prune(const float *src, int d, const uint32_t *R, int64_t 
     a.absmax = B.absmax;
     a.src = src;
     a.R = R;
-    a.inS = inS;
+    a.rin = B.rin;
     a.cen = Scen;
     a.thr = thr;
     a.Rn = Rn;
@@ -994,7 +1094,7 @@ cudaError_t launch_tc_prune(const float *src, int d, const uint32_t *R, int64_t 
     a.pend = P.pend;
     a.npend = P.npend;
     a.st = st;
-    const size_t smem = tc_smem(a.kp);
+    const size_t smem = tc_smem_for(a);
     if ((e = cudaFuncSetAttribute(tc_dmin_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
