@@ -73,6 +73,12 @@ def parse():
     ap.add_argument("--n", type=int, default=0,
                     help="other workloads: fewer points than the configuration's (small profiling cases)")
     ap.add_argument("--k", type=int, default=0, help="8M x 64 workloads: another k (small profiling cases)")
+    ap.add_argument("--report", choices=["k", "phi"], default=None,
+                    help="instead of a bench line: runtime and solution value over k for GON, MRG and EIM "
+                         "(k), or EIM over phi (phi), on 2-D sets shaped like the paper's; JSON rows on "
+                         "stdout, tables on stderr")
+    ap.add_argument("--seeds", type=int, default=3, help="--report: sets drawn per shape")
+    ap.add_argument("--runs", type=int, default=2, help="--report: runs per set and method")
     return ap.parse_args()
 
 
@@ -487,9 +493,30 @@ def run_extra(args):
     print(json.dumps(line), flush=True)
 
 
+def run_report(args):
+    """The k / phi sweeps of paper_1604_03228_gb300.report on one GPU."""
+    import torch
+    from paper_1604_03228_gb300 import report
+    assert torch.cuda.is_available(), "--report needs a CUDA device"
+    if args.report == "k":
+        rows, bad = report.k_sweep(seeds=args.seeds, runs=args.runs)
+    else:
+        rows, bad = report.phi_sweep(seeds=args.seeds, runs=args.runs)
+    for r in rows:
+        print(json.dumps(r), flush=True)
+    log(report.markdown(rows))
+    log(f"guarantee violations: {len(bad)}")
+    for v in bad:
+        log("  " + v)
+    if bad:
+        sys.exit(1)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.report:
+        run_report(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload != WORKLOAD:
         run_extra(args)
