@@ -369,11 +369,19 @@ cudaError_t launch_eim_prune(int dtype, const void *src, int d, const uint32_t *
                              const void *Sc, int64_t sn, const uint32_t *thr, uint32_t *Rn, unsigned long long *rnn,
                              cudaStream_t s) {
     if (dtype == KC_F32) {
-        if (d <= 16) run_prune<float, 16>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
+        // the coordinate count rounded up to a power of two (zero terms are
+        // still evaluated, so a tight bound matters most at small d)
+        if (d <= 2) run_prune<float, 2>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
+        else if (d <= 4) run_prune<float, 4>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
+        else if (d <= 8) run_prune<float, 8>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
+        else if (d <= 16) run_prune<float, 16>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
         else if (d <= 64) run_prune<float, 64>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
         else prune_generic_kernel<float><<<grid_for(rn, 256), 256, 0, s>>>((const float *)src, d, R, rn, inS, (const float *)Sc, sn, thr, Rn, rnn);
     } else {
-        if (d <= 16) run_prune<int32_t, 16>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
+        if (d <= 2) run_prune<int32_t, 2>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
+        else if (d <= 4) run_prune<int32_t, 4>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
+        else if (d <= 8) run_prune<int32_t, 8>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
+        else if (d <= 16) run_prune<int32_t, 16>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
         else if (d <= 64) run_prune<int32_t, 64>(src, d, R, rn, inS, Sc, sn, thr, Rn, rnn, s);
         else prune_generic_kernel<int32_t><<<grid_for(rn, 256), 256, 0, s>>>((const int32_t *)src, d, R, rn, inS, (const int32_t *)Sc, sn, thr, Rn, rnn);
     }

@@ -61,6 +61,16 @@ def test_eim_float_dims(kc, n, d, k):
     check_eim(kc, pts, k, expect_loop=True)
 
 
+@pytest.mark.parametrize("d", [2, 3, 5, 8, 13])
+@pytest.mark.parametrize("tc", ["0", "1"])
+def test_eim_prune_paths_small_d(kc, monkeypatch, d, tc):
+    # both prune paths where the default is the CUDA cores (d < 16); each
+    # CUDA-core width (2, 4, 8, 16 coordinates) and the tensor-core blocks
+    monkeypatch.setenv("KC_PRUNE_TC", tc)
+    pts = I.gauss_mixture(20000, d, 80 + d, 25, 0.1, 0, 100)
+    check_eim(kc, pts, 6, expect_loop=True)
+
+
 def test_eim_eps_variants(kc):
     pts = I.gauss_mixture(30000, 5, 73, 20, 0.2, -3, 3)
     for eps in (0.05, 0.2):
@@ -79,6 +89,7 @@ def test_eim_tc_prune_deferred_pairs(kc, monkeypatch, cap):
     # undecided and the deferred exact check decides them.  cap=1 overflows
     # the pair buffer at once, so the full-scan route decides those rows.
     pts = I.int_points(40000, 8, 19, 0, 20).astype(np.float32)
+    monkeypatch.setenv("KC_PRUNE_TC", "1")   # d = 8 takes the CUDA cores by default
     if cap is not None:
         monkeypatch.setenv("KC_PRUNE_PAIR_CAP", cap)
     kc.kc_counters()
