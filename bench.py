@@ -44,11 +44,12 @@ FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 
 # Further workloads (one JSON line each, same keys): the int GON latency case,
-# GON / MRG on 10M x 16, GON / tensor-core radius / EIM on 8M x 64, and the
-# 4,096-instance batch.
+# GON / MRG on 10M x 16, GON / tensor-core radius / EIM on 8M x 64, the
+# 4,096-instance batch, and the same instances as one kc_gonzalez call each
+# (the unbatched baseline of the batch).
 EXTRA = ("gon_int_n10000_d2_k10", "gon_unif_n10000000_d16_k200", "mrg_unif_n10000000_d16_m64_k200",
          "gon_gau_n8000000_d64_k1024", "radius_gau_n8000000_d64_k1024", "eim_gau_n8000000_d64_k1024",
-         "batch_4096")
+         "batch_4096", "batch_4096_per_call")
 
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from an
 # ncu capture, keyed by the SHA-256 of the kernel's source file at capture
@@ -417,6 +418,18 @@ def run_extra(args):
             dom, bound = "eim_prune", "tensor"
             evals, units = None, None                   # from the prune counters below
             cfg.update(eps=0.1, phi=6.0, seed=40, metric_note="evals = prune |R| x |S| + GON on the sample + radius")
+    elif name == "batch_4096_per_call":
+        insts = [I.batch_instance(i) for i in range(4096)]
+        xs = [dev(z.points) for z in insts]
+        ks = [z.k for z in insts]
+
+        def step():
+            for xi, ki in zip(xs, ks):
+                kc.kc_gonzalez(xi, ki, sweep=sw)
+        evals = sum(z.points.shape[0] * min(z.k, z.points.shape[0]) for z in insts)
+        units = sum(z.points.shape[0] * min(z.k, z.points.shape[0]) * (z.points.shape[1] * bpc + mind_b)
+                    for z in insts)
+        cfg.update(count=4096, step="one synchronous kc_gonzalez call per instance, in order")
     elif name == "batch_4096":
         insts = [I.batch_instance(i) for i in range(4096)]
         xs = [dev(z.points) for z in insts]

@@ -43,6 +43,25 @@
  *    give up after a time budget and return KC_ERR_TIMEOUT; nothing traps.
  *  - Every failure is a status code; kc_last_error() describes the last one
  *    on the calling thread.  No function aborts the process.
+ *
+ * Environment (tuning and testing; none of these changes a result)
+ * ----------------------------------------------------------------
+ *  KC_RADIUS_TC=0|1          covering radius on CUDA cores / on the tensor-core
+ *                            blocks (default: tensor cores for float points
+ *                            when k * d >= 8192 and d <= 128)
+ *  KC_PRUNE_TC=0|1           EIM prune on CUDA cores / tensor cores (default:
+ *                            tensor cores for float points, 16 <= d <= 128,
+ *                            |S| >= 256)
+ *  KC_TC_STREAM_CENTERS=1    tensor-core blocks stream the center tiles through
+ *                            a two-stage ring even when all of them fit in
+ *                            shared memory
+ *  KC_PRUNE_PAIR_CAP=N       capacity of the tensor-core prune's buffer of
+ *                            undecided pairs (rows past it get a full exact
+ *                            scan)
+ *  KC_GON_GRID=G             CTAs of a single Gonzalez launch (clamped to the
+ *                            co-resident maximum)
+ *  KC_BATCH_THETA=x|inf      the batch split of kc_gonzalez_batch and batch
+ *                            plans (see there); overrides the tuned value
  */
 #ifndef KCENTER_H
 #define KCENTER_H

@@ -97,6 +97,15 @@ def test_eim_tc_prune_deferred_pairs(kc, monkeypatch, cap):
     assert kc.kc_counters()[2] > 0
 
 
+@pytest.mark.parametrize("stream", [None, "1"])
+def test_eim_tc_prune_center_ring(kc, monkeypatch, stream):
+    # the sample S through the two-stage center ring and resident
+    if stream:
+        monkeypatch.setenv("KC_TC_STREAM_CENTERS", stream)
+    pts = I.gauss_mixture(40000, 24, 77, 60, 0.5, -10, 10)
+    check_eim(kc, pts, 5, expect_loop=True)
+
+
 def test_eim_tc_prune_matches_cuda_cores(kc, monkeypatch):
     pts = I.gauss_mixture(60000, 32, 75, 100, 0.5, -10, 10)
     a = kc.kc_eim(_dev(pts), 8, eps=0.1, phi=6.0, seed=41)

@@ -206,6 +206,18 @@ def test_radius_tensor_core_matches_cuda_cores(kc, n, d, kc_, monkeypatch):
     assert a.radius == b.radius == r64 and a.argmax == b.argmax == am
 
 
+@pytest.mark.parametrize("n,d,kc_", [(30000, 64, 1000), (9000, 17, 513), (6000, 1, 300)])
+def test_radius_tensor_core_streamed_centers(kc, n, d, kc_, monkeypatch):
+    # the two-stage center ring (the default keeps these center sets resident)
+    pts = I.gauss_mixture(n, d, 300 + d, 11, 0.7, -15, 15)
+    C = I.uniform_int(58, d, kc_, 0, n - 1)
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    monkeypatch.setenv("KC_TC_STREAM_CENTERS", "1")
+    rr = kc.kc_radius(_dev(pts), _dev(C))
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    assert rr.radius == r64 and rr.argmax == am
+
+
 def test_radius_tensor_core_ties_and_far_points(kc):
     # duplicated points, centers among them, and a point far away
     base = I.gauss_mixture(500, 12, 58, 4, 0.3, -2, 2)
