@@ -363,6 +363,8 @@ void take_tc(Carve &cv, RadiusArgs &ra, int dtype, int64_t n, int d, int kc) {
     ra.tc_mlo = cv.take<float>((size_t)n);
     ra.tc_mhi = cv.take<float>((size_t)n);
     ra.tc_mlomax = cv.take<unsigned>(1);
+    ra.tc_flist = cv.take<uint32_t>((size_t)n);
+    ra.tc_fcount = cv.take<unsigned long long>(1);
 }
 
 void copy_tc(RadiusArgs &dst, const RadiusArgs &src) {
@@ -377,6 +379,8 @@ void copy_tc(RadiusArgs &dst, const RadiusArgs &src) {
     dst.tc_mlo = src.tc_mlo;
     dst.tc_mhi = src.tc_mhi;
     dst.tc_mlomax = src.tc_mlomax;
+    dst.tc_flist = src.tc_flist;
+    dst.tc_fcount = src.tc_fcount;
 }
 
 // Point an instance at the low-precision data (its own cenT [d][kcap] and

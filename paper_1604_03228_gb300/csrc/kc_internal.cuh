@@ -395,6 +395,10 @@ struct RadiusArgs {
     float *tc_an, *tc_ae, *tc_cn, *tc_ce, *tc_mlo, *tc_mhi;
     unsigned *tc_maxes, *tc_absmax, *tc_mlomax;
     uint8_t *tc_rin;         // prune only: per point row, 1 when the point is in S
+    // radius: the points that can reach the maximum ([n] slots and their
+    // count); the FP64 recheck then visits only these
+    uint32_t *tc_flist;
+    unsigned long long *tc_fcount;
 };
 
 // ------------------------------------------------- tensor-core blocks
@@ -408,10 +412,12 @@ struct TcBufs {
     float *mlo, *mhi;
     unsigned *mlomax;
     uint8_t *rin;   // prune: per point row, 1 when the point is in S (null for the radius)
+    uint32_t *flist;              // radius: points that can reach the maximum
+    unsigned long long *fcount;   // and their count
 };
 inline TcBufs tc_bufs(const RadiusArgs &a) {
     return TcBufs{a.tc_at, a.tc_bt, a.tc_an, a.tc_ae, a.tc_cn, a.tc_ce, a.tc_maxes, a.tc_absmax, a.tc_mlo, a.tc_mhi,
-                  a.tc_mlomax, a.tc_rin};
+                  a.tc_mlomax, a.tc_rin, a.tc_flist, a.tc_fcount};
 }
 bool tc_supported(int d);
 cudaError_t read_tc_counters(unsigned long long out[2], bool reset);

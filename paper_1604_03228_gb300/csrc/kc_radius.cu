@@ -195,12 +195,15 @@ __device__ double min64_warp(const float *__restrict__ pk, const float *__restri
 }
 
 // Each warp scans 32 points at a time; the flagged ones (ballot) are
-// recomputed one after another by the whole warp.
+// recomputed one after another by the whole warp.  list (optional, with its
+// device count): only the listed points can be flagged (every other point's
+// minimum is 0), so only they are scanned.
 __global__ void recheck_max_kernel(const float *__restrict__ pk, const float *__restrict__ rm, int64_t n, int d,
                                    const float *__restrict__ cen, const int32_t *kc_dev, int kc_max,
                                    const uint32_t *__restrict__ mind, const unsigned long long *key32,
                                    unsigned long long *max64, double *m64, const DevStatus *st,
-                                   const float *eblk, const float *ecmax) {
+                                   const float *eblk, const float *ecmax, const uint32_t *__restrict__ list,
+                                   const unsigned long long *lcount) {
     if (ld_volatile_i32(&st->code) != 0) return;
     if (key_val(*key32) == 0) return;   // every minimum is exactly 0
     const int kc = kc_dev ? *kc_dev : kc_max;
@@ -208,15 +211,17 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, const float *__
     const float opg = __fadd_ru(1.f, lp_slack(d));
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+    const int64_t cnt = list ? (int64_t)*lcount : n;
+    for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < cnt;
          base += warps * 32) {
-        const int64_t x = base + lane;
-        const bool flag = x < n && can_reach(mind, x, thr, eblk, ecmax, opg);
+        const int64_t i = base + lane;
+        const int64_t x = i < cnt ? (list ? (int64_t)list[i] : i) : 0;
+        const bool flag = i < cnt && can_reach(mind, x, thr, eblk, ecmax, opg);
         unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);
         while (todo) {
             const int src = __ffs(todo) - 1;
             todo &= todo - 1;
-            const int64_t xs = base + src;
+            const int64_t xs = __shfl_sync(0xFFFFFFFFu, x, src);
             // FP32 minima: mind holds the canonical one; mixed precision: not
             const double v = min64_warp(pk, rm, xs, d, cen, kc, lane, eblk ? 0xFFFFFFFFu : mind[xs]);
             if (lane == src) {
@@ -230,14 +235,17 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, const float *__
 __global__ void recheck_arg_kernel(int64_t n, int d, const uint32_t *__restrict__ mind,
                                    const unsigned long long *key32, const unsigned long long *max64,
                                    const double *__restrict__ m64, unsigned long long *arg64,
-                                   const DevStatus *st, const float *eblk, const float *ecmax) {
+                                   const DevStatus *st, const float *eblk, const float *ecmax,
+                                   const uint32_t *__restrict__ list, const unsigned long long *lcount) {
     if (ld_volatile_i32(&st->code) != 0) return;
     if (key_val(*key32) == 0) return;
     const double thr = flag_threshold(key32, d);
     const float opg = __fadd_ru(1.f, lp_slack(d));
     const double M = __longlong_as_double((long long)*max64);
-    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t cnt = list ? (int64_t)*lcount : n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = list ? (int64_t)list[i] : i;
         if (can_reach(mind, x, thr, eblk, ecmax, opg) && m64[x] == M)
             atomicMax(arg64, 0xFFFFFFFFFFFFFFFFull - (unsigned long long)x);
     }
@@ -323,13 +331,17 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     if (a.dtype == KC_F32) {
+        // after the tensor-core filter only its listed points have a non-zero minimum
+        const bool tcl = !a.have_mind && a.tc_at && tc_supported(a.d);
+        const uint32_t *list = tcl ? a.tc_flist : nullptr;
+        const unsigned long long *lcount = tcl ? a.tc_fcount : nullptr;
         const int64_t g = (a.n + 255) / 256;
         const int grid = (int)(g > sms * 8 ? sms * 8 : g);
         recheck_max_kernel<<<grid, 256, 0, s>>>((const float *)a.pk, a.rm, a.n, a.d, (const float *)a.cen,
                                                 a.kc_dev, a.kc_max, a.mind, a.key32, a.max64, a.m64,
-                                                a.st, a.eblk, a.ecmax);
+                                                a.st, a.eblk, a.ecmax, list, lcount);
         recheck_arg_kernel<<<grid, 256, 0, s>>>(a.n, a.d, a.mind, a.key32, a.max64, a.m64, a.arg64,
-                                                a.st, a.eblk, a.ecmax);
+                                                a.st, a.eblk, a.ecmax, list, lcount);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     finalize_kernel<<<1, 1, 0, s>>>(a.dtype, a.key32, a.max64, a.arg64, a.radius_out, a.argmax_out,

@@ -816,45 +816,97 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
     }
 }
 
-// Radius: points whose upper bound can reach the largest lower bound (less
-// the FP32-to-FP64 margin) get their exact canonical FP32 minimum (one warp
-// per point, lanes over centers); everyone else gets 0.  The key of the
-// maximum then equals the one the CUDA-core path produces.
-__global__ void tc_exact_kernel(const float *__restrict__ pk, const float *__restrict__ rm, int64_t n, int d,
-                                const float *__restrict__ cen,
-                                const int32_t *kc_dev, int kc_max, const float *__restrict__ mhi,
-                                const unsigned *mlo_max, uint32_t *__restrict__ mind, unsigned long long *key32,
-                                const DevStatus *st) {
+// Radius, exact part.  T = (largest lower bound) (1 - 3 gamma): a point whose
+// upper bound reaches T can hold the maximum (the FP32-to-FP64 margin of the
+// CUDA-core path).  Flag pass: those points go to a list (in no particular
+// order) and start from an empty minimum; every other point gets 0.
+__global__ void tc_flag_kernel(int64_t n, int d, const float *__restrict__ mhi, const unsigned *mlo_max,
+                               uint32_t *__restrict__ mind, uint32_t *__restrict__ flist,
+                               unsigned long long *fcount, const DevStatus *st) {
     if (ld_volatile_i32(&st->code) != 0) return;
-    const int kc = kc_dev ? *kc_dev : kc_max;
-    const bool v4 = (d & 3) == 0 && ((uintptr_t)cen & 15) == 0 && (pk || ((uintptr_t)rm & 15) == 0);
     const double T = (double)__uint_as_float(*mlo_max) * (1.0 - 3.0 * f32_gamma(d));
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    uint64_t best = 0;
     for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
          base += warps * 32) {
         const int64_t x = base + lane;
         const bool flag = x < n && (double)mhi[x] >= T;
-        if (x < n && !flag) mind[x] = 0u;
-        unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);
-        while (todo) {
-            const int srcl = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int64_t xs = base + srcl;
+        if (x < n) mind[x] = flag ? 0xFFFFFFFFu : 0u;
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, flag);
+        if (!b) continue;
+        unsigned long long at = 0;
+        if (lane == 0) at = atomicAdd(fcount, (unsigned long long)__popc(b));
+        at = __shfl_sync(0xFFFFFFFFu, at, 0);
+        if (flag) flist[at + __popc(b & ((1u << lane) - 1u))] = (uint32_t)x;
+    }
+}
+
+// Exact canonical FP32 minima of the listed points: work items are (a group
+// of EX_PG listed points, a chunk of EX_CC centers); a CTA stages the chunk
+// (row stride d | 1: the lanes' rows fall in distinct banks) and the group's
+// coordinates in shared memory, each warp takes points of the group with its
+// lanes over the chunk's centers, and the chunk minima meet in atomicMin
+// (float bits of non-negative values order as the values).
+constexpr int EX_NT = 256, EX_PG = 64, EX_CC = 128;
+__global__ void __launch_bounds__(EX_NT) tc_exact_list_kernel(const float *__restrict__ pk, const float *__restrict__ rm,
+                                                              int d, const float *__restrict__ cen,
+                                                              const int32_t *kc_dev, int kc_max,
+                                                              const uint32_t *__restrict__ flist,
+                                                              const unsigned long long *fcount,
+                                                              uint32_t *__restrict__ mind, const DevStatus *st) {
+    extern __shared__ float ex_smem[];
+    if (ld_volatile_i32(&st->code) != 0) return;
+    const int ld = d | 1;
+    float *scen = ex_smem;                  // [EX_CC][ld]
+    float *spts = ex_smem + EX_CC * ld;     // [EX_PG][d]
+    const int kc = kc_dev ? *kc_dev : kc_max;
+    const int64_t F = (int64_t)*fcount;
+    const int64_t chunks = (kc + EX_CC - 1) / EX_CC;
+    const int64_t items = (F + EX_PG - 1) / EX_PG * chunks;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+        const int64_t p0 = it / chunks * EX_PG;
+        const int c0 = (int)(it % chunks) * EX_CC;
+        const int ncc = kc - c0 < EX_CC ? kc - c0 : EX_CC;
+        const int npg = (int)(F - p0 < EX_PG ? F - p0 : EX_PG);
+        __syncthreads();   // the previous item's reads are done
+        for (int e = tid; e < ncc * d; e += EX_NT) {
+            const int ci = e / d, j = e - ci * d;
+            scen[ci * ld + j] = cen[(int64_t)(c0 + ci) * d + j];
+        }
+        for (int e = tid; e < npg * d; e += EX_NT) {
+            const int q = e / d, j = e - q * d;
+            spts[q * d + j] = point_at(pk, rm, flist[p0 + q], j, d);
+        }
+        __syncthreads();
+        for (int q = warp; q < npg; q += EX_NT / 32) {
+            const float *xp = spts + q * d;
             uint32_t m = 0xFFFFFFFFu;
-            for (int ci = lane; ci < kc; ci += 32)
-                m = min(m, __float_as_uint(point_row_dist(pk, rm, xs, d, cen + (int64_t)ci * d, v4)));
+            for (int ci = lane; ci < ncc; ci += 32) {
+                const float *cr = scen + ci * ld;
+                float acc = 0.f;
+                for (int j = 0; j < d; ++j) acc = sq_step(acc, xp[j], cr[j]);
+                m = min(m, __float_as_uint(acc));
+            }
 #pragma unroll
             for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-            if (lane == srcl) {
-                mind[xs] = m;
-                best = umax64(best, make_key(m, (uint32_t)xs));
-            }
+            if (lane == 0) atomicMin(&mind[flist[p0 + q]], m);
         }
     }
+}
+
+// The argmax key over the listed points (everyone else has minimum 0).
+__global__ void tc_key_list_kernel(const uint32_t *__restrict__ flist, const unsigned long long *fcount,
+                                   const uint32_t *__restrict__ mind, unsigned long long *key32, const DevStatus *st) {
+    if (ld_volatile_i32(&st->code) != 0) return;
+    const int64_t F = (int64_t)*fcount;
+    uint64_t best = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < F; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t x = flist[i];
+        best = umax64(best, make_key(mind[x], x));
+    }
     best = warp_max_u64(best);
-    if (lane == 0 && best) atomicMax(key32, (unsigned long long)best);
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(key32, (unsigned long long)best);
 }
 
 // Canonical FP32 squared distance of rows x and c (d coordinates), with
@@ -1052,8 +1104,18 @@ cudaError_t launch_tc_radius(const float *pk, const float *rm, int64_t n, int d,
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms());
     tc_dmin_kernel<0><<<grid, TC_THREADS, smem, s>>>(a);
     const int g2 = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms() * 8);
-    tc_exact_kernel<<<g2, 256, 0, s>>>(pk, rm, n, d, cen, kc_dev, kc, B.mhi, B.mlomax, mind, key32, st);
-    note_launches(2);
+    cudaMemsetAsync(B.fcount, 0, sizeof(unsigned long long), s);
+    tc_flag_kernel<<<g2, 256, 0, s>>>(n, d, B.mhi, B.mlomax, mind, B.flist, B.fcount, st);
+    const size_t exsm = ((size_t)EX_CC * (d | 1) + (size_t)EX_PG * d) * sizeof(float);
+    if ((e = cudaFuncSetAttribute(tc_exact_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)exsm)) !=
+        cudaSuccess)
+        return e;
+    // the list's length is on the device: the grid covers the largest case
+    const int64_t items_max = (n + EX_PG - 1) / EX_PG * ((kc + EX_CC - 1) / EX_CC);
+    const int g3 = (int)std::min<int64_t>(items_max, (int64_t)sms() * 8);
+    tc_exact_list_kernel<<<g3, EX_NT, exsm, s>>>(pk, rm, d, cen, kc_dev, kc, B.flist, B.fcount, mind, st);
+    tc_key_list_kernel<<<g2, 256, 0, s>>>(B.flist, B.fcount, mind, key32, st);
+    note_launches(4);
     return cudaGetLastError();
 }
 
