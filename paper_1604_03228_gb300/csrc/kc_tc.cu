@@ -827,17 +827,27 @@ __global__ void tc_flag_kernel(int64_t n, int d, const float *__restrict__ mhi, 
     const double T = (double)__uint_as_float(*mlo_max) * (1.0 - 3.0 * f32_gamma(d));
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
-         base += warps * 32) {
-        const int64_t x = base + lane;
-        const bool flag = x < n && (double)mhi[x] >= T;
-        if (x < n) mind[x] = flag ? 0xFFFFFFFFu : 0u;
-        const unsigned b = __ballot_sync(0xFFFFFFFFu, flag);
-        if (!b) continue;
-        unsigned long long at = 0;
-        if (lane == 0) at = atomicAdd(fcount, (unsigned long long)__popc(b));
-        at = __shfl_sync(0xFFFFFFFFu, at, 0);
-        if (flag) flist[at + __popc(b & ((1u << lane) - 1u))] = (uint32_t)x;
+    // a warp takes 128 consecutive points per pass, four loads in flight
+    for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 128; base < n;
+         base += warps * 128) {
+        float h[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t x = base + 32 * q + lane;
+            h[q] = x < n ? mhi[x] : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t x = base + 32 * q + lane;
+            const bool flag = x < n && (double)h[q] >= T;
+            if (x < n) mind[x] = flag ? 0xFFFFFFFFu : 0u;
+            const unsigned b = __ballot_sync(0xFFFFFFFFu, flag);
+            if (!b) continue;
+            unsigned long long at = 0;
+            if (lane == 0) at = atomicAdd(fcount, (unsigned long long)__popc(b));
+            at = __shfl_sync(0xFFFFFFFFu, at, 0);
+            if (flag) flist[at + __popc(b & ((1u << lane) - 1u))] = (uint32_t)x;
+        }
     }
 }
 
