@@ -359,7 +359,7 @@ void take_tc(Carve &cv, RadiusArgs &ra, int dtype, int64_t n, int d, int kc) {
     ra.tc_cn = cv.take<float>((size_t)tc_center_tiles(kc) * 256);
     ra.tc_ce = cv.take<float>((size_t)tc_center_tiles(kc) * 256);
     ra.tc_maxes = cv.take<unsigned>(3);
-    ra.tc_absmax = cv.take<unsigned>(1);
+    ra.tc_absmax = cv.take<unsigned>(3);   // scale words (the row-major path uses all three)
     ra.tc_mlo = cv.take<float>((size_t)n);
     ra.tc_mhi = cv.take<float>((size_t)n);
     ra.tc_mlomax = cv.take<unsigned>(1);
@@ -1297,7 +1297,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
             Ptc.tc_cn = cv.take<float>((size_t)tc_center_tiles(n) * 256);
             Ptc.tc_ce = cv.take<float>((size_t)tc_center_tiles(n) * 256);
             Ptc.tc_maxes = cv.take<unsigned>(3);
-            Ptc.tc_absmax = cv.take<unsigned>(1);
+            Ptc.tc_absmax = cv.take<unsigned>(3);
         }
         Lo.pb = PruneBufs{};
         if (tcp) {   // deferred exact checks: up to 2 pairs per point before full rescans

@@ -207,35 +207,44 @@ __global__ void tc_absmax_kernel(const float *__restrict__ pk, int64_t n, int d,
     if ((threadIdx.x & 31) == 0) atomicMax(absmax, __float_as_uint(m));
 }
 
-// The same maximum over a row-major array of total values, which it also
-// checks as the pack does: NaN/Inf (KC_ERR_NONFINITE), else |v| > 2^54
-// (KC_ERR_RANGE; squared distances then stay far below FLT_MAX).  vec: rm is
-// 16-byte aligned.
+// Row-major points: the scale comes from a sample, the largest finite
+// |coordinate| of every TC_SAMPLE-th row, doubled (one power of two of
+// headroom), into words[1].  The tile pass below checks every value against
+// it and a fix-up pass redoes the tiles in the rare case that the sample
+// missed a larger magnitude, so the scale always covers every coordinate.
+constexpr int TC_SAMPLE = 64;
+__global__ void tc_absmax_sample_kernel(const float *__restrict__ rm, int64_t n, int d, unsigned *words) {
+    float m = 0.f;
+    const int64_t total = (n + TC_SAMPLE - 1) / TC_SAMPLE * d;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / d;
+        const float v = __ldg(rm + r * TC_SAMPLE * d + (e - r * d));
+        if (isfinite(v)) m = fmaxf(m, fabsf(v));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(&words[1], __float_as_uint(2.f * m));
+}
+
+// Checks of one value as the pack performs them: NaN/Inf (KC_ERR_NONFINITE),
+// else |v| > 2^54 (KC_ERR_RANGE; squared distances then stay far below
+// FLT_MAX); m keeps the largest magnitude.
 __device__ __forceinline__ void absmax_check(float v, float &m, bool &bad, bool &nonfin) {
     m = fmaxf(m, fabsf(v));
     if (!(fabsf(v) <= 0x1p54f)) bad = true;   // NaN fails the comparison
     if (!isfinite(v)) nonfin = true;
 }
-__global__ void tc_absmax_rm_kernel(const float *__restrict__ rm, int64_t total, bool vec, unsigned *absmax,
-                                    DevStatus *st) {
-    float m = 0.f;
-    bool bad = false, nonfin = false;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t nv = vec ? total / 4 : 0;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nv; q += stride) {
-        const float4 w = __ldg(reinterpret_cast<const float4 *>(rm) + q);
-        absmax_check(w.x, m, bad, nonfin);
-        absmax_check(w.y, m, bad, nonfin);
-        absmax_check(w.z, m, bad, nonfin);
-        absmax_check(w.w, m, bad, nonfin);
-    }
-    for (int64_t e = 4 * nv + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += stride)
-        absmax_check(rm[e], m, bad, nonfin);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(absmax, __float_as_uint(m));
-    if (nonfin) set_status(st, KC_ERR_NONFINITE, 1, 0);
-    else if (bad) set_status(st, KC_ERR_RANGE, 1, 0);
+
+// Does the scale taken from A (tc_scale: 2^(S - e), A < 2^e) keep every
+// coordinate of magnitude at most T within 2^S?
+__device__ __forceinline__ bool scale_covers(unsigned a_bits, unsigned t_bits) {
+    const float A = __uint_as_float(a_bits), T = __uint_as_float(t_bits);
+    if (!(T > 0.f)) return true;
+    if (!(A > 0.f)) return false;
+    int ea, et;
+    frexpf(A, &ea);
+    frexpf(T, &et);
+    return et <= ea;
 }
 
 // Point tiles straight from the row-major array (the pack's work folded in):
@@ -244,16 +253,29 @@ __global__ void tc_absmax_rm_kernel(const float *__restrict__ rm, int64_t total,
 // conflicts), then threads 0..127 compute their row's norm and rounding bound
 // and all threads write the fp16 tile, one 16-byte core-matrix row per store.
 // Values and rounding are those of tc_rows_kernel<TC_M> on the same points.
+// words: [0] the scale word every later kernel reads, [1] the sampled one,
+// [2] the true largest magnitude.  First pass (FIX false): scale from [1];
+// every value checked as the pack does and its magnitude folded into [2].
+// Fix-up pass (FIX true): [0] = [1] when it covers [2] (nothing else to
+// do), else [0] = [2] and the tiles are redone with that scale.
 constexpr int TC_RM_NT = 256;
 constexpr int TC_RM_V = 8;   // a 128 x 64 FP32 tile is 8 loads per thread
+template <bool FIX>
 __global__ void __launch_bounds__(TC_RM_NT) tc_points_rm_kernel(const float *__restrict__ rm, int64_t n, int d,
-                                                                 bool vec, int kp, int64_t ntiles,
-                                                                 const unsigned *absmax, __half *__restrict__ tiles,
+                                                                 bool vec, int kp, int64_t ntiles, unsigned *words,
+                                                                 DevStatus *st, __half *__restrict__ tiles,
                                                                  float *__restrict__ norm, float *__restrict__ err) {
     extern __shared__ float sx[];   // [TC_M][ld]
     const int ld = d | 1;
-    const float sc = tc_scale(absmax, d);
     const int tid = threadIdx.x;
+    if (FIX) {
+        const bool covered = scale_covers(words[1], words[2]);
+        if (blockIdx.x == 0 && tid == 0) words[0] = covered ? words[1] : words[2];
+        if (covered) return;
+    }
+    const float sc = tc_scale(&words[FIX ? 2 : 1], d);
+    float m = 0.f;
+    bool bad = false, nonfin = false;
     // f / d as a multiply-high: exact for f < 2^14 (a tile's TC_M * d <= 2^14
     // elements) and d <= 2^7
     const uint64_t dmag = 0xFFFFFFFFull / (uint64_t)d + 1;
@@ -280,6 +302,10 @@ __global__ void __launch_bounds__(TC_RM_NT) tc_points_rm_kernel(const float *__r
                 const float vv[4] = {w[v].x, w[v].y, w[v].z, w[v].w};
                 const int f = 4 * q;
                 int r = row_of(f), j = f - r * d;
+                if (!FIX) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) absmax_check(vv[u], m, bad, nonfin);
+                }
                 if ((d & 3) == 0) {   // the four values share a row
                     float *dst = sx + r * ld + j;
 #pragma unroll
@@ -298,7 +324,9 @@ __global__ void __launch_bounds__(TC_RM_NT) tc_points_rm_kernel(const float *__r
         }
         for (int f = 4 * nv + tid; f < total; f += TC_RM_NT) {
             const int r = row_of(f), j = f - r * d;
-            sx[r * ld + j] = __fmul_rn(__ldg(base + f), sc);
+            const float v = __ldg(base + f);
+            if (!FIX) absmax_check(v, m, bad, nonfin);
+            sx[r * ld + j] = __fmul_rn(v, sc);
         }
         for (int f = total + tid; f < TC_M * d; f += TC_RM_NT) {
             const int r = row_of(f), j = f - r * d;
@@ -351,6 +379,13 @@ __global__ void __launch_bounds__(TC_RM_NT) tc_points_rm_kernel(const float *__r
             }
             *reinterpret_cast<uint4 *>(tile + core_off(TC_M, r, k0)) = make_uint4(h[0], h[1], h[2], h[3]);
         }
+    }
+    if (!FIX) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+        if ((tid & 31) == 0) atomicMax(&words[2], __float_as_uint(m));
+        if (nonfin) set_status(st, KC_ERR_NONFINITE, 1, 0);
+        else if (bad) set_status(st, KC_ERR_RANGE, 1, 0);
     }
 }
 
@@ -1072,19 +1107,23 @@ cudaError_t launch_tc_radius(const float *pk, const float *rm, int64_t n, int d,
             return e;
     } else {
         const bool vec = ((uintptr_t)rm & 15) == 0;
-        cudaMemsetAsync(B.absmax, 0, sizeof(unsigned), s);
-        const int64_t total = n * (int64_t)d;
-        const int ga = (int)std::min<int64_t>(std::max<int64_t>(1, (total / 4 + 255) / 256), (int64_t)sms() * 8);
-        tc_absmax_rm_kernel<<<ga, 256, 0, s>>>(rm, total, vec, B.absmax, st);
+        cudaMemsetAsync(B.absmax, 0, 3 * sizeof(unsigned), s);   // final, sampled and true scale words
+        const int64_t stotal = (n + TC_SAMPLE - 1) / TC_SAMPLE * d;
+        const int ga = (int)std::min<int64_t>((stotal + 255) / 256, (int64_t)sms() * 4);
+        tc_absmax_sample_kernel<<<ga, 256, 0, s>>>(rm, n, d, B.absmax);
         const int64_t nt = (n + TC_M - 1) / TC_M;
         const size_t sm = (size_t)TC_M * (d | 1) * sizeof(float);
-        if ((e = cudaFuncSetAttribute(tc_points_rm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)) !=
-            cudaSuccess)
+        if ((e = cudaFuncSetAttribute(tc_points_rm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(tc_points_rm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)sm)) != cudaSuccess)
             return e;
         const int gp = (int)std::min<int64_t>(nt, (int64_t)sms() * 8);
-        tc_points_rm_kernel<<<gp, TC_RM_NT, sm, s>>>(rm, n, d, vec, kpad(d), nt, B.absmax, (__half *)B.at, B.an,
-                                                      B.ae);
-        note_launches(2);
+        tc_points_rm_kernel<false><<<gp, TC_RM_NT, sm, s>>>(rm, n, d, vec, kpad(d), nt, B.absmax, st,
+                                                             (__half *)B.at, B.an, B.ae);
+        tc_points_rm_kernel<true><<<gp, TC_RM_NT, sm, s>>>(rm, n, d, vec, kpad(d), nt, B.absmax, st,
+                                                            (__half *)B.at, B.an, B.ae);
+        note_launches(3);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if ((e = launch_tc_centers(cen, kc_dev, kc, d, B.absmax, B.bt, B.cn, B.ce, B.maxes, s)) != cudaSuccess) return e;

@@ -269,6 +269,19 @@ def test_radius_tensor_core_row_major_sources(kc, monkeypatch, d):
         assert rr.radius == r64 and rr.argmax == am
 
 
+@pytest.mark.parametrize("row", [1, 4095])
+def test_radius_tensor_core_outlier_outside_scale_sample(kc, monkeypatch, row):
+    # the scale comes from every 64th row; a far larger coordinate on another
+    # row forces the fix-up pass, and the radius stays exact
+    pts = I.gauss_mixture(4096, 16, 67, 5, 0.5, -1, 1)
+    pts[row, 3] = 1.0e4
+    C = np.arange(0, 4096, 9)
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    rr = kc.kc_radius(_dev(pts), _dev(C))
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    assert rr.radius == r64 and rr.argmax == am
+
+
 @pytest.mark.parametrize("bad,status", [(np.nan, "KC_ERR_NONFINITE"), (np.inf, "KC_ERR_NONFINITE"),
                                         (1.0e30, "KC_ERR_RANGE")])
 def test_radius_tensor_core_checks_inputs(kc, monkeypatch, bad, status):
