@@ -19,6 +19,12 @@ workload (seed 1 + 1000 * rank): weak scaling, no collective on the data path.
 --impl reference times the CPU oracle (plain C, one thread) on a bounded
 sample of the same workload: the first 5 GON steps plus the radius of those 5
 centers over all n points per step.
+
+--workload NAME measures one of the other paths (one JSON line with the same
+keys): GON / MRG on 10M x 16, GON / tensor-core radius / EIM on 8M x 64, the
+int latency case, the 4,096-instance batch plan and its one-call-per-instance
+baseline.  --report k|phi prints the sweeps over k (GON, MRG, EIM) or over
+EIM's phi on 2-D sets shaped like the paper's experiments instead.
 """
 from __future__ import annotations
 

@@ -5,7 +5,10 @@
 //
 // Operands.  Points and centers are scaled by 2^e (an exact scaling, e chosen
 // so that every |coordinate| <= 2^S with d 2^(2S) <= 2^30 and S <= 14) and
-// rounded to fp16: x~, c~.  A prep pass writes them once as MMA tiles (128
+// rounded to fp16: x~, c~.  e comes from the largest |coordinate|: a pass over
+// packed points, or for row-major points a sample of every 64th row that the
+// tile pass checks against every value (a fix-up pass redoes the tiles with
+// the true maximum when the sample fell short).  A prep pass writes them once as MMA tiles (128
 // point rows or 256 center rows by Kp = d + 3 rounded up to 16) in the
 // shared-memory operand layout, with per-row |x~|^2 and error bound
 // e = ||x~ - 2^e x|| (FP32, rounded up).  The tiles carry the norm term too:
