@@ -138,6 +138,11 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
  *   radius        double out: the covering radius.
  *   argmax_point  int64 out (may be NULL): the farthest point, lowest index on
  *                 ties.
+ * For float points with kc * d >= 8192 and d <= 128 the n x kc block runs on
+ * the tensor cores (fp16 products with per-point bounds; every point that can
+ * reach the maximum is recomputed in canonical FP32, then FP64), reading the
+ * row-major points where they lie; the result is the same as the CUDA-core
+ * path's (KC_RADIUS_TC selects either).
  * Errors: KC_ERR_ARG if kc < 1 or an index is out of range; others as above.
  */
 kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *centers, int32_t kc,
