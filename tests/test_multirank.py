@@ -64,3 +64,26 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.run_reference(bench.argparse.Namespace(gpus=2, steps=1, warmup=0))
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
+    # rank 0 prints one JSON line with the keys the benchmark contract names
+    sys.path.insert(0, ROOT)
+    import json
+
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    bench.run_reference(bench.argparse.Namespace(gpus=1, steps=1, warmup=0))
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    assert j["impl"] == "reference" and j["metric"] == bench.METRIC and j["unit"] == bench.UNIT
+    assert j["value"] > 0 and j["ms_per_step"] > 0 and j["higher_is_better"] is True
+    assert (j["n_gpus"], j["steps"], j["warmup"], j["scaling"], j["data"]) == (1, 1, 0, "weak", "synthetic")
+    assert j["config"]["workload"] == bench.WORKLOAD and j["vs_baseline"] is None
+    cb = j["cpu_baseline"]
+    assert cb["value"] == j["value"] and cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    e = j["e2e"]
+    assert e["value"] == j["value"] and e["unit"] == j["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
