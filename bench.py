@@ -80,10 +80,10 @@ def parse():
     ap.add_argument("--n", type=int, default=0,
                     help="other workloads: fewer points than the configuration's (small profiling cases)")
     ap.add_argument("--k", type=int, default=0, help="8M x 64 workloads: another k (small profiling cases)")
-    ap.add_argument("--report", choices=["k", "phi"], default=None,
-                    help="instead of a bench line: runtime and solution value over k for GON, MRG and EIM "
-                         "(k), or EIM over phi (phi), on 2-D sets shaped like the paper's; JSON rows on "
-                         "stdout, tables on stderr")
+    ap.add_argument("--report", choices=["k", "n", "phi"], default=None,
+                    help="instead of a bench line: runtime and solution value over k (k) or over n at "
+                         "k = 10 and 100 (n) for GON, MRG and EIM, or EIM over phi (phi), on 2-D sets shaped "
+                         "like the paper's; JSON rows on stdout, tables on stderr")
     ap.add_argument("--seeds", type=int, default=3, help="--report: sets drawn per shape")
     ap.add_argument("--runs", type=int, default=2, help="--report: runs per set and method")
     return ap.parse_args()
@@ -519,6 +519,8 @@ def run_report(args):
     assert torch.cuda.is_available(), "--report needs a CUDA device"
     if args.report == "k":
         rows, bad = report.k_sweep(seeds=args.seeds, runs=args.runs)
+    elif args.report == "n":
+        rows, bad = report.n_sweep(seeds=args.seeds, runs=args.runs)
     else:
         rows, bad = report.phi_sweep(seeds=args.seeds, runs=args.runs)
     for r in rows:

@@ -1,7 +1,7 @@
-"""Sweeps over k (and EIM's phi) for GON, MRG and EIM through the C ABI, on
+"""Sweeps over k, n and EIM's phi for GON, MRG and EIM through the C ABI, on
 2-D synthetic sets shaped like the paper's experiments (Section 7): runtime
-curves like Figures 2 and 3, solution-value tables like Tables 2-4, and the
-phi trade-off of Tables 6 and 7.
+curves over k like Figures 2 and 3 and over n like Figure 4, solution-value
+tables like Tables 2-4, and the phi trade-off of Tables 6 and 7.
 
 The paper's sets (Section 7.2): Unif, n points uniform in a square; Gau, k'
 cluster centers uniform in the square and Gaussian clusters of similar size;
@@ -44,6 +44,9 @@ SETS = {
     "unb_n200000_k25": ("unb", 200_000, 25),      # Table 4
 }
 PHI_SET = ("gau", 200_000, 25)                    # Tables 6 and 7
+NS = (10_000, 20_000, 50_000, 100_000, 200_000, 500_000, 1_000_000)   # Figure 4
+N_KS = (10, 100)
+N_SET = ("gau", 25)
 
 
 def point_set(kind: str, n: int, clusters: int, seed: int) -> np.ndarray:
@@ -123,6 +126,23 @@ def k_sweep(sets=None, ks=KS, seeds: int = 3, runs: int = 2, m: int = M, eps: fl
     return rows, violations
 
 
+def n_sweep(ns=NS, ks=N_KS, seeds: int = 3, runs: int = 2, m: int = M, eps: float = EPS, phi: float = PHI,
+            set_shape=N_SET, methods=("mrg", "eim", "gon"), device: str = "cuda"):
+    """Mean wall time and radius per (n, method, k) for fixed k over n
+    (Figure 4); the guarantees are checked on every run."""
+    kind, clusters = set_shape
+    rows, violations = [], []
+    for n in ns:
+        r, bad = k_sweep({f"{kind}_n{n}_k{clusters}": (kind, n, clusters)}, ks=ks, seeds=seeds, runs=runs, m=m,
+                         eps=eps, phi=phi, methods=methods, device=device)
+        for row in r:
+            row["report"] = "n_sweep"
+            row["set"] = f"{kind}_k{clusters}"
+        rows += r
+        violations += bad
+    return rows, violations
+
+
 def phi_sweep(phis=PHIS, ks=KS, seeds: int = 3, runs: int = 2, eps: float = EPS, set_shape=PHI_SET,
               device: str = "cuda"):
     """EIM's mean radius and wall time per (phi, k) (Tables 6 and 7)."""
@@ -151,11 +171,24 @@ def phi_sweep(phis=PHIS, ks=KS, seeds: int = 3, runs: int = 2, eps: float = EPS,
 
 
 def markdown(rows) -> str:
-    """Tables of radius and time over k, one per set (k sweep) or over phi."""
+    """Tables of radius and time over k (one per set), over n (one per k) or
+    over phi."""
     out = []
     if not rows:
         return ""
-    if rows[0]["report"] == "k_sweep":
+    if rows[0]["report"] == "n_sweep":
+        meths = list(dict.fromkeys(r["method"] for r in rows))
+        cell = {(r["method"], r["k"], r["n"]): r for r in rows}
+        for k in sorted(set(r["k"] for r in rows)):
+            out.append(f"{rows[0]['set']}, k = {k}: ms per call | radius over n")
+            out.append("| n | " + " | ".join(f"{m} ms" for m in meths) + " | " + " | ".join(meths) + " |")
+            out.append("|---" * (1 + 2 * len(meths)) + "|")
+            for n in sorted(set(r["n"] for r in rows if r["k"] == k)):
+                ms = " | ".join(f"{cell[(m, k, n)]['ms']:.3g}" for m in meths)
+                rad = " | ".join(f"{cell[(m, k, n)]['radius']:.4g}" for m in meths)
+                out.append(f"| {n} | {ms} | {rad} |")
+            out.append("")
+    elif rows[0]["report"] == "k_sweep":
         for name in dict.fromkeys(r["set"] for r in rows):
             rs = [r for r in rows if r["set"] == name]
             meths = list(dict.fromkeys(r["method"] for r in rs))

@@ -49,6 +49,16 @@ def test_guarantee_checks_flag_each_bound():
     assert R.check_guarantees({"gon": 1.0, "mrg": float("nan")})
 
 
+def test_n_sweep_table():
+    rows = [{"report": "n_sweep", "set": "gau_k25", "n": n, "method": m, "k": k, "m": 50, "ms": n / 1000,
+             "radius": 100.0 / n, "runs": 2} for k in (10, 100) for n in (10000, 20000) for m in ("mrg", "gon")]
+    md = R.markdown(rows).splitlines()
+    assert md[0] == "gau_k25, k = 10: ms per call | radius over n"
+    assert md[1] == "| n | mrg ms | gon ms | mrg | gon |"
+    assert md[3] == "| 10000 | 10 | 10 | 0.01 | 0.01 |" and md[4] == "| 20000 | 20 | 20 | 0.005 | 0.005 |"
+    assert md[6] == "gau_k25, k = 100: ms per call | radius over n"
+
+
 def test_markdown_tables():
     rows = [{"report": "k_sweep", "set": "s", "n": 10, "method": m, "k": k, "m": 2, "ms": 1.0 + k,
              "radius": 10.0 / k, "runs": 2} for k in (2, 5) for m in ("mrg", "gon")]
