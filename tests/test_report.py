@@ -69,3 +69,41 @@ def test_markdown_tables():
             for p in (1.0, 6.0)]
     md = R.markdown(prow).splitlines()
     assert md[1] == "| k | phi 1 | phi 6 | phi 1 ms | phi 6 ms |" and md[3] == "| 2 | 1 | 0.1667 | 1 | 6 |"
+
+
+class _Res:
+    def __init__(self, radius):
+        self.radius = radius
+
+
+def _oracle_calls(monkeypatch):
+    # the sweeps' library calls answered by the oracle, on the CPU
+    from oracle import oracle as O
+    from paper_1604_03228_gb300 import inputs as I
+
+    def r64(pts, centers):
+        return O.radius(pts, centers, mode="f64")[0]
+
+    monkeypatch.setattr(R.B, "kc_gonzalez",
+                        lambda x, k: _Res(r64(x.numpy(), O.gonzalez(x.numpy(), k, mode="f32").centers)))
+    monkeypatch.setattr(R.B, "kc_mrg",
+                        lambda x, k, m: _Res(r64(x.numpy(), O.mrg(x.numpy(), k, I.even_offsets(len(x), m),
+                                                                   mode="f32").centers)))
+    monkeypatch.setattr(R.B, "kc_eim",
+                        lambda x, k, eps, phi, seed: _Res(r64(x.numpy(), O.eim(x.numpy(), k, eps, phi, seed,
+                                                                                mode="f32").centers)))
+
+
+def test_sweeps_on_the_oracle(monkeypatch):
+    # every row present and the guarantees hold on the oracle's own GON, MRG
+    # and EIM results (Lemmas 1 and 2; EIM's bound at phi = 6)
+    _oracle_calls(monkeypatch)
+    rows, bad = R.n_sweep(ns=(3000, 6000), ks=(5, 20), seeds=1, runs=2, m=10, device="cpu")
+    assert bad == [] and len(rows) == 2 * 2 * 3
+    assert {(r["n"], r["k"], r["method"]) for r in rows} == {(n, k, m) for n in (3000, 6000) for k in (5, 20)
+                                                             for m in ("mrg", "eim", "gon")}
+    assert all(r["report"] == "n_sweep" and r["runs"] == 2 and r["radius"] > 0 for r in rows)
+    rows, bad = R.k_sweep({"unb": ("unb", 4000, 5)}, ks=(2, 8), seeds=1, runs=1, m=8, device="cpu")
+    assert bad == [] and len(rows) == 6
+    rows, bad = R.phi_sweep(phis=(1.0, 6.0), ks=(4,), seeds=1, runs=1, set_shape=("gau", 4000, 5), device="cpu")
+    assert bad == [] and len(rows) == 2
