@@ -1,30 +1,36 @@
 #!/usr/bin/env python
 """Benchmark of the k-center farthest-point hot path on GB300.
 
-Workload: GON (Section 3.1) with k = 100 followed by the covering radius of
-its centers (kc_radius), on n = 1,000,000 points in d = 10, a mixture of 25
-isotropic Gaussians (sigma 1, means uniform in [-50, 50]^10), FP32, seed 1.
-One step = one kc_gonzalez + one kc_radius call through the C ABI.
+Headline workload: GON (Section 3.1) with k = 1024 on n = 8,000,000 points in
+d = 64, a mixture of 100 isotropic Gaussians (sigma 0.5, means uniform in
+[-10, 10]^64), FP32, seed 4: the largest single-GPU configuration of the
+Gonzalez + EIM precision workload.  One step = one kc_gonzalez call through
+the C ABI (pack, the persistent k-step kernel, the FP64 radius recheck).
 
-Metric: point-center distance evaluations per second (GON: k sweeps of n
-points; radius: n x k), whole job over all ranks.  `value` is device-timed
-with the points resident in HBM (CUDA events around every step, 256 MiB L2
-flush between steps outside the events); `e2e` is the same metric with the
-points in pinned host memory passed to the C ABI, host<->device copies and
-result read-back inside the wall-clock timed region.
+Metric: point-center distance evaluations per second (k sweeps of n points
+per solve), whole job over all ranks.  `value` is device-timed with the
+points resident in HBM (CUDA events around every step; the 2 GB point set is
+larger than L2, so no flush is needed); `e2e` is the same metric with the
+points in pinned host memory passed to the C ABI, host-to-device traffic and
+result read-back inside the wall-clock timed region.  The same line carries
+the mixed-precision comparison of the metric ("mixed"): the bf16 sweep
+against the FP32 sweep on this workload (identical selections checked), and
+the 4,096-instance batch (bf16 sweep, one CUDA-graph replay) against one
+FP32 kc_gonzalez call per instance and against the FP32 batch.
 
 Under torchrun (N > 1) every rank solves its own independent instance of the
-workload (seed 1 + 1000 * rank): weak scaling, no collective on the data path.
+workload (seed 4 + 1000 * rank): weak scaling, no collective on the data path.
 
---impl reference times the CPU oracle (plain C, one thread) on a bounded
-sample of the same workload: the first 5 GON steps plus the radius of those 5
-centers over all n points per step.
+--impl reference times the CPU oracle as it stands on all host cores: one
+worker process per core, each running the oracle's GON on its contiguous
+shard of the same point set (first 8 centers per shard), per step.
 
 --workload NAME measures one of the other paths (one JSON line with the same
-keys): GON / MRG on 10M x 16, GON / tensor-core radius / EIM on 8M x 64, the
-int latency case, the 4,096-instance batch plan and its one-call-per-instance
-baseline.  --report k|phi prints the sweeps over k (GON, MRG, EIM) or over
-EIM's phi on 2-D sets shaped like the paper's experiments instead.
+keys): GON + radius on 1M x 10 (L2-resident, against the measured L2 read
+peak), GON / MRG on 10M x 16, tensor-core radius / EIM on 8M x 64, the int
+latency case, the 4,096-instance batch plan and its one-call-per-instance
+baseline.  --report k|n|phi prints the sweeps over k, over n, or over EIM's
+phi on 2-D sets shaped like the paper's experiments instead.
 """
 from __future__ import annotations
 
@@ -43,42 +49,44 @@ sys.path.insert(0, ROOT)
 
 METRIC = "point-center dist evals/s & % HBM roofline; mixed-prec batched vs FP32 solve ms"
 UNIT = "dist_evals/s"
-N, D, K = 1_000_000, 10, 100
-WORKLOAD = "gon_radius_gau_n1000000_d10_k100"
+N, D, K = 8_000_000, 64, 1024
+WORKLOAD = "gon_gau_n8000000_d64_k1024"
+CFG2 = "gon_radius_gau_n1000000_d10_k100"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
+CPU_K_SINGLE = 4      # oracle sample, one thread: GON with 4 centers on all n points
+CPU_K_SHARD = 8       # oracle sample, all cores: GON with 8 centers on each core's shard
 
-# Further workloads (one JSON line each, same keys): the int GON latency case,
-# GON / MRG on 10M x 16, GON / tensor-core radius / EIM on 8M x 64, the
-# 4,096-instance batch, and the same instances as one kc_gonzalez call each
-# (the unbatched baseline of the batch).
-EXTRA = ("gon_int_n10000_d2_k10", "gon_unif_n10000000_d16_k200", "mrg_unif_n10000000_d16_m64_k200",
-         "gon_gau_n8000000_d64_k1024", "radius_gau_n8000000_d64_k1024", "eim_gau_n8000000_d64_k1024",
-         "batch_4096", "batch_4096_per_call")
+# Further workloads (one JSON line each, same keys): GON + radius on the
+# L2-resident 1M x 10 set, the int GON latency case, GON / MRG on 10M x 16,
+# the tensor-core radius and EIM on 8M x 64, the 4,096-instance batch, and the
+# same instances as one kc_gonzalez call each (the unbatched baseline).
+EXTRA = (CFG2, "gon_int_n10000_d2_k10", "gon_unif_n10000000_d16_k200", "mrg_unif_n10000000_d16_m64_k200",
+         "radius_gau_n8000000_d64_k1024", "eim_gau_n8000000_d64_k1024", "batch_4096", "batch_4096_per_call")
 
 # DRAM traffic (read + write bytes) per launch of the dominant kernel from an
 # ncu capture, keyed by the SHA-256 of the kernel's source file at capture
-# time; reported only while the source is unchanged.
-NCU_TRAFFIC = {
-    # gon_group_kernel<float,10>, n=1e6, d=10, k=100: 40,171,776 B read + 50,176 B written
-    "83d6b9d6aa15d5e0bbd6ec721055ace70324555880c49da6f01b4b47d298c92a": 40_221_952,
-}
+# time; reported only while the source is unchanged.  Values are for the
+# full workload (a smaller capture scaled by the units processed).
+NCU_TRAFFIC = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="headline: leave out the 4,096-instance part of the mixed-precision comparison")
     ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD,) + EXTRA,
                     help="the default is the headline line; the others measure the remaining paths")
     ap.add_argument("--sweep", default="f32", choices=["f32", "bf16", "fp8"],
                     help="sweep precision for the GON / MRG / batch workloads")
     ap.add_argument("--n", type=int, default=0,
-                    help="other workloads: fewer points than the configuration's (small profiling cases)")
+                    help="fewer points than the configuration's (small profiling cases)")
     ap.add_argument("--k", type=int, default=0, help="8M x 64 workloads: another k (small profiling cases)")
     ap.add_argument("--report", choices=["k", "n", "phi"], default=None,
                     help="instead of a bench line: runtime and solution value over k (k) or over n at "
@@ -101,8 +109,8 @@ def log(*a):
 
 
 def workload_seed(rank: int) -> int:
-    """Seed of rank r's replica of the workload (independent instances)."""
-    return 1 + 1000 * rank
+    """Seed of rank r's replica of the headline workload (independent instances)."""
+    return 4 + 1000 * rank
 
 
 def job_reduce(x: float, op: str, device) -> float:
@@ -133,9 +141,32 @@ def peaks(kind="hbm"):
     return (FALLBACK_HBM_GBS if kind == "hbm" else FALLBACK_BF16_TFLOPS), "fallback"
 
 
-def workload(rank: int):
+def read_peak(nbytes: int, reps: int = 20, tries: int = 10) -> float:
+    """Read bandwidth (GB/s, best of `tries`) of a device buffer of `nbytes`
+    swept `reps` times in one kc_read_sweep launch: the L2 read peak for a
+    buffer well under the L2 size."""
+    import torch
+    import paper_1604_03228_gb300 as kc
+    buf = torch.ones(nbytes // 4, dtype=torch.float32, device="cuda")
+    sink = torch.zeros(1, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    for _ in range(3):
+        kc.kc_read_sweep(buf, reps, sink)
+    best = 0.0
+    for _ in range(tries):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        kc.kc_read_sweep(buf, reps, sink)
+        b.record(s)
+        b.synchronize()
+        best = max(best, nbytes * reps / (a.elapsed_time(b) / 1e3) / 1e9)
+    del buf
+    return best
+
+
+def workload(rank: int, n: int = N):
     from paper_1604_03228_gb300 import inputs as I
-    return I.gauss_mixture(N, D, workload_seed(rank), 25, 1.0, -50.0, 50.0)
+    return I.eim_gau_8m(n=n, seed=workload_seed(rank))
 
 
 # ------------------------------------------------------------------ clocks
@@ -198,48 +229,125 @@ class ClockSampler:
 
 # ------------------------------------------------------------- CPU oracle
 
-def oracle_sample(pts, k_sample=5):
-    """Oracle on a bounded sample: first k_sample GON steps + their radius."""
+def cpu_single(pts, k: int = CPU_K_SINGLE):
+    """The oracle on one thread: GON with k centers on all points (canonical
+    FP32 selection, then its FP64 radius), as kc_gonzalez computes."""
     from oracle import oracle as O
     t0 = time.perf_counter()
-    g = O.gonzalez(pts, k_sample, mode="f64")
-    O.radius(pts, g.centers, mode="f64")
+    O.gonzalez(pts, k, mode="f32")
     dt = time.perf_counter() - t0
-    evals = pts.shape[0] * k_sample * 2
-    return evals, dt
+    return k * pts.shape[0], dt
 
 
-def cpu_baseline(pts):
-    evals, dt = oracle_sample(pts)
-    return {"value": evals / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first 5 GON steps + radius of those 5 centers, n={N}, d={D}, FP64, "
-                      f"one thread ({dt:.2f} s)"}
+def cpu_baseline(pts, rows: int):
+    """The oracle as it stands on the host's cores: one thread, and one worker
+    process per core on contiguous shards of the same points."""
+    from oracle.parallel import ShardPool
+    nproc = os.cpu_count() or 1
+    e1, t1 = cpu_single(pts)
+    pool = ShardPool(pts)
+    try:
+        wall, evals, _ = pool.gon(CPU_K_SHARD, "f32")
+    finally:
+        pool.close()
+    return {"value": evals / wall, "unit": UNIT, "cores": pool.procs, "nproc": nproc, "kind": "oracle",
+            "sample": f"GON with {CPU_K_SHARD} centers (canonical FP32 selection + FP64 radius) on each of "
+                      f"{pool.procs} contiguous shards of the n={rows} x d={pts.shape[1]} points, one worker "
+                      f"process per core ({wall:.2f} s wall)",
+            "single_thread": {"value": e1 / t1, "unit": UNIT, "cores": 1,
+                              "sample": f"GON with {CPU_K_SINGLE} centers on all {rows} points, one thread "
+                                        f"({t1:.2f} s)"}}
 
 
 def run_reference(args):
+    """The CPU oracle, unmodified, on every host core (rank 0 only)."""
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    pts = workload(0)
-    for _ in range(args.warmup):
-        oracle_sample(pts)
-    tot_e, tot_t = 0, 0.0
-    for _ in range(args.steps):
-        e, t = oracle_sample(pts)
-        tot_e += e
-        tot_t += t
+    from oracle.parallel import ShardPool
+    n = getattr(args, "n", 0) or N
+    pts = workload(0, n)
+    pool = ShardPool(pts)
+    try:
+        for _ in range(args.warmup):
+            pool.gon(CPU_K_SHARD, "f32")
+        tot_e, tot_t = 0, 0.0
+        for _ in range(args.steps):
+            t, e, _ = pool.gon(CPU_K_SHARD, "f32")
+            tot_e += e
+            tot_t += t
+    finally:
+        pool.close()
     v = tot_e / tot_t
+    sample = (f"per step: GON with {CPU_K_SHARD} centers (canonical FP32 selection + FP64 radius) on each of "
+              f"{pool.procs} contiguous shards of the n={n} x d={D} points, one worker process per core")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": N, "d": D, "k": K},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "first 5 GON steps + radius of those 5 centers per step"},
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": n, "d": D, "k": K},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": pool.procs, "nproc": os.cpu_count(),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------- GPU
+
+def timed_steps(step, steps, s, flush=None):
+    """Device ms of each of `steps` calls of step() (CUDA events on stream s)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()
+        ev[i][0].record(s)
+        step()
+        ev[i][1].record(s)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def batch_comparison(args, kc, sw="bf16"):
+    """The 4,096-instance workload: the mixed-precision batch (one CUDA-graph
+    replay of a plan, bf16 sweep) against one FP32 kc_gonzalez call per
+    instance and against the FP32 batch plan; selections compared."""
+    import numpy as np
+    import torch
+    from paper_1604_03228_gb300 import inputs as I
+    s = torch.cuda.current_stream()
+    insts = [I.batch_instance(i) for i in range(4096)]
+    xs = [torch.from_numpy(np.ascontiguousarray(z.points)).cuda() for z in insts]
+    ks = [z.k for z in insts]
+    evals = sum(z.points.shape[0] * min(z.k, z.points.shape[0]) for z in insts)
+    out = {"workload": "batch_4096", "count": 4096, "evals_per_solve": evals}
+    steps = max(3, min(args.steps, 10))
+    for name, sweep in (("lp", sw), ("f32", None)):
+        plan = kc.kc_batch_plan_create(xs, ks, sweep=sweep, flags=kc.KC_AUTOTUNE)
+        for _ in range(3):
+            kc.kc_batch_plan_run(plan)
+        res = kc.kc_batch_plan_wait(plan)
+        ms = timed_steps(lambda: kc.kc_batch_plan_run(plan), steps, s)
+        kc.kc_batch_plan_wait(plan)
+        out[f"{name}_plan_ms"] = statistics.median(ms)
+        out[f"{name}_plan_theta"] = kc.kc_batch_plan_info(plan)[0]
+        if name == "lp":
+            lp_res = [(r.centers.cpu().tolist(), r.radius) for r in res]
+        else:
+            out["selections_identical"] = all((r.centers.cpu().tolist(), r.radius) == q
+                                              for r, q in zip(res, lp_res))
+        kc.kc_batch_plan_destroy(plan)
+    # the unbatched FP32 baseline: one synchronous call per instance, in order
+    def per_call():
+        for xi, ki in zip(xs, ks):
+            kc.kc_gonzalez(xi, ki)
+    per_call()
+    ms = timed_steps(per_call, 2, s)
+    out["f32_per_call_ms"] = statistics.median(ms)
+    out["sweep"] = sw
+    out["speedup_vs_f32_per_call"] = out["f32_per_call_ms"] / out["lp_plan_ms"]
+    out["speedup_vs_f32_plan"] = out["f32_plan_ms"] / out["lp_plan_ms"]
+    return out
+
 
 def run_gpu(args):
     import numpy as np
@@ -253,106 +361,116 @@ def run_gpu(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     kc.load()
-    pts = workload(rank)
+    n, k = args.n or N, args.k or K
+    pts = workload(rank, n)
     x = torch.from_numpy(pts).cuda()
     s = torch.cuda.current_stream()
-    cen = torch.empty(K, dtype=torch.int64, device="cuda")
+    cen = torch.empty(k, dtype=torch.int64, device="cuda")
     kout = torch.empty(1, dtype=torch.int32, device="cuda")
     rad = torch.empty(1, dtype=torch.float64, device="cuda")
-    rrad = torch.empty(1, dtype=torch.float64, device="cuda")
-    ram = torch.empty(1, dtype=torch.int64, device="cuda")
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    big = n * D * 4 > 2 * L2_FLUSH_BYTES
+    flush = None if big else torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step():
-        kc.kc_gonzalez(x, K, flags=kc.KC_ASYNC, out=(cen, kout, rad))
-        kc.kc_radius(x, cen, flags=kc.KC_ASYNC, out=(rrad, ram))
+    def step(sweep=None):
+        kc.kc_gonzalez(x, k, flags=kc.KC_ASYNC, out=(cen, kout, rad), sweep=sweep)
 
     sampler = ClockSampler(local)
     sampler.start()
     for _ in range(max(args.warmup, 3)):
-        flush.zero_()
         step()
-    kc.kc_sync(s)
-    assert int(kout.item()) == K
+    assert kc.kc_sync(s) == kc.KC_OK
+    ref_centers, ref_rad = cen.cpu().tolist(), float(rad.item())
+    assert int(kout.item()) == k
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
     kc.kc_trace_read()
     kc.kc_trace_enable(True)
     launches0 = kc.kc_launch_count()
     t_wall0 = time.time()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(s)
-        step()
-        ev[i][1].record(s)
-    torch.cuda.synchronize()
+    step_ms = timed_steps(step, args.steps, s, flush)
     t_wall1 = time.time()
     launches = kc.kc_launch_count() - launches0
     kc.kc_trace_enable(False)
     trace = kc.kc_trace_read()
-    kc.kc_sync(s)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    assert kc.kc_sync(s) == kc.KC_OK
     total_ms = job_reduce(sum(step_ms), "max", "cuda")
-    sampler.stop()
     clocks = sampler.summary(t_wall0, t_wall1)
 
-    evals_step = N * K + N * K
+    evals_step = n * k
     value = job_throughput(evals_step, args.steps, world, total_ms)
 
     # dominant kernel: the persistent GON kernel (one launch per step)
     gon_ms = [ms for (name, nk, ms) in trace if name == "gonzalez"]
     gon_avg = statistics.mean(gon_ms)
-    alg_bytes = K * N * (4 * D + 4)
+    alg_bytes = k * n * (4 * D + 4)
     achieved = alg_bytes / (gon_avg / 1e3) / 1e9
     peak, peak_kind = peaks()
     src = open(os.path.join(ROOT, "paper_1604_03228_gb300", "csrc", "kc_gon.cu"), "rb").read()
-    traffic = NCU_TRAFFIC.get(hashlib.sha256(src).hexdigest())
+    traffic = NCU_TRAFFIC.get(hashlib.sha256(src).hexdigest()) if (n, k) == (N, K) else None
     shares = {}
     for name, nk, ms in trace:
         shares[name] = shares.get(name, 0.0) + ms
 
+    # mixed precision on the same workload: the bf16 sweep, same selections
+    mixed = {}
+    for sw in ("bf16",):
+        for _ in range(2):
+            step(sw)
+        assert kc.kc_sync(s) == kc.KC_OK
+        kc.kc_counters()
+        ms = timed_steps(lambda: step(sw), args.steps, s, flush)
+        cnt = kc.kc_counters()
+        assert kc.kc_sync(s) == kc.KC_OK
+        same = cen.cpu().tolist() == ref_centers and float(rad.item()) == ref_rad
+        mixed[f"gon_{sw}_ms"] = statistics.median(ms)
+        mixed[f"gon_{sw}_identical_selection"] = same
+        mixed[f"gon_{sw}_rechecks_per_solve"] = cnt[0] / args.steps
+        mixed[f"gon_{sw}_speedup"] = statistics.median(step_ms) / statistics.median(ms)
+    mixed["gon_f32_ms"] = statistics.median(step_ms)
+    if not args.no_batch:
+        mixed["batch"] = batch_comparison(args, kc)
+    sampler.stop()
+
     # end to end: points in pinned host memory through the C ABI each step
     e2e = None
-    if rank == 0 or world > 1:
-        hp = torch.from_numpy(pts).pin_memory()
-        for _ in range(2):
-            g = kc.kc_gonzalez(hp, K)
-            kc.kc_radius(hp, g.centers)
-        reps = max(3, min(args.steps, 20))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            g = kc.kc_gonzalez(hp, K)
-            r = kc.kc_radius(hp, g.centers)
-            _ = (g.radius, r.radius)
-        t1 = time.perf_counter()
-        # whole job: every rank's rate no better than the slowest rank's
-        e2e_val = job_reduce(evals_step * reps / (t1 - t0), "min", "cuda") * world
-        h2d = 2 * N * D * 4 + K * 8
-        d2h = K * 8 + 4 + 8 + 8 + 8
-        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    hp = torch.from_numpy(pts).pin_memory()
+    for _ in range(2):
+        kc.kc_gonzalez(hp, k)
+    reps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g = kc.kc_gonzalez(hp, k)     # host buffers: the call reads the points and returns host results
+        _ = (g.centers[0], g.radius)
+    t1 = time.perf_counter()
+    # whole job: every rank's rate no better than the slowest rank's
+    e2e_val = job_reduce(evals_step * reps / (t1 - t0), "min", "cuda") * world
+    e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": n * D * 4,
+           "d2h_bytes_per_step": k * 8 + 4 + 8}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(pts)
+        cpu = cpu_baseline(pts, n)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": N, "d": D, "k": K, "points": "25-Gaussian mixture",
-                           "l2": f"{L2_FLUSH_BYTES >> 20} MiB flush between steps",
-                           "step": "kc_gonzalez + kc_radius", "replicas": world},
+                "config": {"workload": WORKLOAD if (n, k) == (N, K) else f"gon_gau_n{n}_d{D}_k{k}",
+                           "n": n, "d": D, "k": k,
+                           "points": "100-Gaussian mixture, sigma 0.5, means U[-10,10]^64",
+                           "l2": ("inputs larger than L2 (no flush)" if big
+                                  else f"{L2_FLUSH_BYTES >> 20} MiB flush between steps"),
+                           "step": "one kc_gonzalez call: pack + persistent k-step GON + FP64 radius recheck",
+                           "sweep": "f32", "replicas": world},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": traffic, "kernel": "gon_kernel",
-                             "peak_kind": peak_kind, "avg_ms": gon_avg,
-                             "alg_bytes_per_launch": alg_bytes},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                             "frac": achieved / peak, "traffic": traffic, "kernel": "gon_group_kernel",
+                             "peak_kind": peak_kind, "avg_ms": gon_avg, "alg_bytes_per_launch": alg_bytes,
+                             "alg_bytes_rule": "k n (4 d + 4): each step reads every point and its running minimum"},
+                "mixed": mixed, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "step_share_ms": {k_: v / args.steps for k_, v in shares.items()}}
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -381,8 +499,32 @@ def run_extra(args):
     cfg = {"workload": name, "sweep": args.sweep, "l2": "inputs larger than L2"}
     if args.n:
         cfg["n_override"] = args.n
-    dom, bound, plan = "gonzalez", "hbm", None
-    if name == "gon_int_n10000_d2_k10":
+    dom, bound, plan, flush, peak_l2 = "gonzalez", "hbm", None, None, None
+    if name == CFG2:
+        # GON k=100 + kc_radius on 1M x 10: the 40 MB point set stays in L2
+        # between the k sweeps, so the bound is the measured L2 read peak
+        n, d, k = args.n or 1_000_000, 10, 100
+        pts = I.gauss_mixture(n, d, 1, 25, 1.0, -50.0, 50.0)
+        x = dev(pts)
+        cen = torch.empty(k, dtype=torch.int64, device="cuda")
+        kout = torch.empty(1, dtype=torch.int32, device="cuda")
+        rad = torch.empty(1, dtype=torch.float64, device="cuda")
+        rrad = torch.empty(1, dtype=torch.float64, device="cuda")
+        ram = torch.empty(1, dtype=torch.int64, device="cuda")
+
+        def step():
+            kc.kc_gonzalez(x, k, flags=kc.KC_ASYNC, out=(cen, kout, rad), sweep=sw)
+            kc.kc_radius(x, cen, flags=kc.KC_ASYNC, out=(rrad, ram))
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        evals = 2 * k * n                              # GON's k sweeps + the n x k radius block
+        units = k * n * (d * bpc + mind_b)
+        bound = "l2"
+        peak_l2 = max(read_peak(n * d * 4), read_peak(64 << 20))
+        cfg.update(n=n, d=d, k=k, points="25-Gaussian mixture, sigma 1, means U[-50,50]^10",
+                   step="kc_gonzalez + kc_radius", l2=f"{L2_FLUSH_BYTES >> 20} MiB flush between steps; "
+                   "the 40 MB point set stays in L2 across the k sweeps of a step",
+                   l2_read_peak_gbs=peak_l2, hbm_read_gbs=read_peak(4 << 30, reps=2, tries=5))
+    elif name == "gon_int_n10000_d2_k10":
         w = I.gon_int_10k()
         x, k, n, d = dev(w.points), w.k, 10_000, 2
         step = lambda: kc.kc_gonzalez(x, k)
@@ -460,11 +602,15 @@ def run_extra(args):
     launches0 = kc.kc_launch_count()
     t0 = time.time()
     for i in range(args.steps):
+        if flush is not None:
+            flush.zero_()
         ev[i][0].record(s)
         step()
         ev[i][1].record(s)
     torch.cuda.synchronize()
     t1 = time.time()
+    if name == CFG2:
+        assert kc.kc_sync(s) == kc.KC_OK
     launches = kc.kc_launch_count() - launches0
     sampler.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in ev)
@@ -490,8 +636,8 @@ def run_extra(args):
         cfg.update(prune_pairs_per_solve=pairs)
     roof = None
     if units is not None and dom_ms:
-        peak, pk = peaks(bound)
-        if bound == "hbm":
+        peak, pk = (peak_l2, "measured here (kc_read_sweep, best of 10)") if bound == "l2" else peaks(bound)
+        if bound in ("hbm", "l2"):
             achieved, unit = units / (dom_ms / 1e3) / 1e9, "GB/s"
         else:
             achieved, unit = units / (dom_ms / 1e3) / 1e12, "TFLOP/s"

@@ -99,6 +99,13 @@ typedef enum { KC_SWEEP_F32 = 0, KC_SWEEP_BF16 = 1, KC_SWEEP_FP8 = 2 } kc_sweep;
 /* Flags for kc_opts.flags. */
 #define KC_ASYNC 1u        /* enqueue only; see kc_sync() */
 #define KC_AUTOTUNE 2u     /* batched form only: time launch shapes, keep the fastest */
+/* Testing only (kc_gonzalez): in the first step the last CTA of the launch
+ * does not publish its exchange slot, so every CTA's wait for the step's
+ * slots runs out of its budget (kc_opts.timeout_ms) and the call returns
+ * KC_ERR_TIMEOUT.  Exercises the abort path of the persistent kernel
+ * without faulting or hanging the GPU; has no effect when the launch has a
+ * single CTA (no exchange). */
+#define KC_TEST_WITHHOLD 0x80000000u
 
 typedef struct {
     int32_t dtype;          /* kc_dtype of the points */
@@ -287,7 +294,9 @@ kc_status kc_batch_plan_destroy(kc_batch_plan *plan);
  * exits, and calls no allocating routine.
  *   Arguments and results are those of kc_gonzalez, except: every pointer
  *   must be device memory of the current device; opts->flags must be 0 (the
- *   call always waits and returns the final status); inputs needing more
+ *   call always waits and returns the final status); opts->sweep must be
+ *   KC_SWEEP_F32 and opts->reserved 0 (else KC_ERR_ARG: the low-precision
+ *   copies would not fit the array); inputs needing more
  *   than KC_NOALLOC_MAX_BYTES of scratch (about n * (4 d + 12) bytes for
  *   float points, n * (4 d + 4) for int32) are rejected with KC_ERR_ARG and
  *   a message naming the size, before any work is enqueued.
@@ -354,6 +363,20 @@ int64_t kc_launch_count(void);
  * (11), or -1 on a CUDA error.
  */
 int32_t kc_counters(int64_t *out, int32_t cap);
+
+/*
+ * kc_read_sweep -- measurement helper, no counterpart in the paper: enqueue
+ * on `stream` one kernel that reads the device buffer `buf` (`bytes` long,
+ * both multiples of 16 and 16-byte aligned) `reps` times with 16-byte loads
+ * over the whole GPU and folds the words into *sink (device memory).  Timed
+ * with events around it, bytes * reps / time is the read bandwidth of the
+ * level that holds the buffer: L2 for a buffer well under the L2 size, HBM
+ * for one well over it.  This is the roofline denominator of a Gonzalez
+ * sweep whose points stay in L2 between its k passes (Section 5.1).
+ * Errors: KC_ERR_ARG for bad sizes or alignment, KC_ERR_CUDA on a launch
+ * failure.
+ */
+kc_status kc_read_sweep(const void *buf, size_t bytes, int32_t reps, unsigned long long *sink, void *stream);
 
 #ifdef __cplusplus
 }

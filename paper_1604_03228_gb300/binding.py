@@ -21,6 +21,7 @@ KC_OK, KC_ERR_ARG, KC_ERR_CUDA, KC_ERR_OOM, KC_ERR_TIMEOUT, KC_ERR_RANGE, KC_ERR
 KC_F32, KC_I32 = 0, 1
 KC_ASYNC = 1
 KC_AUTOTUNE = 2
+KC_TEST_WITHHOLD = 0x80000000
 STATUS_NAMES = {0: "KC_OK", 1: "KC_ERR_ARG", 2: "KC_ERR_CUDA", 3: "KC_ERR_OOM", 4: "KC_ERR_TIMEOUT",
                 5: "KC_ERR_RANGE", 6: "KC_ERR_NONFINITE"}
 
@@ -91,8 +92,20 @@ def load(path: str | None = None):
     L.kc_launch_count.restype = i64
     L.kc_counters.restype = i32
     L.kc_counters.argtypes = [vp, i32]
+    L.kc_read_sweep.restype = ct.c_int
+    L.kc_read_sweep.argtypes = [vp, ct.c_size_t, i32, vp, vp]
     _LIB = L
     return L
+
+
+def kc_read_sweep(buf, reps: int, sink, *, stream=None) -> None:
+    """Enqueue one kernel that reads the CUDA tensor `buf` `reps` times
+    (16-byte loads, whole GPU) into the 8-byte CUDA tensor `sink`; time it
+    with events for a read bandwidth (the L2 roofline denominator)."""
+    L = load()
+    nbytes = buf.numel() * buf.element_size()
+    st = L.kc_read_sweep(_ptr(buf), nbytes, reps, _ptr(sink), _stream_handle(buf, stream))
+    _check(L, st)
 
 
 def kc_counters():

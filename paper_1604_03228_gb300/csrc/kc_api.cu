@@ -540,7 +540,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     if (k < 1) return fail(KC_ERR_ARG, "k=%d must be >= 1", k);
     if (first < 0 || first >= n) return fail(KC_ERR_ARG, "first=%lld outside [0, n)", (long long)first);
     CallCtx c;
-    kc_status r = begin(opts, c);
+    kc_status r = begin(opts, c, KC_ASYNC | KC_TEST_WITHHOLD);
     if (r != KC_OK) return r;
 
     const bool dev_pts = is_device_ptr(pts, c.dev);
@@ -625,6 +625,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     g.st = c.arena->status;
     ra.st = c.arena->status;
     g.timeout_cycles = timeout_cycles(c.o);
+    g.withhold = (c.o.flags & KC_TEST_WITHHOLD) ? 1 : 0;
 
     KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
     const void *src;

@@ -212,7 +212,7 @@ struct Shared {
 // All k steps of one instance by this CTA (rank r of a group of G).
 template <typename T, int DC, int NT>
 __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, DevStatus *st,
-                          long long timeout) {
+                          long long timeout, int withhold = 0) {
     constexpr int W = NT / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = DC > 0 ? DC : I.d;
@@ -238,7 +238,8 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
             bool ab = false;
             if (G > 1) {
                 const int64_t row = (int64_t)it * slot_stride(G);
-                if (lane == 0) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
+                const bool held = withhold == it + 1 && r == G - 1;
+                if (lane == 0 && !held) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
                 g = poll_slots(I.slots + row, G, timeout, st, it, &ab);
             }
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {
@@ -450,7 +451,8 @@ __device__ __forceinline__ void lp_load_center(const GonInst &I, int64_t c, int 
 }
 
 template <int KIND, int DC, int NT>
-__device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &sh, DevStatus *st, long long timeout) {
+__device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &sh, DevStatus *st, long long timeout,
+                             int withhold = 0) {
     constexpr int W = NT / 32;
     constexpr int LG = lp_group(KIND);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -690,7 +692,8 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             bool ab = false;
             if (G > 1) {
                 const int64_t row = (int64_t)it * slot_stride(G);
-                if (lane == 0) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
+                const bool held = withhold == it + 1 && r == G - 1;
+                if (lane == 0 && !held) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
                 g = poll_slots(I.slots + row, G, timeout, st, it, &ab);
             }
             if (lane == 0) sh.Lcta = 0u;   // next step's admission bound starts over
@@ -761,7 +764,7 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_kernel(GonArgs a) {
     if (r < 0 || r >= I.G) return;
     if (ld_volatile_i32(&a.st->code) != 0) return;
     if (!instance_ok<T>(I, a.st)) return;
-    gon_solve<T, DC, GROUP_NT>(I, r, I.G, cs, sh, a.st, a.timeout_cycles);
+    gon_solve<T, DC, GROUP_NT>(I, r, I.G, cs, sh, a.st, a.timeout_cycles, a.withhold);
 }
 
 // Queue mode, optionally with heavy instances in front: insts[0, nheavy)
@@ -811,7 +814,7 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_lp_kernel(GonArgs a) {
     const int r = (int)blockIdx.x - I.cta0;
     if (r < 0 || r >= I.G) return;
     if (ld_volatile_i32(&a.st->code) != 0) return;
-    gon_solve_lp<KIND, DC, GROUP_NT>(I, r, I.G, smem_f, sh, a.st, a.timeout_cycles);
+    gon_solve_lp<KIND, DC, GROUP_NT>(I, r, I.G, smem_f, sh, a.st, a.timeout_cycles, a.withhold);
 }
 
 template <int KIND, int DC>

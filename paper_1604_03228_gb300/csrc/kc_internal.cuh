@@ -29,6 +29,16 @@ __device__ __forceinline__ float point_at(const float *__restrict__ pk, const fl
 }
 
 
+// A count that an earlier kernel writes on the device (e.g. k_out), clamped
+// to [0, cap]: after a kernel that gave up (a timeout) the word may still
+// hold whatever the caller's buffer held, and no later kernel may index past
+// the `cap` entries its buffers were sized for.
+__device__ __forceinline__ int64_t dev_count(const int32_t *cnt_dev, int64_t cap) {
+    if (!cnt_dev) return cap;
+    const int64_t v = *cnt_dev;
+    return v < 0 ? 0 : (v > cap ? cap : v);
+}
+
 // Device status word (first error wins).
 struct DevStatus {
     int32_t code;
@@ -222,6 +232,10 @@ struct GonArgs {
     int nheavy;              // queue mode: insts[0, nheavy) are solved by CTA groups first
     int gheavy;              // queue mode: CTAs of those groups (the first gheavy of the grid)
     int lp_kind;             // 0: FP32 sweep; KC_SWEEP_BF16 / KC_SWEEP_FP8 (float points)
+    // testing hook (KC_TEST_WITHHOLD): 1 + the step at which the last CTA of
+    // a group does not publish its exchange slot, so that the group's waits
+    // run out of their budget; 0 = never
+    int withhold;
 };
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s);
 // Mixed-precision diagnostics (synchronous): exact rechecks, overflows.

@@ -127,6 +127,9 @@ extern "C" kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, 
     if (opts) o = *opts;
     if (o.dtype != KC_F32 && o.dtype != KC_I32) return na_fail(KC_ERR_ARG, "dtype must be KC_F32 or KC_I32");
     if (o.flags != 0) return na_fail(KC_ERR_ARG, "kc_gonzalez_noalloc takes no flags (it always waits)");
+    if (o.sweep != KC_SWEEP_F32)
+        return na_fail(KC_ERR_ARG, "kc_gonzalez_noalloc sweeps in FP32 only (sweep must be KC_SWEEP_F32)");
+    if (o.reserved != 0) return na_fail(KC_ERR_ARG, "kc_opts.reserved must be 0");
     cudaStream_t s = (cudaStream_t)o.stream;
     int dev = 0;
     NA_CUDA(cudaGetDevice(&dev), "cudaGetDevice");

@@ -31,7 +31,8 @@ template <typename T>
 __global__ void gather_kernel(const T *__restrict__ pk, const T *__restrict__ rm, int64_t n, int d,
                               const int64_t *__restrict__ centers, const int32_t *kc_dev, int kc_max,
                               T *__restrict__ cen, DevStatus *st) {
-    const int kc = kc_dev ? *kc_dev : kc_max;
+    if (ld_volatile_i32(&st->code) != 0) return;
+    const int kc = (int)dev_count(kc_dev, kc_max);
     const int64_t total = (int64_t)kc * d;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(RAD_NT) radius_min_kernel(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *cs = reinterpret_cast<T *>(smem_raw);
     if (ld_volatile_i32(&st->code) != 0) return;
-    const int kc = kc_dev ? *kc_dev : kc_max;
+    const int kc = (int)dev_count(kc_dev, kc_max);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t nb = nblocks(n);
     const int tile = RAD_TILE_BYTES / (DR * (int)sizeof(T));
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(RAD_NT) radius_min_generic_kernel(
     int kc_max, uint32_t *__restrict__ mind, unsigned long long *key32, const DevStatus *st) {
     using A = typename AccOf<T>::type;
     if (ld_volatile_i32(&st->code) != 0) return;
-    const int kc = kc_dev ? *kc_dev : kc_max;
+    const int kc = (int)dev_count(kc_dev, kc_max);
     uint64_t best = 0;
     for (int64_t x = blockIdx.x * (int64_t)RAD_NT + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * RAD_NT) {
@@ -206,7 +207,7 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, const float *__
                                    const unsigned long long *lcount) {
     if (ld_volatile_i32(&st->code) != 0) return;
     if (key_val(*key32) == 0) return;   // every minimum is exactly 0
-    const int kc = kc_dev ? *kc_dev : kc_max;
+    const int kc = (int)dev_count(kc_dev, kc_max);
     const double thr = flag_threshold(key32, d);
     const float opg = __fadd_ru(1.f, lp_slack(d));
     const int lane = threadIdx.x & 31;

@@ -407,7 +407,7 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
                                float *__restrict__ norm, float *__restrict__ err, unsigned *maxes,
                                const uint8_t *__restrict__ inS, uint8_t *__restrict__ rin) {
     constexpr bool CENTER = R == TC_N;
-    const int64_t cnt = cnt_dev ? (int64_t)*cnt_dev : cnt_max;
+    const int64_t cnt = dev_count(cnt_dev, cnt_max);
     const float sc = tc_scale(absmax, d);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ntiles * R;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -907,7 +907,7 @@ __global__ void __launch_bounds__(EX_NT) tc_exact_list_kernel(const float *__res
     const int ld = d | 1;
     float *scen = ex_smem;                  // [EX_CC][ld]
     float *spts = ex_smem + EX_CC * ld;     // [EX_PG][d]
-    const int kc = kc_dev ? *kc_dev : kc_max;
+    const int kc = (int)dev_count(kc_dev, kc_max);
     const int64_t F = (int64_t)*fcount;
     const int64_t chunks = (kc + EX_CC - 1) / EX_CC;
     const int64_t items = (F + EX_PG - 1) / EX_PG * chunks;

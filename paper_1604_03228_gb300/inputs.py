@@ -175,9 +175,9 @@ def mrg_unif_10m(n: int = 10_000_000, m: int = 64, k: int = 200):
     return pts, off, k
 
 
-def eim_gau_8m(n: int = 8_000_000, d: int = 64):
+def eim_gau_8m(n: int = 8_000_000, d: int = 64, seed: int = 4):
     """n=8M, d=64, 100 clusters (sigma 0.5, means U[-10,10]^64), seed 4."""
-    return gauss_mixture(n, d, 4, 100, 0.5, -10.0, 10.0)
+    return gauss_mixture(n, d, seed, 100, 0.5, -10.0, 10.0)
 
 
 @dataclass

@@ -2,12 +2,8 @@
 bench.py times (points resident on the device, default options): sampled
 oracle checks (tests/sampled_checks.py) and identities between paths that
 must agree exactly (mixed-precision and FP32 sweeps; tensor-core and
-CUDA-core radius and prune).  The three longest (the CUDA-core radius and
-prune references, the 4,096-instance plan: minutes of GPU and host time) run
-when KC_FULL_SIZE=1.
+CUDA-core radius and prune), and the 4,096-instance plan against the oracle.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -16,7 +12,6 @@ from paper_1604_03228_gb300 import inputs as I
 from sampled_checks import farthest_steps, radius_checks, sample_rows
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
-long_run = pytest.mark.skipif(os.environ.get("KC_FULL_SIZE") != "1", reason="minutes long: run with KC_FULL_SIZE=1")
 
 
 def _dev(x):
@@ -83,7 +78,6 @@ def test_gon_8m_d64_k1024(kc, gau8m):
     assert radius_checks(pts, ca, rr.radius, rr.argmax, s) == []
 
 
-@long_run
 def test_radius_8m_tensor_cores_equal_cuda_cores(kc, gau8m, monkeypatch):
     pts = gau8m
     n = len(pts)
@@ -96,7 +90,6 @@ def test_radius_8m_tensor_cores_equal_cuda_cores(kc, gau8m, monkeypatch):
     assert radius_checks(pts, C, a.radius, a.argmax, sample_rows(n, 4000, 14)) == []
 
 
-@long_run
 def test_eim_8m_tensor_core_prune_equals_cuda_cores(kc, gau8m, monkeypatch):
     pts = gau8m
     x = _dev(pts)
@@ -111,7 +104,6 @@ def test_eim_8m_tensor_core_prune_equals_cuda_cores(kc, gau8m, monkeypatch):
     assert radius_checks(pts, ca, rr.radius, rr.argmax, sample_rows(len(pts), 4000, 15)) == []
 
 
-@long_run
 def test_batch_4096_plan(kc):
     insts = [I.batch_instance(i) for i in range(4096)]
     xs = [_dev(z.points) for z in insts]

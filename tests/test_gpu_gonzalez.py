@@ -21,6 +21,7 @@ from paper_1604_03228_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 REL = 1e-6
+_TALLY = {"calls": 0, "diverged": 0}   # float GON checks, and those whose FP64 selection parted from FP32's
 
 
 def _dev(x):
@@ -40,9 +41,23 @@ def check_float_gon(kc, pts, k, first=0, res=None):
     sel2, max2 = O.eval_sequence(pts, got, mode="f64")
     for j in range(1, len(got)):
         assert math.sqrt(sel2[j]) >= (1 - REL) * math.sqrt(max2[j])
+    # Against FP64 GON: where the FP64 selection makes the same choices, the
+    # radius is within 1e-6 of its radius.  Where it does not, the first step
+    # at which the sequences part must be a near-tie in FP64 (the FP32 choice
+    # within 1e-6 of that step's FP64 maximum, which the FP64 choice attains);
+    # later steps differ legitimately, so the radius is then held to the FP64
+    # covering radius of the returned centers (exact, above).
     g64 = O.gonzalez(pts, k, first=first, mode="f64")
+    _TALLY["calls"] += 1
     if np.array_equal(g64.centers, got):
         assert abs(res.radius - g64.radius) <= REL * g64.radius
+    else:
+        _TALLY["diverged"] += 1
+        m = min(len(got), len(g64.centers))
+        j = next((i for i in range(m) if got[i] != g64.centers[i]), m)
+        assert j >= 1 and j < m, (j, m)
+        assert sel2[j] < max2[j] or got[j] > g64.centers[j]   # FP64 takes the larger, lowest index
+        assert math.sqrt(sel2[j]) >= (1 - REL) * math.sqrt(max2[j])
     return res
 
 
@@ -315,3 +330,12 @@ def test_pinned_host_points_read_in_place(kc):
     hv = torch.from_numpy(np.concatenate([pts[:1], pts])).pin_memory()[1:]
     g2 = kc.kc_gonzalez(hv, 40)
     assert g2.centers.tolist() == ref.centers.tolist()
+
+
+def test_zz_fp64_divergence_is_rare():
+    """Runs after the float tests of this module: the FP64 and FP32 selections
+    part (at a near-tie) in few of the cases checked."""
+    if _TALLY["calls"] < 20:
+        pytest.skip("too few float GON checks ran in this session")
+    print(f"FP64 selection parted from FP32 in {_TALLY['diverged']} of {_TALLY['calls']} checks")
+    assert _TALLY["diverged"] <= 0.1 * _TALLY["calls"]

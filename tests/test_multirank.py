@@ -62,7 +62,7 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     import bench
     monkeypatch.setenv("RANK", "1")
     monkeypatch.setenv("WORLD_SIZE", "2")
-    bench.run_reference(bench.argparse.Namespace(gpus=2, steps=1, warmup=0))
+    bench.run_reference(bench.argparse.Namespace(gpus=2, steps=1, warmup=0, n=20000))
     assert capsys.readouterr().out == ""
 
 
@@ -74,7 +74,7 @@ def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
     import bench
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
-    bench.run_reference(bench.argparse.Namespace(gpus=1, steps=1, warmup=0))
+    bench.run_reference(bench.argparse.Namespace(gpus=1, steps=1, warmup=0, n=20000))
     lines = capsys.readouterr().out.strip().splitlines()
     assert len(lines) == 1
     j = json.loads(lines[0])
@@ -83,7 +83,8 @@ def test_reference_arm_line_keeps_the_contract(monkeypatch, capsys):
     assert (j["n_gpus"], j["steps"], j["warmup"], j["scaling"], j["data"]) == (1, 1, 0, "weak", "synthetic")
     assert j["config"]["workload"] == bench.WORKLOAD and j["vs_baseline"] is None
     cb = j["cpu_baseline"]
-    assert cb["value"] == j["value"] and cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"]
+    assert cb["value"] == j["value"] and cb["kind"] == "oracle" and cb["sample"]
+    assert cb["cores"] == cb["nproc"] == os.cpu_count()   # one oracle worker per host core
     e = j["e2e"]
     assert e["value"] == j["value"] and e["unit"] == j["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0

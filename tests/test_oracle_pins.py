@@ -381,6 +381,48 @@ def test_eim_loop_brute_force_first_iteration(mode):
     assert len(e.sample) == e.s_size + e.r_size
 
 
+def _brute_gon_from_zero(q, k):
+    """GON written out with numpy on rows q (first center q[0]; np.argmax
+    takes the first, i.e. lowest, index among equal maxima)."""
+    C = [0]
+    mind = ((q - q[0]) ** 2).sum(1)
+    while len(C) < k:
+        j = int(np.argmax(mind))
+        if mind[j] == 0:
+            break
+        C.append(j)
+        mind = np.minimum(mind, ((q - q[j]) ** 2).sum(1))
+    return C
+
+
+@pytest.mark.parametrize("mode", ["i64", "f64"])
+def test_eim_final_gon_on_brute_force_sample(mode):
+    """The last step of Algorithm 2 with Section 4.2: the centers are GON run
+    on C = S u R in ascending index order from C's lowest index, where S and R
+    are rebuilt by brute force for a set on which the sampling loop runs once."""
+    raw = I.int_points(6000, 2, 18, 0, 3000)
+    pts = raw if mode == "i64" else raw.astype(np.float32) * np.float32(0.37)
+    n, k, eps, phi, seed = len(pts), 6, 0.1, 6.0, 41
+    e = O.eim(pts, k, eps, phi, seed, mode=mode)
+    assert e.iterations == 1
+    pS, pH = e.trace[0][0], e.trace[0][1]
+    S = [x for x in range(n) if O.uniform(seed, 0, x, 0) < pS]
+    H = [x for x in range(n) if O.uniform(seed, 0, x, 1) < pH]
+    q = pts.astype(np.int64 if mode == "i64" else np.float64)
+    d2S = ((q[:, None, :] - q[None, S, :]) ** 2).sum(-1).min(1)
+    order = sorted(H, key=lambda x: (-d2S[x], x))
+    p = min(len(H), max(1, math.ceil(phi * math.log(n))))
+    thr = d2S[order[p - 1]]
+    R = [x for x in range(n) if d2S[x] > thr]
+    C = sorted(set(S) | set(R))
+    assert e.sample.tolist() == C
+    local = _brute_gon_from_zero(q[C], k)
+    want = [C[i] for i in local]
+    assert e.centers.tolist() == want
+    r2 = ((q[:, None, :] - q[None, want, :]) ** 2).sum(-1).min(1).max()
+    assert e.radius == pytest.approx(math.sqrt(r2), rel=0, abs=0)
+
+
 def test_eim_sampling_rates_statistical():
     n = 20000
     pts = I.int_points(n, 2, 19, 0, 10000)

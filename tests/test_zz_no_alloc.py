@@ -19,7 +19,7 @@ from paper_1604_03228_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-def _call_noalloc(kc, x, k, first=0):
+def _call_noalloc(kc, x, k, first=0, sweep=0):
     import torch
     L = kc.load()
     n, d = x.shape
@@ -28,6 +28,7 @@ def _call_noalloc(kc, x, k, first=0):
     radius = torch.zeros(1, dtype=torch.float64, device=x.device)
     o = kc.binding.kc_opts()
     o.dtype = kc.KC_F32 if x.dtype == torch.float32 else kc.KC_I32
+    o.sweep = sweep
     o.stream = int(torch.cuda.current_stream().cuda_stream)
     st = L.kc_gonzalez_noalloc(x.data_ptr(), n, d, k, first, centers.data_ptr(), k_out.data_ptr(),
                                radius.data_ptr(), ct.byref(o))
@@ -68,3 +69,27 @@ def test_noalloc_rejects_oversize_and_host_pointers(kc):
     assert b"static array" in kc.load().kc_last_error()
     with pytest.raises(TypeError):
         kc.kc_gonzalez_noalloc(np.zeros((10, 2), dtype=np.float32), 2)
+    # the low-precision sweeps need copies that the fixed array does not hold
+    small = torch.from_numpy(I.gauss_mixture(1000, 4, 35, 3, 1.0, 0, 1)).cuda()
+    for sw in (kc.KC_SWEEP_BF16, kc.KC_SWEEP_FP8, 7):
+        st, *_ = _call_noalloc(kc, small, 4, sweep=sw)
+        assert st == kc.KC_ERR_ARG and b"KC_SWEEP_F32" in kc.load().kc_last_error()
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(kc):
+    import torch
+    x = torch.from_numpy(I.gauss_mixture(100_000, 8, 36, 10, 1.0, -5, 5)).cuda()
+    st, *_ = _call_noalloc(kc, x, 16)   # the first call may load the module that holds the array
+    assert st == kc.KC_OK
+    torch.cuda.synchronize()
+    centers = torch.empty(16, dtype=torch.int64, device="cuda")
+    k_out = torch.empty(1, dtype=torch.int32, device="cuda")
+    radius = torch.empty(1, dtype=torch.float64, device="cuda")
+    o = kc.binding.kc_opts()
+    o.stream = int(torch.cuda.current_stream().cuda_stream)
+    L = kc.load()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        assert L.kc_gonzalez_noalloc(x.data_ptr(), 100_000, 8, 16, 0, centers.data_ptr(), k_out.data_ptr(),
+                                     radius.data_ptr(), ct.byref(o)) == kc.KC_OK
+    assert torch.cuda.mem_get_info()[0] == free0
