@@ -87,14 +87,17 @@ typedef enum { KC_F32 = 0, KC_I32 = 1 } kc_dtype;
 
 /*
  * Storage precision of the Gonzalez sweep for float points (kc_opts.sweep).
- * KC_SWEEP_BF16 / KC_SWEEP_FP8 stream a bf16 (or fp8 e4m3 with a per-column
- * scale max|x_j| / 448) copy of the points and keep, per point, an error bound
+ * KC_SWEEP_BF16 / KC_SWEEP_FP16 / KC_SWEEP_FP8 stream a bf16 (or fp16 with
+ * one power-of-two scale for all coordinates, chosen from the largest
+ * magnitude so that nothing overflows; or fp8 e4m3 with a per-column scale
+ * max|x_j| / 448) copy of the points and keep, per point, an error bound
  * e_x >= ||decoded(x) - x||_2.  Every candidate whose low-precision distance
  * could reach the step's maximum is recomputed in canonical FP32 from the
  * FP32 points, so the selected centers, k_out and radius are identical to
- * KC_SWEEP_F32.  Ignored for int32 points.
+ * KC_SWEEP_F32.  fp16 streams as many bytes as bf16 with 3 more mantissa
+ * bits, so far fewer candidates need the recheck.  Ignored for int32 points.
  */
-typedef enum { KC_SWEEP_F32 = 0, KC_SWEEP_BF16 = 1, KC_SWEEP_FP8 = 2 } kc_sweep;
+typedef enum { KC_SWEEP_F32 = 0, KC_SWEEP_BF16 = 1, KC_SWEEP_FP8 = 2, KC_SWEEP_FP16 = 3 } kc_sweep;
 
 /* Flags for kc_opts.flags. */
 #define KC_ASYNC 1u        /* enqueue only; see kc_sync() */

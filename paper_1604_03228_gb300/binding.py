@@ -38,8 +38,8 @@ class kc_opts(ct.Structure):
                 ("stream", ct.c_void_p), ("timeout_ms", ct.c_int64)]
 
 
-KC_SWEEP_F32, KC_SWEEP_BF16, KC_SWEEP_FP8 = 0, 1, 2
-_SWEEPS = {"f32": 0, "bf16": 1, "fp8": 2, None: 0, 0: 0, 1: 1, 2: 2}
+KC_SWEEP_F32, KC_SWEEP_BF16, KC_SWEEP_FP8, KC_SWEEP_FP16 = 0, 1, 2, 3
+_SWEEPS = {"f32": 0, "bf16": 1, "fp8": 2, "fp16": 3, None: 0, 0: 0, 1: 1, 2: 2, 3: 3}
 
 
 _LIB = None

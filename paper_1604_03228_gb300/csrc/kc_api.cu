@@ -285,7 +285,7 @@ kc_status begin(const kc_opts *opts, CallCtx &c, uint32_t allowed = KC_ASYNC) {
     c.o = opts ? *opts : default_opts();
     if (c.o.dtype != KC_F32 && c.o.dtype != KC_I32) return fail(KC_ERR_ARG, "dtype must be KC_F32 or KC_I32");
     if (c.o.flags & ~allowed) return fail(KC_ERR_ARG, "flags 0x%x not accepted by this call", c.o.flags);
-    if (c.o.sweep < KC_SWEEP_F32 || c.o.sweep > KC_SWEEP_FP8) return fail(KC_ERR_ARG, "unknown sweep %d", c.o.sweep);
+    if (c.o.sweep < KC_SWEEP_F32 || c.o.sweep > KC_SWEEP_FP16) return fail(KC_ERR_ARG, "unknown sweep %d", c.o.sweep);
     c.s = (cudaStream_t)c.o.stream;
     c.async = (c.o.flags & KC_ASYNC) != 0;
     KC_CUDA(cudaGetDevice(&c.dev), "cudaGetDevice");
@@ -313,6 +313,15 @@ kc_status stage_points(const CallCtx &c, const void *pts, size_t bytes, bool dev
 
 // Low-precision sweep kind for a call: only float points use it.
 int lp_of(const kc_opts &o) { return o.dtype == KC_F32 ? o.sweep : 0; }
+
+// CTA groups of the mixed-precision sweep filter their exact rechecks against
+// their own largest lower bound (1) or the group's (0); KC_LP_LOCAL_T=0|1
+// overrides the default (the group's bound for bf16 and fp8, whose wide error
+// bands make a CTA's own band hold many points; the CTA's own for fp16).
+int lp_local_t(int lp) {
+    if (const char *env = getenv("KC_LP_LOCAL_T")) return atoi(env) != 0;
+    return lp == KC_SWEEP_FP16;
+}
 
 // Scratch of the mixed-precision sweep over one packed array of n points.
 struct LPBufs {
@@ -586,8 +595,10 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         if (lp) {
             attach_lp(g.single, LB, lp, cenT, keff, ecmax);
             g.lp_kind = lp;
+            g.lp_local_t = lp_local_t(lp);
             ra.eblk = LB.eblk;
             ra.ecmax = ecmax;
+            ra.lpscale = lp == KC_SWEEP_FP16 ? LB.scale : nullptr;
         }
         ra.pk = pk;
         ra.dtype = c.o.dtype;
@@ -631,6 +642,8 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     const void *src;
     r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, staging, &src, pin_pts);
     if (r != KC_OK) return r;
+    // exact rechecks read the FP32 rows where they are in device memory
+    if (lp && !pin_pts) g.single.rm = (const float *)src;
     {
         TraceStep t("pack", c.s);
         KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)g.single.pk, (int32_t *)g.single.range2,
@@ -1002,6 +1015,8 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
     const void *src;
     r = stage_points(c, pts, (size_t)n * d * esz, dev_pts, Lo.staging, &src, pin_pts);
     if (r != KC_OK) return r;
+    if (lp && !pin_pts)
+        for (int i = 0; i < m; ++i) h1[i].rm = (const float *)src + off[i] * d;
     r = upload(c.arena, c.s, h1.data(), h1.size() * sizeof(GonInst), Lo.insts1);
     if (r != KC_OK) return r;
     const long long tmo = timeout_cycles(c.o);
@@ -1026,6 +1041,7 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
         g.grid = grid1;
         g.counter = Lo.counter;
         g.lp_kind = lp;
+        g.lp_local_t = lp_local_t(lp);
         g.queue = 1;   // queue kernel: every part a CTA group, or one CTA per part from the queue
         if (!queue1) {
             g.nheavy = m;
@@ -1419,6 +1435,7 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
         if (lp) {
             attach_lp(g.single, LB, lp, cenT, kC, ecmax);
             g.lp_kind = lp;
+            g.lp_local_t = lp_local_t(lp);
         }
         g.st = st;
         g.timeout_cycles = timeout_cycles(c.o);
@@ -1773,8 +1790,9 @@ kc_status batch_check(int32_t count, const void *const *pts, const int64_t *n, c
     b.count = count;
     b.dtype = o.dtype;
     b.lp = lp_of(o);
-    if (b.lp == KC_SWEEP_FP8)
-        return fail(KC_ERR_ARG, "the batched form takes KC_SWEEP_F32 or KC_SWEEP_BF16 (fp8 needs per-instance scales)");
+    if (b.lp == KC_SWEEP_FP8 || b.lp == KC_SWEEP_FP16)
+        return fail(KC_ERR_ARG,
+                    "the batched form takes KC_SWEEP_F32 or KC_SWEEP_BF16 (fp8 and fp16 need per-instance scales)");
     b.dc = (dcommon == 3 || dcommon == 8 || dcommon == 32) && o.dtype == KC_F32 ? dcommon : 0;
     b.dmax = dmax;
     return KC_OK;

@@ -291,6 +291,15 @@ template <> struct LPDec<KC_SWEEP_BF16> {
         o[1] = __uint_as_float(w & 0xFFFF0000u);
     }
 };
+// fp16 codes decode to their fp16 values, in the pack's scaled units (the
+// sweep never leaves them).
+template <> struct LPDec<KC_SWEEP_FP16> {
+    __device__ static __forceinline__ void dec(uint32_t w, const float *, float o[2]) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        o[0] = f.x;
+        o[1] = f.y;
+    }
+};
 template <> struct LPDec<KC_SWEEP_FP8> {
     __device__ static __forceinline__ void dec(uint32_t w, const float *sc, float o[4]) {
 #pragma unroll
@@ -330,10 +339,36 @@ constexpr int MEMO_LANE_GAP = 4;   // gaps up to this many centers: one lane per
 
 // Canonical FP32 squared distance of packed point gx and center i of cenT,
 // loads issued four coordinates at a time (coordinates past d are zero
-// pairs, whose term fma(0, 0, acc) leaves acc unchanged).
+// pairs, whose term fma(0, 0, acc) leaves acc unchanged).  row: the point's
+// FP32 row when the instance has one (then read with 16-byte loads, all of
+// them in flight at once, when d % 4 == 0 and the row is aligned).
 __device__ __forceinline__ float memo_dist(const float *__restrict__ pk, int64_t gx, int d,
-                                           const float *__restrict__ cenT, int kcap, int i) {
+                                           const float *__restrict__ cenT, int kcap, int i,
+                                           const float *__restrict__ row = nullptr) {
     float acc = 0.f;
+    if (row) {
+        if ((d & 3) == 0 && ((uintptr_t)row & 15) == 0) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(row);
+            for (int q0 = 0; q0 < d / 4; q0 += 8) {
+                float4 xv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (q0 + u < d / 4) xv[u] = __ldg(r4 + q0 + u);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (q0 + u < d / 4) {
+                        const int j = 4 * (q0 + u);
+                        acc = sq_step(acc, xv[u].x, cenT[(int64_t)j * kcap + i]);
+                        acc = sq_step(acc, xv[u].y, cenT[(int64_t)(j + 1) * kcap + i]);
+                        acc = sq_step(acc, xv[u].z, cenT[(int64_t)(j + 2) * kcap + i]);
+                        acc = sq_step(acc, xv[u].w, cenT[(int64_t)(j + 3) * kcap + i]);
+                    }
+            }
+        } else {
+            for (int j = 0; j < d; ++j) acc = sq_step(acc, __ldg(row + j), cenT[(int64_t)j * kcap + i]);
+        }
+        return acc;
+    }
     for (int j0 = 0; j0 < d; j0 += 4) {
         float xv[4], cv[4];
 #pragma unroll
@@ -351,10 +386,11 @@ __device__ __forceinline__ float memo_dist(const float *__restrict__ pk, int64_t
 // One lane, centers [stamp, ncen) in order.
 __device__ __forceinline__ uint32_t memo_min_lane(const float *__restrict__ pk, int64_t gx, int d,
                                                   const float *__restrict__ cenT, int kcap, int ncen,
-                                                  uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp) {
+                                                  uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp,
+                                                  const float *__restrict__ row) {
     const int s0 = (int)stamp[gx];
     uint32_t m = s0 ? m32[gx] : 0xFFFFFFFFu;
-    for (int i = s0; i < ncen; ++i) m = min(m, __float_as_uint(memo_dist(pk, gx, d, cenT, kcap, i)));
+    for (int i = s0; i < ncen; ++i) m = min(m, __float_as_uint(memo_dist(pk, gx, d, cenT, kcap, i, row)));
     m32[gx] = m;
     stamp[gx] = (uint32_t)ncen;
     return m;
@@ -363,10 +399,11 @@ __device__ __forceinline__ uint32_t memo_min_lane(const float *__restrict__ pk, 
 // The whole warp: lane l takes centers stamp + l, stamp + l + 32, ...
 __device__ uint32_t memo_min_warp(const float *__restrict__ pk, int64_t gx, int d, const float *__restrict__ cenT,
                                   int kcap, int ncen, uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp,
-                                  int lane) {
+                                  int lane, const float *__restrict__ row) {
     const int s0 = (int)stamp[gx];
     uint32_t m = s0 ? m32[gx] : 0xFFFFFFFFu;
-    for (int i = s0 + lane; i < ncen; i += 32) m = min(m, __float_as_uint(memo_dist(pk, gx, d, cenT, kcap, i)));
+    for (int i = s0 + lane; i < ncen; i += 32)
+        m = min(m, __float_as_uint(memo_dist(pk, gx, d, cenT, kcap, i, row)));
 #pragma unroll
     for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
     __syncwarp();
@@ -386,7 +423,8 @@ __device__ __forceinline__ void memo_recheck(const GonInst &I, const float *__re
     const int64_t gx = I.lo + idx;
     const bool small = want && ncen - (int)I.stamp[gx] <= MEMO_LANE_GAP;
     if (small) {
-        const uint32_t mm = memo_min_lane(pk, gx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp);
+        const uint32_t mm = memo_min_lane(pk, gx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp,
+                                          I.rm ? I.rm + (int64_t)idx * d : nullptr);
         best = umax64(best, make_key(mm, idx));
         ++nre;
     }
@@ -396,7 +434,8 @@ __device__ __forceinline__ void memo_recheck(const GonInst &I, const float *__re
         const int src = __ffs(big) - 1;
         big &= big - 1;
         const uint32_t bidx = __shfl_sync(0xFFFFFFFFu, idx, src);
-        const uint32_t mm = memo_min_warp(pk, I.lo + bidx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp, lane);
+        const uint32_t mm = memo_min_warp(pk, I.lo + bidx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp, lane,
+                                          I.rm ? I.rm + (int64_t)bidx * d : nullptr);
         if (lane == src) {
             best = umax64(best, make_key(mm, bidx));
             ++nre;
@@ -452,7 +491,7 @@ __device__ __forceinline__ void lp_load_center(const GonInst &I, int64_t c, int 
 
 template <int KIND, int DC, int NT>
 __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &sh, DevStatus *st, long long timeout,
-                             int withhold = 0) {
+                             int withhold = 0, bool local_t = false) {
     constexpr int W = NT / 32;
     constexpr int LG = lp_group(KIND);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -614,7 +653,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
         if (clk && tid == 0) pc_mark(sh.pc, 0);
         float T = -INFINITY;
         for (int w = 0; w < W; ++w) T = fmaxf(T, sh.Lw[w]);
-        if (G > 1) {
+        if (G > 1 && !local_t) {
             // The group's largest lower bound: a point whose upper bound is
             // below it is strictly below that point's exact value, so only
             // candidates reaching it are rechecked (slots [k G, 2 k G)).
@@ -814,7 +853,7 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_lp_kernel(GonArgs a) {
     const int r = (int)blockIdx.x - I.cta0;
     if (r < 0 || r >= I.G) return;
     if (ld_volatile_i32(&a.st->code) != 0) return;
-    gon_solve_lp<KIND, DC, GROUP_NT>(I, r, I.G, smem_f, sh, a.st, a.timeout_cycles, a.withhold);
+    gon_solve_lp<KIND, DC, GROUP_NT>(I, r, I.G, smem_f, sh, a.st, a.timeout_cycles, a.withhold, a.lp_local_t != 0);
 }
 
 template <int KIND, int DC>
@@ -828,7 +867,7 @@ __global__ void __launch_bounds__(QUEUE_NT, 4) gon_queue_lp_kernel(GonArgs a) {
         __syncthreads();
         const int r = (int)blockIdx.x - I.cta0;
         if (r >= 0 && r < I.G && ld_volatile_i32(&a.st->code) == 0)
-            gon_solve_lp<KIND, DC, QUEUE_NT>(I, r, I.G, smem_f, sh, a.st, a.timeout_cycles);
+            gon_solve_lp<KIND, DC, QUEUE_NT>(I, r, I.G, smem_f, sh, a.st, a.timeout_cycles, 0, a.lp_local_t != 0);
         __syncthreads();
     }
     for (;;) {
@@ -856,15 +895,25 @@ void *pick_group_lp(int kind, int dc) {
             default: return group_lp_fn<KC_SWEEP_FP8, 0>();
         }
     }
+    if (kind == KC_SWEEP_FP16) {
+        switch (dc) {
+            case 10: return group_lp_fn<KC_SWEEP_FP16, 10>();
+            case 16: return group_lp_fn<KC_SWEEP_FP16, 16>();
+            case 64: return group_lp_fn<KC_SWEEP_FP16, 64>();
+            default: return group_lp_fn<KC_SWEEP_FP16, 0>();
+        }
+    }
     switch (dc) {
         case 10: return group_lp_fn<KC_SWEEP_BF16, 10>();
         case 16: return group_lp_fn<KC_SWEEP_BF16, 16>();
+        case 64: return group_lp_fn<KC_SWEEP_BF16, 64>();
         default: return group_lp_fn<KC_SWEEP_BF16, 0>();
     }
 }
 
 void *pick_queue_lp(int kind, int dc) {
     if (kind == KC_SWEEP_FP8) return queue_lp_fn<KC_SWEEP_FP8, 0>();
+    if (kind == KC_SWEEP_FP16) return queue_lp_fn<KC_SWEEP_FP16, 0>();
     switch (dc) {
         case 3: return queue_lp_fn<KC_SWEEP_BF16, 3>();
         case 8: return queue_lp_fn<KC_SWEEP_BF16, 8>();

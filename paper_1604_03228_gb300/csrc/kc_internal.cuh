@@ -182,6 +182,11 @@ cudaError_t launch_range_check(const int32_t *range2, int d, DevStatus *st, cuda
 // centers written out are base + local index (or map[local] when map is set).
 struct GonInst {
     const void *pk;          // packed points of this instance (block aligned)
+    // FP32 rows of the instance's points, row of local index 0 (row-major,
+    // d floats per row), or nullptr: the exact rechecks of the mixed-precision
+    // sweep then read the packed copy (one point's coordinates 512 bytes
+    // apart) instead of one contiguous row
+    const float *rm;
     uint32_t *mind;          // [nblocks(n) * BLK] running minimum (value bits)
     uint64_t *slots;         // [k * G] per-step, per-CTA argmax keys (zeroed)
     int64_t *centers;        // [k] out
@@ -231,7 +236,12 @@ struct GonArgs {
     int *counter;            // queue mode: next instance (zeroed)
     int nheavy;              // queue mode: insts[0, nheavy) are solved by CTA groups first
     int gheavy;              // queue mode: CTAs of those groups (the first gheavy of the grid)
-    int lp_kind;             // 0: FP32 sweep; KC_SWEEP_BF16 / KC_SWEEP_FP8 (float points)
+    int lp_kind;             // 0: FP32 sweep; KC_SWEEP_BF16 / _FP16 / _FP8 (float points)
+    // mixed-precision sweep of a CTA group: 1 = each CTA filters its exact
+    // rechecks against its own largest lower bound (no extra exchange per
+    // step); 0 = the group first exchanges the CTAs' bounds and filters
+    // against the group's largest
+    int lp_local_t;
     // testing hook (KC_TEST_WITHHOLD): 1 + the step at which the last CTA of
     // a group does not publish its exchange slot, so that the group's waits
     // run out of their budget; 0 = never
@@ -261,6 +271,7 @@ inline void gon_single(GonArgs &g, const void *pk, int dtype, int64_t n, int d, 
                        uint64_t *final_key, const int32_t *range2, int grid) {
     GonInst &I = g.single;
     I.pk = pk;
+    I.rm = nullptr;
     I.mind = mind;
     I.slots = slots;
     I.centers = centers;
@@ -296,6 +307,7 @@ inline void gon_single(GonArgs &g, const void *pk, int dtype, int64_t n, int d, 
     g.queue = 0;
     g.counter = nullptr;
     g.lp_kind = 0;
+    g.lp_local_t = 0;
 }
 
 // Bounds on sqrt(m32) from the approximate minimum m~ (value bits), the
@@ -312,7 +324,8 @@ __device__ __forceinline__ float lp_lower(uint32_t mbits, float delta, float omg
 __host__ __device__ inline float lp_slack(int d) { return (float)(f32_gamma(d) + 0x1p-20); }
 
 // --------------------------------------------- low-precision sweep data
-// Coordinates per 32-bit word of the low-precision copy (bf16: 2, fp8: 4).
+// Coordinates per 32-bit word of the low-precision copy (bf16, fp16: 2;
+// fp8: 4).
 __host__ __device__ constexpr int lp_group(int kind) { return kind == KC_SWEEP_FP8 ? 4 : 2; }
 __host__ __device__ inline int lp_ngroups(int kind, int d) { return (d + lp_group(kind) - 1) / lp_group(kind); }
 // Build the low-precision copy of a packed FP32 array: words `lp`
@@ -404,6 +417,9 @@ struct RadiusArgs {
     // flag test then uses the upper bound U(x) (eblk per block, *ecmax)
     const float *eblk;
     const float *ecmax;
+    // fp16 sweep: the device word holding its power-of-two scale (the
+    // bounds above are in the scaled units); nullptr = 1
+    const float *lpscale;
     // tensor-core filter scratch (float points, d <= 128); tc_at null: CUDA cores
     void *tc_at, *tc_bt;
     float *tc_an, *tc_ae, *tc_cn, *tc_ce, *tc_mlo, *tc_mhi;

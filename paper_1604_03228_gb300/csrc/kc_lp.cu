@@ -2,7 +2,8 @@
 // mixed-precision sweep, with a rigorous per-point error bound.
 //
 // Layout: blocks of BLK points as in the FP32 pack; inside a block, 32-bit
-// words hold LP_G consecutive coordinates of one point (bf16: 2, fp8: 4):
+// words hold LP_G consecutive coordinates of one point (bf16, fp16: 2;
+// fp8: 4):
 //   word (i, jg) at ((i / BLK) * ng + jg) * BLK + i % BLK,  ng = ceil(d / LP_G),
 // so a lane's 16-byte load carries 4 points x LP_G coordinates.  Coordinates
 // past d are zero.
@@ -14,6 +15,13 @@
 // sums the exact squared differences with upward rounding.  e_pt holds it
 // per point (used for the centers), e_blk the maximum over each block (used in
 // the sweep).  The pack also zeroes the per-point stamp of the recheck memo.
+//
+// fp16 works in scaled units: one power of two S = 2^s for all coordinates,
+// s chosen from the largest magnitude M so that M / S < 2^14 (no overflow,
+// and 28 binades below it before fp16 runs out of normal numbers).  The code
+// is fp16(x / S), decoded(x) its fp16 value, and every quantity the sweep
+// uses (distances, e_x, the center bounds) is in units of S; S itself is
+// stored in scale[0] for the final radius test.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -43,11 +51,24 @@ __device__ __forceinline__ float fp8_scale(const unsigned *colmax, int j) {
     return m > 0.f ? m / 448.f : 1.f;
 }
 
+// fp16 exponent s (S = 2^s) from the column maxima: M / 2^s < 2^14 with M the
+// largest magnitude, kept within [-100, 100] (finite coordinates below 2^54
+// keep every scaled value and bound finite).
+__device__ __forceinline__ int fp16_exponent(const unsigned *colmax, int d) {
+    float m = 0.f;
+    for (int j = 0; j < d; ++j) m = fmaxf(m, __uint_as_float(colmax[j]));
+    if (!(m > 0.f)) return 0;
+    int e;
+    frexpf(m, &e);   // m = f 2^e, f in [0.5, 1)
+    const int s = e - 14;
+    return s < -100 ? -100 : (s > 100 ? 100 : s);
+}
+
 // One block b of BLK points (one thread per point).
 template <int KIND>
 __device__ void lp_pack_block(const float *__restrict__ pk, int64_t n, int d, const unsigned *__restrict__ colmax,
                               uint32_t *__restrict__ lp, float *__restrict__ ept, float *__restrict__ eblk,
-                              uint32_t *__restrict__ stamp, int64_t b) {
+                              uint32_t *__restrict__ stamp, int64_t b, float fp16_s = 1.f, float fp16_inv = 1.f) {
     constexpr int G = lp_group(KIND);
     const int ng = (d + G - 1) / G;
     {
@@ -68,6 +89,13 @@ __device__ void lp_pack_block(const float *__restrict__ pk, int64_t n, int d, co
                     code = (uint32_t)__bfloat16_as_ushort(q);
                     dec = __uint_as_float(code << 16);
                     word |= code << (16 * t);
+                } else if (KIND == KC_SWEEP_FP16) {
+                    // fp16(x / S); the unscaled value dec = fp16 * S is exact
+                    // (a power-of-two multiple of an 11-bit value, in range)
+                    const __half q = __float2half_rn(__fmul_rn(x, fp16_inv));
+                    code = (uint32_t)__half_as_ushort(q);
+                    dec = __fmul_rn(__half2float(q), fp16_s);
+                    word |= code << (16 * t);
                 } else {
                     const float s = j < d ? fp8_scale(colmax, j) : 1.f;
                     const __nv_fp8_storage_t q = __nv_cvt_float_to_fp8(__fdiv_rn(x, s), __NV_SATFINITE, __NV_E4M3);
@@ -83,7 +111,8 @@ __device__ void lp_pack_block(const float *__restrict__ pk, int64_t n, int d, co
             }
             lp[(b * ng + jg) * BLK + i] = word;
         }
-        const float e = valid ? __fsqrt_ru(e2) : 0.f;
+        float e = valid ? __fsqrt_ru(e2) : 0.f;
+        if (KIND == KC_SWEEP_FP16) e = __fmul_ru(e, fp16_inv);   // in units of S
         ept[b * BLK + i] = e;
         float m = e;
 #pragma unroll
@@ -109,7 +138,15 @@ __global__ void __launch_bounds__(BLK) lp_pack_kernel(const float *__restrict__ 
     const int ng = (d + G - 1) / G;
     if (KIND == KC_SWEEP_FP8 && blockIdx.x == 0)
         for (int j = threadIdx.x; j < ng * G; j += blockDim.x) scale[j] = j < d ? fp8_scale(colmax, j) : 1.f;
-    for (int64_t b = blockIdx.x; b < nblocks(n); b += gridDim.x) lp_pack_block<KIND>(pk, n, d, colmax, lp, ept, eblk, stamp, b);
+    float fs = 1.f, fi = 1.f;
+    if (KIND == KC_SWEEP_FP16) {
+        const int e = fp16_exponent(colmax, d);
+        fs = ldexpf(1.f, e);
+        fi = ldexpf(1.f, -e);
+        if (blockIdx.x == 0 && threadIdx.x == 0) scale[0] = fs;
+    }
+    for (int64_t b = blockIdx.x; b < nblocks(n); b += gridDim.x)
+        lp_pack_block<KIND>(pk, n, d, colmax, lp, ept, eblk, stamp, b, fs, fi);
 }
 
 // bf16 copies of many packed arrays in one launch (segment s owns blocks
@@ -153,12 +190,15 @@ cudaError_t launch_lp_pack(int kind, const float *pk, int64_t n, int d, unsigned
     const int64_t nb = nblocks(n);
     const int grid = (int)(nb < (int64_t)sms * 16 ? nb : (int64_t)sms * 16);
     int kernels = 1;
-    if (kind == KC_SWEEP_FP8) {
+    if (kind == KC_SWEEP_FP8 || kind == KC_SWEEP_FP16) {
         cudaMemsetAsync(colmax, 0, (size_t)d * sizeof(unsigned), s);
         const int64_t total = nb * (int64_t)d * BLK;
         const int g2 = (int)((total + 255) / 256 < (int64_t)sms * 8 ? (total + 255) / 256 : (int64_t)sms * 8);
         colmax_kernel<<<g2, 256, 0, s>>>(pk, n, d, colmax);
-        lp_pack_kernel<KC_SWEEP_FP8><<<grid, BLK, 0, s>>>(pk, n, d, colmax, scale, lp, ept, eblk, stamp);
+        if (kind == KC_SWEEP_FP8)
+            lp_pack_kernel<KC_SWEEP_FP8><<<grid, BLK, 0, s>>>(pk, n, d, colmax, scale, lp, ept, eblk, stamp);
+        else
+            lp_pack_kernel<KC_SWEEP_FP16><<<grid, BLK, 0, s>>>(pk, n, d, colmax, scale, lp, ept, eblk, stamp);
         kernels = 2;
     } else {
         lp_pack_kernel<KC_SWEEP_BF16><<<grid, BLK, 0, s>>>(pk, n, d, colmax, scale, lp, ept, eblk, stamp);

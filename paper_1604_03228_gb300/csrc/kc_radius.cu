@@ -154,12 +154,13 @@ __device__ __forceinline__ double flag_threshold(const unsigned long long *key32
 // with U(x) >= sqrt of the exact minimum (kc_gon.cu), which also bounds the
 // FP64 value within the same (1 - 3 gamma) margin.
 __device__ __forceinline__ bool can_reach(const uint32_t *mind, int64_t x, double thr, const float *eblk,
-                                          const float *ecmax, float opg) {
+                                          const float *ecmax, float opg, double sc) {
     if (!eblk) return (double)__uint_as_float(mind[x]) >= thr;
-    // mixed precision: 16-bit truncated codes, upper end of the code's interval
+    // mixed precision: 16-bit truncated codes, upper end of the code's
+    // interval; sc: the fp16 sweep's power-of-two unit (exact in double)
     const uint32_t hi = ((uint32_t)reinterpret_cast<const uint16_t *>(mind)[x] + 1u) << 16;
-    const float U = lp_upper(hi, __fadd_ru(eblk[x / BLK], *ecmax), opg);
-    return (double)U * (double)U >= thr;
+    const double U = (double)lp_upper(hi, __fadd_ru(eblk[x / BLK], *ecmax), opg) * sc;
+    return U * U >= thr;
 }
 
 // FP64 minimum over all centers of point x, computed by the whole warp (lane
@@ -203,10 +204,11 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, const float *__
                                    const float *__restrict__ cen, const int32_t *kc_dev, int kc_max,
                                    const uint32_t *__restrict__ mind, const unsigned long long *key32,
                                    unsigned long long *max64, double *m64, const DevStatus *st,
-                                   const float *eblk, const float *ecmax, const uint32_t *__restrict__ list,
-                                   const unsigned long long *lcount) {
+                                   const float *eblk, const float *ecmax, const float *lpscale,
+                                   const uint32_t *__restrict__ list, const unsigned long long *lcount) {
     if (ld_volatile_i32(&st->code) != 0) return;
     if (key_val(*key32) == 0) return;   // every minimum is exactly 0
+    const double sc = lpscale ? (double)*lpscale : 1.0;
     const int kc = (int)dev_count(kc_dev, kc_max);
     const double thr = flag_threshold(key32, d);
     const float opg = __fadd_ru(1.f, lp_slack(d));
@@ -217,7 +219,7 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, const float *__
          base += warps * 32) {
         const int64_t i = base + lane;
         const int64_t x = i < cnt ? (list ? (int64_t)list[i] : i) : 0;
-        const bool flag = i < cnt && can_reach(mind, x, thr, eblk, ecmax, opg);
+        const bool flag = i < cnt && can_reach(mind, x, thr, eblk, ecmax, opg, sc);
         unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);
         while (todo) {
             const int src = __ffs(todo) - 1;
@@ -237,9 +239,11 @@ __global__ void recheck_arg_kernel(int64_t n, int d, const uint32_t *__restrict_
                                    const unsigned long long *key32, const unsigned long long *max64,
                                    const double *__restrict__ m64, unsigned long long *arg64,
                                    const DevStatus *st, const float *eblk, const float *ecmax,
-                                   const uint32_t *__restrict__ list, const unsigned long long *lcount) {
+                                   const float *lpscale, const uint32_t *__restrict__ list,
+                                   const unsigned long long *lcount) {
     if (ld_volatile_i32(&st->code) != 0) return;
     if (key_val(*key32) == 0) return;
+    const double sc = lpscale ? (double)*lpscale : 1.0;
     const double thr = flag_threshold(key32, d);
     const float opg = __fadd_ru(1.f, lp_slack(d));
     const double M = __longlong_as_double((long long)*max64);
@@ -247,7 +251,7 @@ __global__ void recheck_arg_kernel(int64_t n, int d, const uint32_t *__restrict_
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t x = list ? (int64_t)list[i] : i;
-        if (can_reach(mind, x, thr, eblk, ecmax, opg) && m64[x] == M)
+        if (can_reach(mind, x, thr, eblk, ecmax, opg, sc) && m64[x] == M)
             atomicMax(arg64, 0xFFFFFFFFFFFFFFFFull - (unsigned long long)x);
     }
 }
@@ -340,9 +344,9 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
         const int grid = (int)(g > sms * 8 ? sms * 8 : g);
         recheck_max_kernel<<<grid, 256, 0, s>>>((const float *)a.pk, a.rm, a.n, a.d, (const float *)a.cen,
                                                 a.kc_dev, a.kc_max, a.mind, a.key32, a.max64, a.m64,
-                                                a.st, a.eblk, a.ecmax, list, lcount);
+                                                a.st, a.eblk, a.ecmax, a.lpscale, list, lcount);
         recheck_arg_kernel<<<grid, 256, 0, s>>>(a.n, a.d, a.mind, a.key32, a.max64, a.m64, a.arg64,
-                                                a.st, a.eblk, a.ecmax, list, lcount);
+                                                a.st, a.eblk, a.ecmax, a.lpscale, list, lcount);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     finalize_kernel<<<1, 1, 0, s>>>(a.dtype, a.key32, a.max64, a.arg64, a.radius_out, a.argmax_out,

@@ -4,12 +4,19 @@ oracle checks (tests/sampled_checks.py) and identities between paths that
 must agree exactly (mixed-precision and FP32 sweeps; tensor-core and
 CUDA-core radius and prune), and the 4,096-instance plan against the oracle.
 """
+import hashlib
+import json
+import os
+
 import numpy as np
 import pytest
 
 from oracle import oracle as O
+from oracle_pool import batch_oracle
 from paper_1604_03228_gb300 import inputs as I
 from sampled_checks import farthest_steps, radius_checks, sample_rows
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -33,6 +40,47 @@ def gau8m():
 
 def _centers(res):
     return res.centers.cpu().numpy()
+
+
+def test_gon_10m_d16_golden_and_oracle_at_full_n(kc, unif10m):
+    """Whole center sequences at full n, element by element: the stored
+    oracle record (k = 32) and the oracle run here (k = 16, FP32 sweep and
+    bf16 sweep)."""
+    pts, _, _ = unif10m
+    g = json.load(open(os.path.join(GOLDEN, "gon_unif_n10000000_d16_k32.json")))
+    assert hashlib.sha256(pts.tobytes()).hexdigest() == g["points_sha256"]
+    x = _dev(pts)
+    res = kc.kc_gonzalez(x, g["k"])
+    assert _centers(res).tolist() == g["centers"] and res.radius == g["radius"]
+    ref = O.gonzalez(pts, 16, mode="f32")
+    for sw in (None, "bf16"):
+        r16 = kc.kc_gonzalez(x, 16, sweep=sw)
+        assert _centers(r16).tolist() == ref.centers.tolist()
+        assert r16.radius == ref.radius
+
+
+def test_mrg_10m_zipf_parts_oracle_at_full_n(kc, unif10m):
+    """MRG on the 64 Zipf parts at full n with k = 16 per part: the round-2
+    selection and the radius equal the oracle's."""
+    pts, off, _ = unif10m
+    ref = O.mrg(pts, 16, off, mode="f32")
+    x, o = _dev(pts), _dev(off)
+    for sw in (None, "bf16"):
+        m = kc.kc_mrg(x, 16, len(off) - 1, o, sweep=sw)
+        assert _centers(m).tolist() == ref.centers.tolist()
+        assert m.radius == ref.radius
+
+
+def test_gon_8m_d64_oracle_at_full_n(kc, gau8m):
+    """The 8M x 64 workload at full n with k = 16: the whole sequence and the
+    radius equal the oracle's, for the FP32 and bf16 sweeps."""
+    pts = gau8m
+    ref = O.gonzalez(pts, 16, mode="f32")
+    x = _dev(pts)
+    for sw in (None, "bf16"):
+        r = kc.kc_gonzalez(x, 16, sweep=sw)
+        assert _centers(r).tolist() == ref.centers.tolist()
+        assert r.radius == ref.radius
 
 
 def test_gon_10m_d16_k200(kc, unif10m):
@@ -114,10 +162,9 @@ def test_batch_4096_plan(kc):
     lp = kc.kc_gonzalez_batch(xs, ks, sweep="bf16")
     for r, q in zip(res, lp):
         assert r.centers.cpu().tolist() == q.centers.cpu().tolist() and r.radius == q.radius
-    rng = np.random.default_rng(16)
-    for i in rng.choice(len(insts), 8, replace=False):
-        z = insts[i]
-        ref = O.gonzalez(z.points, z.k, mode="f32")
-        assert res[i].centers.cpu().numpy().tolist() == ref.centers.tolist()
-        assert res[i].radius == O.radius(z.points, ref.centers, mode="f64")[0]
+    # every instance against the oracle, element by element
+    ref = batch_oracle(len(insts))
+    bad = [i for i in range(len(insts))
+           if (res[i].centers.cpu().numpy().tolist(), res[i].radius) != ref[i]]
+    assert bad == [], bad[:10]
     kc.kc_batch_plan_destroy(plan)

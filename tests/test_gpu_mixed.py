@@ -1,7 +1,8 @@
-"""Mixed-precision sweeps (bf16, fp8 e4m3 with per-column scale) must select
-exactly what the FP32 sweep selects: same center sequence, same k_out, same
-FP64 radius.  The FP32 path itself is pinned to the oracle elsewhere; here a
-few cases are also compared with the oracle directly.
+"""Mixed-precision sweeps (bf16, fp16 with one power-of-two scale, fp8 e4m3
+with per-column scale) must select exactly what the FP32 sweep selects: same
+center sequence, same k_out, same FP64 radius.  The FP32 path itself is pinned
+to the oracle elsewhere; here a few cases are also compared with the oracle
+directly.
 """
 import numpy as np
 import pytest
@@ -10,7 +11,7 @@ from oracle import oracle as O
 from paper_1604_03228_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
-SWEEPS = ["bf16", "fp8"]
+SWEEPS = ["bf16", "fp16", "fp8"]
 
 
 def _dev(x):
@@ -87,5 +88,46 @@ def test_batch_bf16_equals_f32(kc):
     b = kc.kc_gonzalez_batch(xs, ks)
     for ra, rb in zip(a, b):
         same(ra, rb)
-    with pytest.raises(kc.KCError):
-        kc.kc_gonzalez_batch(xs[:3], ks[:3], sweep="fp8")
+    for sw in ("fp8", "fp16"):
+        with pytest.raises(kc.KCError):
+            kc.kc_gonzalez_batch(xs[:3], ks[:3], sweep=sw)
+
+
+@pytest.mark.parametrize("scale", [1e-15, 1e-3, 1e4, 1e12])
+def test_fp16_scale_extremes(kc, scale):
+    # the fp16 copy is taken in units of a power of two fitted to the largest
+    # magnitude: tiny and huge coordinates select exactly as FP32 does
+    pts = (I.gauss_mixture(30000, 12, 507, 15, 0.3, -10, 10) * np.float32(scale)).astype(np.float32)
+    x = _dev(pts)
+    for k in (7, 90):
+        same(kc.kc_gonzalez(x, k, sweep="fp16"), kc.kc_gonzalez(x, k))
+    ref = O.gonzalez(pts, 90, mode="f32")
+    assert kc.kc_gonzalez(x, 90, sweep="fp16").centers.cpu().tolist() == ref.centers.tolist()
+
+
+@pytest.mark.parametrize("local_t", ["0", "1"])
+@pytest.mark.parametrize("sweep", ["bf16", "fp16"])
+def test_lp_group_and_local_bounds(kc, sweep, local_t, monkeypatch):
+    # CTA groups filter their exact rechecks against the group's largest lower
+    # bound or each CTA's own: both select what FP32 selects
+    monkeypatch.setenv("KC_LP_LOCAL_T", local_t)
+    pts = I.gauss_mixture(300_000, 64, 508, 40, 0.5, -10, 10)
+    x = _dev(pts)
+    same(kc.kc_gonzalez(x, 200, sweep=sweep), kc.kc_gonzalez(x, 200))
+    n, m = 300_000, 16
+    off = I.offsets_from_sizes(I.zipf_partition_sizes(n, m, 1.1))
+    same(kc.kc_mrg(x, 40, m, off, sweep=sweep), kc.kc_mrg(x, 40, m, off))
+
+
+def test_lp_rechecks_read_rows_or_packed_copy(kc):
+    # device rows (aligned or not) are read by the exact rechecks; pinned host
+    # rows are not (the packed copy is read instead): same selections
+    import torch
+    pts = I.gauss_mixture(100_000, 32, 509, 30, 0.5, -10, 10)
+    ref = kc.kc_gonzalez(_dev(pts), 120)
+    unal = torch.from_numpy(np.concatenate([pts[:1].ravel()[:1], pts.ravel()])).cuda()[1:].view(100_000, 32)
+    hp = torch.from_numpy(pts).pin_memory()
+    for sw in ("bf16", "fp16"):
+        same(kc.kc_gonzalez(unal, 120, sweep=sw), ref)
+        r = kc.kc_gonzalez(hp, 120, sweep=sw)
+        assert r.centers.tolist() == ref.centers.cpu().tolist() and r.radius == ref.radius

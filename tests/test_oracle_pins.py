@@ -441,3 +441,20 @@ def test_golden_int_10k_reproduces():
     w = I.gon_int_10k()
     r = O.gonzalez(w.points, w.k)
     assert [int(c) for c in r.centers] == g["centers"] and int(r.radius2) == g["radius2"]
+
+
+def test_golden_unif_10m_record_is_consistent():
+    """The stored 10M x 16 record: its point hash covers the generator (the
+    first rows of the stream are the same draws whatever n is), and the stored
+    selection has GON's invariants: first center 0, distinct centers, and
+    selected distances that never increase (Section 3.1)."""
+    import hashlib
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "gon_unif_n10000000_d16_k32.json")))
+    pre = I.unif_points(g["prefix_rows"], g["d"], 3)
+    assert hashlib.sha256(pre.tobytes()).hexdigest() == g["prefix_sha256"]
+    c, s2 = g["centers"], g["sel2_f32"]
+    assert c[0] == 0 and len(set(c)) == len(c) == g["k"]
+    assert all(a >= b for a, b in zip(s2[1:], s2[2:]))
+    assert g["radius"] > 0 and g["radius"] ** 2 <= s2[-1] * (1 + 1e-5)
