@@ -23,7 +23,7 @@ workload (seed 4 + 1000 * rank): weak scaling, no collective on the data path.
 
 --impl reference times the CPU oracle as it stands on all host cores: one
 worker process per core, each running the oracle's GON on its contiguous
-shard of the same point set (first 8 centers per shard), per step.
+shard of the same point set (first 32 centers per shard), per step.
 
 --workload NAME measures one of the other paths (one JSON line with the same
 keys): GON + radius on 1M x 10 (L2-resident, against the measured L2 read
@@ -56,7 +56,7 @@ L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 FALLBACK_BF16_TFLOPS = 1900.0
 CPU_K_SINGLE = 4      # oracle sample, one thread: GON with 4 centers on all n points
-CPU_K_SHARD = 8       # oracle sample, all cores: GON with 8 centers on each core's shard
+CPU_K_SHARD = 32      # oracle sample, all cores: GON with 32 centers on each core's shard
 
 # Further workloads (one JSON line each, same keys): GON + radius on the
 # L2-resident 1M x 10 set, the int GON latency case, GON / MRG on 10M x 16,
@@ -416,7 +416,7 @@ def run_gpu(args):
 
     # mixed precision on the same workload: the bf16 sweep, same selections
     mixed = {}
-    for sw in ("bf16",):
+    for sw in ("bf16", "fp16"):
         for _ in range(2):
             step(sw)
         assert kc.kc_sync(s) == kc.KC_OK

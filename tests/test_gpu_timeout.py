@@ -53,7 +53,9 @@ def test_withheld_slot_async_reports_at_sync(kc):
     kout = torch.empty(1, dtype=torch.int32, device="cuda").fill_(12345)   # stale count: must not be trusted
     rad = torch.empty(1, dtype=torch.float64, device="cuda")
     kc.kc_gonzalez(x, 16, flags=kc.KC_ASYNC | kc.KC_TEST_WITHHOLD, timeout_ms=1, out=(cen, kout, rad))
-    assert kc.kc_sync(s) == kc.KC_ERR_TIMEOUT
+    with pytest.raises(kc.KCError) as e:
+        kc.kc_sync(s)
+    assert e.value.status == kc.KC_ERR_TIMEOUT
     assert kc.kc_sync(s) == kc.KC_OK   # the status word was cleared
     kc.kc_gonzalez(x, 16, flags=kc.KC_ASYNC, out=(cen, kout, rad))
     assert kc.kc_sync(s) == kc.KC_OK
