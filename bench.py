@@ -83,7 +83,7 @@ def parse():
                     help="headline: leave out the 4,096-instance part of the mixed-precision comparison")
     ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD,) + EXTRA,
                     help="the default is the headline line; the others measure the remaining paths")
-    ap.add_argument("--sweep", default="f32", choices=["f32", "bf16", "fp8"],
+    ap.add_argument("--sweep", default="f32", choices=["f32", "bf16", "fp16", "fp8"],
                     help="sweep precision for the GON / MRG / batch workloads")
     ap.add_argument("--n", type=int, default=0,
                     help="fewer points than the configuration's (small profiling cases)")
@@ -493,7 +493,7 @@ def run_extra(args):
     torch.cuda.set_device(0)
     kc.load()
     name, sw = args.workload, (None if args.sweep == "f32" else args.sweep)
-    bpc = {"f32": 4, "bf16": 2, "fp8": 1}[args.sweep]
+    bpc = {"f32": 4, "bf16": 2, "fp16": 2, "fp8": 1}[args.sweep]
     mind_b = 4 if sw is None else 2          # running minimum: u32, or 16-bit code in the mixed sweep
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     cfg = {"workload": name, "sweep": args.sweep, "l2": "inputs larger than L2"}

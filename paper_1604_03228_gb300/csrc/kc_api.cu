@@ -315,12 +315,14 @@ kc_status stage_points(const CallCtx &c, const void *pts, size_t bytes, bool dev
 int lp_of(const kc_opts &o) { return o.dtype == KC_F32 ? o.sweep : 0; }
 
 // CTA groups of the mixed-precision sweep filter their exact rechecks against
-// their own largest lower bound (1) or the group's (0); KC_LP_LOCAL_T=0|1
-// overrides the default (the group's bound for bf16 and fp8, whose wide error
-// bands make a CTA's own band hold many points; the CTA's own for fp16).
+// their own largest lower bound (1) or the group's (0, the default);
+// KC_LP_LOCAL_T=0|1 overrides.  Measured on 8M x 64, k = 1024: the CTA's own
+// bound skips one exchange per step but leaves a different CTA rechecking
+// the most points at every step (bf16 180 -> 365 ms, fp16 183 -> 239 ms).
 int lp_local_t(int lp) {
+    (void)lp;
     if (const char *env = getenv("KC_LP_LOCAL_T")) return atoi(env) != 0;
-    return lp == KC_SWEEP_FP16;
+    return 0;
 }
 
 // Scratch of the mixed-precision sweep over one packed array of n points.
@@ -562,7 +564,11 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
 
     const int keff = (int)(k < n ? k : n);
     const int lp = lp_of(c.o);
-    const int grid = choose_gon_grid(c.o.dtype, d, n, lp);
+    // points that fit on chip: the resident kernel reads the rows in place
+    // (device memory or the staging copy) and keeps them for all k steps
+    int res_cap = 0, res_sw = 0;
+    const int res_grid = (!lp && !pin_pts) ? gon_resident_plan(c.o.dtype, d, n, &res_cap, &res_sw) : 0;
+    const int grid = res_grid ? res_grid : choose_gon_grid(c.o.dtype, d, n, lp);
     const int64_t nb = nblocks(n);
     const size_t esz = 4;
     LPBufs LB;
@@ -577,10 +583,11 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         unsigned long long *arg64 = cv.take<unsigned long long>(1);
         // per (step, CTA): argmax keys, and for the mixed-precision sweep the
         // CTAs' lower bounds too
-        uint64_t *slots = cv.take<uint64_t>((size_t)slot_words(keff, grid, lp != 0));
+        uint64_t *slots = cv.take<uint64_t>(res_grid ? (size_t)keff * grid * res_sw
+                                                      : (size_t)slot_words(keff, grid, lp != 0));
         *zero_bytes = cv.off;
         *staging = (dev_pts || pin_pts) ? nullptr : cv.take<char>((size_t)n * d * esz);
-        void *pk = cv.take<char>((size_t)nb * BLK * d * esz);
+        void *pk = res_grid ? nullptr : cv.take<char>((size_t)nb * BLK * d * esz);
         uint32_t *mind = cv.take<uint32_t>((size_t)nb * BLK);
         void *cen = cv.take<char>((size_t)keff * d * esz);
         double *m64 = cv.take<double>(c.o.dtype == KC_F32 ? (size_t)n : 1);
@@ -644,7 +651,13 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     if (r != KC_OK) return r;
     // exact rechecks read the FP32 rows where they are in device memory
     if (lp && !pin_pts) g.single.rm = (const float *)src;
-    {
+    if (res_grid) {
+        // the resident kernel reads (and checks) the rows itself: no pack
+        g.single.pk = src;
+        g.res_cap = res_cap;
+        ra.pk = nullptr;
+        ra.rm = (const float *)src;
+    } else {
         TraceStep t("pack", c.s);
         KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)g.single.pk, (int32_t *)g.single.range2,
                             c.arena->status, c.s),
@@ -657,6 +670,8 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     {
         TraceStep t("gonzalez", c.s);
         KC_CUDA(launch_gon(g, c.s), "gonzalez launch");
+        if (res_grid && c.o.dtype == KC_I32)
+            KC_CUDA(launch_range_check(g.single.range2, d, c.arena->status, c.s), "range check");
     }
     {
         TraceStep t("radius_recheck", c.s);

@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <cstdlib>
 #include <type_traits>
 
 #include "kc_internal.cuh"
@@ -342,20 +343,21 @@ constexpr int MEMO_LANE_GAP = 4;   // gaps up to this many centers: one lane per
 // pairs, whose term fma(0, 0, acc) leaves acc unchanged).  row: the point's
 // FP32 row when the instance has one (then read with 16-byte loads, all of
 // them in flight at once, when d % 4 == 0 and the row is aligned).
+template <bool VEC>
 __device__ __forceinline__ float memo_dist(const float *__restrict__ pk, int64_t gx, int d,
                                            const float *__restrict__ cenT, int kcap, int i,
-                                           const float *__restrict__ row = nullptr) {
+                                           const float *__restrict__ row) {
     float acc = 0.f;
     if (row) {
-        if ((d & 3) == 0 && ((uintptr_t)row & 15) == 0) {
+        if (VEC && (d & 3) == 0 && ((uintptr_t)row & 15) == 0) {
             const float4 *r4 = reinterpret_cast<const float4 *>(row);
-            for (int q0 = 0; q0 < d / 4; q0 += 8) {
-                float4 xv[8];
+            for (int q0 = 0; q0 < d / 4; q0 += 4) {
+                float4 xv[4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
+                for (int u = 0; u < 4; ++u)
                     if (q0 + u < d / 4) xv[u] = __ldg(r4 + q0 + u);
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
+                for (int u = 0; u < 4; ++u)
                     if (q0 + u < d / 4) {
                         const int j = 4 * (q0 + u);
                         acc = sq_step(acc, xv[u].x, cenT[(int64_t)j * kcap + i]);
@@ -384,26 +386,28 @@ __device__ __forceinline__ float memo_dist(const float *__restrict__ pk, int64_t
 }
 
 // One lane, centers [stamp, ncen) in order.
+template <bool VEC>
 __device__ __forceinline__ uint32_t memo_min_lane(const float *__restrict__ pk, int64_t gx, int d,
                                                   const float *__restrict__ cenT, int kcap, int ncen,
                                                   uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp,
                                                   const float *__restrict__ row) {
     const int s0 = (int)stamp[gx];
     uint32_t m = s0 ? m32[gx] : 0xFFFFFFFFu;
-    for (int i = s0; i < ncen; ++i) m = min(m, __float_as_uint(memo_dist(pk, gx, d, cenT, kcap, i, row)));
+    for (int i = s0; i < ncen; ++i) m = min(m, __float_as_uint(memo_dist<VEC>(pk, gx, d, cenT, kcap, i, row)));
     m32[gx] = m;
     stamp[gx] = (uint32_t)ncen;
     return m;
 }
 
 // The whole warp: lane l takes centers stamp + l, stamp + l + 32, ...
+template <bool VEC>
 __device__ uint32_t memo_min_warp(const float *__restrict__ pk, int64_t gx, int d, const float *__restrict__ cenT,
                                   int kcap, int ncen, uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp,
                                   int lane, const float *__restrict__ row) {
     const int s0 = (int)stamp[gx];
     uint32_t m = s0 ? m32[gx] : 0xFFFFFFFFu;
     for (int i = s0 + lane; i < ncen; i += 32)
-        m = min(m, __float_as_uint(memo_dist(pk, gx, d, cenT, kcap, i, row)));
+        m = min(m, __float_as_uint(memo_dist<VEC>(pk, gx, d, cenT, kcap, i, row)));
 #pragma unroll
     for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
     __syncwarp();
@@ -418,12 +422,13 @@ __device__ uint32_t memo_min_warp(const float *__restrict__ pk, int64_t gx, int 
 // Exact values of the points lanes flag (want; local index idx): small gaps
 // lane by lane, the rest one at a time by the whole warp.  Updates the lane's
 // best key and recheck count.
+template <bool VEC>
 __device__ __forceinline__ void memo_recheck(const GonInst &I, const float *__restrict__ pk, int d, int ncen,
                                              bool want, uint32_t idx, int lane, uint64_t &best, unsigned &nre) {
     const int64_t gx = I.lo + idx;
     const bool small = want && ncen - (int)I.stamp[gx] <= MEMO_LANE_GAP;
     if (small) {
-        const uint32_t mm = memo_min_lane(pk, gx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp,
+        const uint32_t mm = memo_min_lane<VEC>(pk, gx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp,
                                           I.rm ? I.rm + (int64_t)idx * d : nullptr);
         best = umax64(best, make_key(mm, idx));
         ++nre;
@@ -434,7 +439,7 @@ __device__ __forceinline__ void memo_recheck(const GonInst &I, const float *__re
         const int src = __ffs(big) - 1;
         big &= big - 1;
         const uint32_t bidx = __shfl_sync(0xFFFFFFFFu, idx, src);
-        const uint32_t mm = memo_min_warp(pk, I.lo + bidx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp, lane,
+        const uint32_t mm = memo_min_warp<VEC>(pk, I.lo + bidx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp, lane,
                                           I.rm ? I.rm + (int64_t)bidx * d : nullptr);
         if (lane == src) {
             best = umax64(best, make_key(mm, bidx));
@@ -682,7 +687,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                 const int e = e0 + lane;
                 Cand c = {0u, -INFINITY};
                 if (e < cnt) c = buf[e];
-                memo_recheck(I, pk, d, ncen, e < cnt && c.U >= T, c.idx, lane, best, nre);
+                memo_recheck<(DC > 0)>(I, pk, d, ncen, e < cnt && c.U >= T, c.idx, lane, best, nre);
             }
         } else {
             // the buffer overflowed: rescan the warp's running minima against
@@ -706,7 +711,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                     if (c2 > LP_CAP - 32) {
                         __syncwarp();
                         for (int e0 = 0; e0 < c2; e0 += 32)
-                            memo_recheck(I, pk, d, ncen, e0 + lane < c2, e0 + lane < c2 ? buf[e0 + lane].idx : 0u,
+                            memo_recheck<(DC > 0)>(I, pk, d, ncen, e0 + lane < c2, e0 + lane < c2 ? buf[e0 + lane].idx : 0u,
                                          lane, best, nre);
                         c2 = 0;
                         __syncwarp();
@@ -715,7 +720,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             }
             __syncwarp();
             for (int e0 = 0; e0 < c2; e0 += 32)
-                memo_recheck(I, pk, d, ncen, e0 + lane < c2, e0 + lane < c2 ? buf[e0 + lane].idx : 0u, lane, best,
+                memo_recheck<(DC > 0)>(I, pk, d, ncen, e0 + lane < c2, e0 + lane < c2 ? buf[e0 + lane].idx : 0u, lane, best,
                              nre);
         }
         nre = __reduce_add_sync(0xFFFFFFFFu, nre);
@@ -883,6 +888,248 @@ __global__ void __launch_bounds__(QUEUE_NT, 4) gon_queue_lp_kernel(GonArgs a) {
     }
 }
 
+// ------------------------------------------------ resident single GON
+//
+// For one instance whose points fit on chip across the grid (one CTA per SM),
+// every CTA keeps its contiguous share [lo_r, hi_r) of the rows for all k
+// steps: local point t + j * 1024 belongs to thread t; j = 0 sits in the
+// thread's registers, j >= 1 in shared memory, coordinate-major (column i of
+// coordinate c at c * cap + i - 1024, so a warp's loads hit 32 banks); the
+// running minima stay in registers and go to global memory once, at the end.
+// The rows are read where they lie (no packed copy), with the pack's checks
+// (NaN/Inf and magnitude for floats; the int32 range, checked after the
+// launch).  Each step's exchange slot carries the CTA's candidate with its
+// coordinates (one 64-bit word each: a non-zero tag over the value bits), so
+// the winner's coordinates arrive with the keys: warps 0..P-1 poll one slot
+// per lane until the key and every tag are in (bounded by the cycle budget).
+constexpr int RES_PPT = 8;   // points per thread (1 in registers + 7 in shared memory)
+
+__host__ __device__ constexpr int res_slot_words(int d) { return 1 + d; }
+
+struct ShRes {
+    uint64_t red[32];
+    uint32_t cand[32][12];   // each warp's candidate coordinates (value bits)
+    uint64_t pkey[8];        // each polling warp's best slot key
+    uint32_t pc[8][12];      // and its coordinates
+    int abort;
+};
+
+template <typename T>
+__device__ __forceinline__ uint32_t val_bits(T v) {
+    if constexpr (std::is_same<T, float>::value) return __float_as_uint(v);
+    else return (uint32_t)v;
+}
+template <typename T>
+__device__ __forceinline__ T bits_val(uint32_t b) {
+    if constexpr (std::is_same<T, float>::value) return __uint_as_float(b);
+    else return (T)(int32_t)b;
+}
+
+template <typename T>
+__device__ __forceinline__ void res_check(T v, bool &bad, bool &nonfin, uint32_t &lo, uint32_t &hi) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (!(fabsf(v) <= 0x1p54f)) bad = true;
+        if (!isfinite(v)) nonfin = true;
+    } else {
+        const uint32_t bv = (uint32_t)v ^ 0x80000000u;
+        lo = max(lo, 0xFFFFFFFFu - bv);
+        hi = max(hi, bv);
+    }
+}
+
+template <typename T, int DC>
+__global__ void __launch_bounds__(GROUP_NT, 1) gon_resident_kernel(GonArgs a) {
+    using A = typename AccOf<T>::type;
+    constexpr int NT = GROUP_NT, W = NT / 32, SW = res_slot_words(DC);
+    static_assert(DC <= 12, "candidate coordinates are staged in 12 words");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ ShRes sh;
+    const GonInst &I = a.single;
+    const T *__restrict__ rows = (const T *)I.pk;   // row-major [n][DC]
+    const int G = gridDim.x, r = blockIdx.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t lo_r = I.n * r / G, hi_r = I.n * (r + 1) / G;
+    const int np = (int)(hi_r - lo_r);
+    const int cap = a.res_cap;
+    T *sp = reinterpret_cast<T *>(smem_raw);
+    const int P = (G + 31) / 32;
+
+    // load this CTA's rows, with the pack's checks
+    T xr[DC];
+    {
+        bool bad = false, nonfin = false;
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int c = 0; c < DC; ++c) {
+            xr[c] = T(0);
+            if (tid < np) {
+                xr[c] = rows[(lo_r + tid) * DC + c];
+                res_check(xr[c], bad, nonfin, lo, hi);
+            }
+        }
+        const int64_t ns = np > NT ? (int64_t)(np - NT) * DC : 0;
+        const T *src = rows + (lo_r + NT) * DC;
+        for (int64_t e = tid; e < ns; e += NT) {
+            const int i = (int)(e / DC), c = (int)(e - (int64_t)i * DC);
+            const T v = src[e];
+            res_check(v, bad, nonfin, lo, hi);
+            sp[c * cap + i] = v;
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            if (nonfin) set_status(a.st, KC_ERR_NONFINITE, 1, 0);
+            else if (bad) set_status(a.st, KC_ERR_RANGE, 1, 0);
+        } else {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                lo = max(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+                hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+            }
+            if (lane == 0 && (lo | hi)) {
+                atomicMax((uint32_t *)&I.range2[0], lo);
+                atomicMax((uint32_t *)&I.range2[1], hi);
+            }
+        }
+    }
+    if (tid == 0) {
+        sh.abort = 0;
+        sh.pkey[0] = make_key(1u, (uint32_t)I.first);
+    }
+    if (warp == 0 && lane < DC) sh.pc[0][lane] = val_bits(rows[I.first * DC + lane]);
+    if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
+    __syncthreads();
+
+    uint32_t mm[RES_PPT];
+#pragma unroll
+    for (int j = 0; j < RES_PPT; ++j) mm[j] = 0xFFFFFFFFu;
+    int it, pw = 0;
+    uint64_t K = 0;
+    for (it = 0; it < I.k; ++it) {
+        T cc[DC];
+#pragma unroll
+        for (int c = 0; c < DC; ++c) cc[c] = bits_val<T>(sh.pc[pw][c]);
+        uint64_t best = 0;
+#pragma unroll
+        for (int j = 0; j < RES_PPT; ++j) {
+            const int i = tid + j * NT;
+            if (i < np) {
+                A acc = A(0);
+#pragma unroll
+                for (int c = 0; c < DC; ++c) acc = sq_step(acc, j == 0 ? xr[c] : sp[c * cap + (i - NT)], cc[c]);
+                mm[j] = min(mm[j], acc_bits(acc));
+                best = umax64(best, make_key(mm[j], (uint32_t)(lo_r + i)));
+            }
+        }
+        // the warp's candidate and its coordinates
+        const uint64_t wb = warp_max_u64(best);
+        const unsigned own = __ballot_sync(0xFFFFFFFFu, wb != 0 && best == wb);
+        if (own && lane == __ffs(own) - 1) {
+            const int i = (int)((int64_t)key_idx(wb) - lo_r);
+#pragma unroll
+            for (int c = 0; c < DC; ++c) sh.cand[warp][c] = val_bits(i < NT ? xr[c] : sp[c * cap + (i - NT)]);
+        }
+        if (lane == 0) sh.red[warp] = wb;
+        __syncthreads();
+        if (warp == 0) {
+            const uint64_t v = lane < W ? sh.red[lane] : 0;
+            const uint64_t g = warp_max_u64(v);
+            const unsigned ow = __ballot_sync(0xFFFFFFFFu, lane < W && g != 0 && v == g);
+            const int wsrc = ow ? __ffs(ow) - 1 : 0;
+            if (G > 1) {
+                uint64_t *row = I.slots + ((int64_t)it * G + r) * SW;
+                if (!(a.withhold == it + 1 && r == G - 1)) {
+                    if (lane < DC) st_relaxed_u64(row + 1 + lane, (1ull << 32) | sh.cand[wsrc][lane]);
+                    if (lane == 0) st_relaxed_u64(row, g ? g : 1);
+                }
+            } else {
+                if (lane == 0) sh.pkey[0] = g;
+                if (lane < DC) sh.pc[0][lane] = sh.cand[wsrc][lane];
+            }
+        }
+        if (G > 1 && warp < P) {
+            const int s = warp * 32 + lane;
+            uint64_t key = 0;
+            uint32_t cw[DC];
+            bool ab = false;
+            if (s < G) {
+                const uint64_t *row = I.slots + ((int64_t)it * G + s) * SW;
+                const long long t0 = clock64();
+                for (;;) {
+                    uint64_t w[DC];
+                    key = ld_relaxed_u64(row);
+#pragma unroll
+                    for (int c = 0; c < DC; ++c) w[c] = ld_relaxed_u64(row + 1 + c);
+                    bool done = key != 0;
+#pragma unroll
+                    for (int c = 0; c < DC; ++c) {
+                        done = done && (w[c] >> 32) != 0;
+                        cw[c] = (uint32_t)w[c];
+                    }
+                    if (done) break;
+                    if (clock64() - t0 > a.timeout_cycles || ld_volatile_i32(&a.st->code) != 0) {
+                        set_status(a.st, KC_ERR_TIMEOUT, 3, it);
+                        ab = true;
+                        key = 0;
+                        break;
+                    }
+                }
+            }
+            const uint64_t wk = warp_max_u64(key);
+            const unsigned ow = __ballot_sync(0xFFFFFFFFu, s < G && wk != 0 && key == wk);
+            if (ow && lane == __ffs(ow) - 1) {
+                sh.pkey[warp] = wk;
+#pragma unroll
+                for (int c = 0; c < DC; ++c) sh.pc[warp][c] = cw[c];
+            } else if (!ow && lane == 0) {
+                sh.pkey[warp] = 0;
+            }
+            if (__any_sync(0xFFFFFFFFu, ab) && lane == 0) sh.abort = 1;
+        }
+        __syncthreads();
+        if (sh.abort) return;
+        uint64_t g = 0;
+        pw = 0;
+        for (int q = 0; q < (G > 1 ? P : 1); ++q)
+            if (sh.pkey[q] > g) {
+                g = sh.pkey[q];
+                pw = q;
+            }
+        K = g;
+        if (key_val(K) == 0) {   // every point is at distance 0: stop early
+            ++it;
+            break;
+        }
+        if (r == 0 && tid == 0 && it + 1 < I.k) I.centers[it + 1] = out_index(I, key_idx(g));
+    }
+    // the running minima, for the radius recheck
+#pragma unroll
+    for (int j = 0; j < RES_PPT; ++j) {
+        const int i = tid + j * NT;
+        if (i < np) I.mind[lo_r + i] = mm[j];
+    }
+    if (r == 0 && tid == 0) {
+        *I.k_out = it;
+        *I.final_key = K;
+    }
+}
+
+template <typename T, int DC> void *resident_fn() { return (void *)gon_resident_kernel<T, DC>; }
+
+void *pick_resident(int dtype, int d) {
+    if (dtype == KC_F32) {
+        switch (d) {
+            case 2: return resident_fn<float, 2>();
+            case 3: return resident_fn<float, 3>();
+            case 8: return resident_fn<float, 8>();
+            case 10: return resident_fn<float, 10>();
+            default: return nullptr;
+        }
+    }
+    switch (d) {
+        case 2: return resident_fn<int32_t, 2>();
+        case 10: return resident_fn<int32_t, 10>();
+        default: return nullptr;
+    }
+}
+
 template <typename T, int DC> void *group_fn() { return (void *)gon_group_kernel<T, DC>; }
 template <typename T, int DC> void *queue_fn() { return (void *)gon_queue_kernel<T, DC>; }
 template <int KIND, int DC> void *group_lp_fn() { return (void *)gon_group_lp_kernel<KIND, DC>; }
@@ -917,6 +1164,7 @@ void *pick_queue_lp(int kind, int dc) {
     switch (dc) {
         case 3: return queue_lp_fn<KC_SWEEP_BF16, 3>();
         case 8: return queue_lp_fn<KC_SWEEP_BF16, 8>();
+        case 32: return queue_lp_fn<KC_SWEEP_BF16, 32>();
         default: return queue_lp_fn<KC_SWEEP_BF16, 0>();
     }
 }
@@ -1010,7 +1258,60 @@ int gon_queue_grid(int dtype, int d, int lp) {
     return gon_occupancy(pick_fn(dtype, lp, d, true), QUEUE_NT, smem_for(dtype, lp, d, true)) * sms;
 }
 
+int gon_resident_plan(int dtype, int d, int64_t n, int *cap, int *slot_words) {
+    if (const char *env = getenv("KC_GON_RESIDENT"))
+        if (atoi(env) == 0) return 0;
+    void *fn = pick_resident(dtype, d);
+    if (!fn || n < 1) return 0;
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int64_t want = (n + GROUP_NT - 1) / GROUP_NT;
+    const int G = (int)(want < sms ? want : sms);
+    const int64_t npmax = (n + G - 1) / G;
+    if (npmax > (int64_t)RES_PPT * GROUP_NT) return 0;
+    const int64_t c = npmax > GROUP_NT ? npmax - GROUP_NT : 1;
+    const size_t smem = (size_t)c * d * 4;
+    if (smem + sizeof(ShRes) + 1024 > (size_t)optin) return 0;
+    if (smem > 48 * 1024 && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, GROUP_NT, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    *cap = (int)c;
+    *slot_words = res_slot_words(d);
+    return G;
+}
+
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s) {
+    if (a.res_cap > 0) {
+        // resident single instance: one CTA per SM, all co-resident
+        void *fn = pick_resident(a.dtype, a.dc);
+        if (!fn) return cudaErrorInvalidValue;
+        const size_t smem = (size_t)a.res_cap * a.dc * 4;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        note_launches(1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(a.grid);
+        cfg.blockDim = dim3(GROUP_NT);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void *args[] = {&a};
+        return cudaLaunchKernelExC(&cfg, fn, args);
+    }
     const size_t smem = smem_for(a.dtype, a.lp_kind, a.dmax, a.queue != 0);
     void *fn = pick_fn(a.dtype, a.lp_kind, a.dc, a.queue != 0);
     if (smem > 48 * 1024) {

@@ -246,8 +246,16 @@ struct GonArgs {
     // a group does not publish its exchange slot, so that the group's waits
     // run out of their budget; 0 = never
     int withhold;
+    // resident form (single instance, gon_resident_kernel): points per
+    // coordinate held in each CTA's shared memory; 0 = the streaming kernels
+    int res_cap;
 };
 cudaError_t launch_gon(GonArgs &a, cudaStream_t s);
+// Resident form for one instance of n points (row-major rows in device
+// memory): the grid (0 when the instance does not fit on chip or d has no
+// specialisation), with the shared-memory columns per coordinate in *cap and
+// the exchange-slot words per (step, CTA) in *slot_words.
+int gon_resident_plan(int dtype, int d, int64_t n, int *cap, int *slot_words);
 // Mixed-precision diagnostics (synchronous): exact rechecks, overflows.
 cudaError_t read_counters(unsigned long long out[8], bool reset);
 int gon_max_grid(int dtype, int d, int lp = 0);

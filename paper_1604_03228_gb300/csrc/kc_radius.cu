@@ -316,13 +316,15 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
             gather_kernel<float><<<grid, 256, 0, s>>>((const float *)a.pk, a.rm, a.n, a.d, a.centers,
                                                       a.kc_dev, a.kc_max, (float *)a.cen, a.st);
         else
-            gather_kernel<int32_t><<<grid, 256, 0, s>>>((const int32_t *)a.pk, nullptr, a.n, a.d, a.centers,
-                                                        a.kc_dev, a.kc_max, (int32_t *)a.cen, a.st);
+            gather_kernel<int32_t><<<grid, 256, 0, s>>>((const int32_t *)a.pk, (const int32_t *)a.rm, a.n, a.d,
+                                                        a.centers, a.kc_dev, a.kc_max, (int32_t *)a.cen, a.st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // row-major points are read only by the tensor-core path
-    if (a.rm && (a.pk || a.have_mind || a.dtype != KC_F32 || !a.tc_at || !tc_supported(a.d)))
+    // row-major points (pk null) are read by the tensor-core path, and by
+    // the rechecks after a Gonzalez kernel that held the minima (have_mind)
+    if (a.rm && (a.pk || (!a.have_mind && (a.dtype != KC_F32 || !a.tc_at || !tc_supported(a.d)))))
         return cudaErrorInvalidValue;
+    if (!a.rm && !a.pk) return cudaErrorInvalidValue;
     if (!a.have_mind) {
         if (a.dtype == KC_F32 && a.tc_at && tc_supported(a.d)) {
             // tensor-core filter: fp16 dot products bound every point's
