@@ -428,6 +428,12 @@ def run_gpu(args):
         mixed[f"gon_{sw}_ms"] = statistics.median(ms)
         mixed[f"gon_{sw}_identical_selection"] = same
         mixed[f"gon_{sw}_rechecks_per_solve"] = cnt[0] / args.steps
+        # per-CTA phase time of the persistent kernel (clock cycles summed
+        # over CTAs, per solve, at the sampled SM clock)
+        ctas = max(1, int(torch.cuda.get_device_properties(local).multi_processor_count))
+        mhz = (sampler.summary(0, time.time()).get("sm_mhz") or 2070.0)
+        mixed[f"gon_{sw}_phase_ms"] = {ph: cnt[i] / args.steps / ctas / (mhz * 1e3)
+                                       for ph, i in (("sweep", 6), ("recheck", 7), ("exchange", 8))}
         mixed[f"gon_{sw}_speedup"] = statistics.median(step_ms) / statistics.median(ms)
     mixed["gon_f32_ms"] = statistics.median(step_ms)
     if not args.no_batch:

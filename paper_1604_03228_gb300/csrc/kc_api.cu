@@ -1747,6 +1747,9 @@ std::vector<char> batch_descriptors(const BatchShape &b, BatchBufs &B, const voi
             I.stamp = P.stamp;
             I.ecmax_out = P.ecmax;
             I.lp_kind = b.lp;
+            // the exact rechecks read the instance's FP32 rows (device memory
+            // or its staging copy) rather than its packed copy
+            I.rm = (const float *)(dev_pts[i] ? pts[i] : P.staging);
         }
     }
     B.blocks = blk0;

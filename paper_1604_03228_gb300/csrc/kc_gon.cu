@@ -899,9 +899,10 @@ __global__ void __launch_bounds__(QUEUE_NT, 4) gon_queue_lp_kernel(GonArgs a) {
 // The rows are read where they lie (no packed copy), with the pack's checks
 // (NaN/Inf and magnitude for floats; the int32 range, checked after the
 // launch).  Each step's exchange slot carries the CTA's candidate with its
-// coordinates (one 64-bit word each: a non-zero tag over the value bits), so
-// the winner's coordinates arrive with the keys: warps 0..P-1 poll one slot
-// per lane until the key and every tag are in (bounded by the cycle budget).
+// coordinates (one 64-bit word each: a non-zero tag over the value bits):
+// warp 0 polls the keys (up to five slots per lane, all loads in flight),
+// then reads the winner's coordinates from its slot, still in L2, waiting for
+// each tag (every wait bounded by the cycle budget).
 constexpr int RES_PPT = 8;   // points per thread (1 in registers + 7 in shared memory)
 
 __host__ __device__ constexpr int res_slot_words(int d) { return 1 + d; }
@@ -909,8 +910,8 @@ __host__ __device__ constexpr int res_slot_words(int d) { return 1 + d; }
 struct ShRes {
     uint64_t red[32];
     uint32_t cand[32][12];   // each warp's candidate coordinates (value bits)
-    uint64_t pkey[8];        // each polling warp's best slot key
-    uint32_t pc[8][12];      // and its coordinates
+    uint64_t pkey[1];        // the step's winning key
+    uint32_t pc[1][12];      // and its coordinates: the next center
     int abort;
 };
 
@@ -951,7 +952,6 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_resident_kernel(GonArgs a) {
     const int np = (int)(hi_r - lo_r);
     const int cap = a.res_cap;
     T *sp = reinterpret_cast<T *>(smem_raw);
-    const int P = (G + 31) / 32;
 
     // load this CTA's rows, with the pack's checks
     T xr[DC];
@@ -1000,12 +1000,12 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_resident_kernel(GonArgs a) {
     uint32_t mm[RES_PPT];
 #pragma unroll
     for (int j = 0; j < RES_PPT; ++j) mm[j] = 0xFFFFFFFFu;
-    int it, pw = 0;
+    int it;
     uint64_t K = 0;
     for (it = 0; it < I.k; ++it) {
         T cc[DC];
 #pragma unroll
-        for (int c = 0; c < DC; ++c) cc[c] = bits_val<T>(sh.pc[pw][c]);
+        for (int c = 0; c < DC; ++c) cc[c] = bits_val<T>(sh.pc[0][c]);
         uint64_t best = 0;
 #pragma unroll
         for (int j = 0; j < RES_PPT; ++j) {
@@ -1034,64 +1034,73 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_resident_kernel(GonArgs a) {
             const unsigned ow = __ballot_sync(0xFFFFFFFFu, lane < W && g != 0 && v == g);
             const int wsrc = ow ? __ffs(ow) - 1 : 0;
             if (G > 1) {
-                uint64_t *row = I.slots + ((int64_t)it * G + r) * SW;
+                // publish the CTA's candidate: coordinates (tagged) and key
+                uint64_t *mine = I.slots + ((int64_t)it * G + r) * SW;
                 if (!(a.withhold == it + 1 && r == G - 1)) {
-                    if (lane < DC) st_relaxed_u64(row + 1 + lane, (1ull << 32) | sh.cand[wsrc][lane]);
-                    if (lane == 0) st_relaxed_u64(row, g ? g : 1);
+                    if (lane < DC) st_relaxed_u64(mine + 1 + lane, (1ull << 32) | sh.cand[wsrc][lane]);
+                    if (lane == 0) st_relaxed_u64(mine, g ? g : 1);
+                }
+                // poll the keys of the step's slots (lane: slots lane + 32 q)
+                const uint64_t *row = I.slots + (int64_t)it * G * SW;
+                uint64_t kv[5] = {0, 0, 0, 0, 0};
+                unsigned pend = 0;
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    if (lane + 32 * q < G) pend |= 1u << q;
+                bool ab = false;
+                const long long t0 = clock64();
+                while (pend) {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q)
+                        if (pend >> q & 1u) kv[q] = ld_relaxed_u64(row + (int64_t)(lane + 32 * q) * SW);
+#pragma unroll
+                    for (int q = 0; q < 5; ++q)
+                        if ((pend >> q & 1u) && kv[q] != 0) pend &= ~(1u << q);
+                    if (pend && (clock64() - t0 > a.timeout_cycles || ld_volatile_i32(&a.st->code) != 0)) {
+                        set_status(a.st, KC_ERR_TIMEOUT, 3, it);
+                        ab = true;
+                        break;
+                    }
+                }
+                ab = __any_sync(0xFFFFFFFFu, ab);
+                uint64_t lk = 0;
+                int ls = 0;
+#pragma unroll
+                for (int q = 0; q < 5; ++q)
+                    if (kv[q] > lk) {
+                        lk = kv[q];
+                        ls = lane + 32 * q;
+                    }
+                const uint64_t gg = warp_max_u64(lk);
+                const unsigned wl = __ballot_sync(0xFFFFFFFFu, gg != 0 && lk == gg);
+                const int win = __shfl_sync(0xFFFFFFFFu, ls, wl ? __ffs(wl) - 1 : 0);
+                // the winner's coordinates from its slot (each tag set once written)
+                if (!ab && lane < DC) {
+                    const uint64_t *wp = row + (int64_t)win * SW + 1 + lane;
+                    uint64_t w = ld_relaxed_u64(wp);
+                    while ((w >> 32) == 0) {
+                        if (clock64() - t0 > a.timeout_cycles || ld_volatile_i32(&a.st->code) != 0) {
+                            set_status(a.st, KC_ERR_TIMEOUT, 3, it);
+                            ab = true;
+                            break;
+                        }
+                        w = ld_relaxed_u64(wp);
+                    }
+                    sh.pc[0][lane] = (uint32_t)w;
+                }
+                ab = __any_sync(0xFFFFFFFFu, ab);
+                if (lane == 0) {
+                    sh.pkey[0] = gg;
+                    if (ab) sh.abort = 1;
                 }
             } else {
                 if (lane == 0) sh.pkey[0] = g;
                 if (lane < DC) sh.pc[0][lane] = sh.cand[wsrc][lane];
             }
         }
-        if (G > 1 && warp < P) {
-            const int s = warp * 32 + lane;
-            uint64_t key = 0;
-            uint32_t cw[DC];
-            bool ab = false;
-            if (s < G) {
-                const uint64_t *row = I.slots + ((int64_t)it * G + s) * SW;
-                const long long t0 = clock64();
-                for (;;) {
-                    uint64_t w[DC];
-                    key = ld_relaxed_u64(row);
-#pragma unroll
-                    for (int c = 0; c < DC; ++c) w[c] = ld_relaxed_u64(row + 1 + c);
-                    bool done = key != 0;
-#pragma unroll
-                    for (int c = 0; c < DC; ++c) {
-                        done = done && (w[c] >> 32) != 0;
-                        cw[c] = (uint32_t)w[c];
-                    }
-                    if (done) break;
-                    if (clock64() - t0 > a.timeout_cycles || ld_volatile_i32(&a.st->code) != 0) {
-                        set_status(a.st, KC_ERR_TIMEOUT, 3, it);
-                        ab = true;
-                        key = 0;
-                        break;
-                    }
-                }
-            }
-            const uint64_t wk = warp_max_u64(key);
-            const unsigned ow = __ballot_sync(0xFFFFFFFFu, s < G && wk != 0 && key == wk);
-            if (ow && lane == __ffs(ow) - 1) {
-                sh.pkey[warp] = wk;
-#pragma unroll
-                for (int c = 0; c < DC; ++c) sh.pc[warp][c] = cw[c];
-            } else if (!ow && lane == 0) {
-                sh.pkey[warp] = 0;
-            }
-            if (__any_sync(0xFFFFFFFFu, ab) && lane == 0) sh.abort = 1;
-        }
         __syncthreads();
         if (sh.abort) return;
-        uint64_t g = 0;
-        pw = 0;
-        for (int q = 0; q < (G > 1 ? P : 1); ++q)
-            if (sh.pkey[q] > g) {
-                g = sh.pkey[q];
-                pw = q;
-            }
+        const uint64_t g = sh.pkey[0];
         K = g;
         if (key_val(K) == 0) {   // every point is at distance 0: stop early
             ++it;
@@ -1268,7 +1277,8 @@ int gon_resident_plan(int dtype, int d, int64_t n, int *cap, int *slot_words) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int64_t want = (n + GROUP_NT - 1) / GROUP_NT;
-    const int G = (int)(want < sms ? want : sms);
+    int G = (int)(want < sms ? want : sms);
+    if (G > 160) G = 160;   // warp 0 polls five slots per lane
     const int64_t npmax = (n + G - 1) / G;
     if (npmax > (int64_t)RES_PPT * GROUP_NT) return 0;
     const int64_t c = npmax > GROUP_NT ? npmax - GROUP_NT : 1;
