@@ -114,17 +114,46 @@ __device__ __forceinline__ void dist4(const T *__restrict__ blk, int d, const T 
     acc[3] = a3;
 }
 
+// The blocks of CTA r (of G, W warps each) over [b0, b1] are
+// b(i) = b0 + r W + i % W + (i / W) G W for i = 0, 1, ... (increasing in i).
+// Within a step the CTA's warps take i from a counter in shared memory (ctr;
+// the next index is claimed while the current block is processed), so a warp
+// whose loads came back sooner takes more blocks and the CTA's share is done
+// when its blocks are, not when its slowest warp's fixed list is.  A block's
+// minima stay with the CTA, which orders every step's accesses with its
+// barriers.  ctr null: the fixed assignment i = warp + j W.
+__device__ __forceinline__ int64_t cta_block(int64_t b0, int r, int G, int W, int i) {
+    return b0 + (int64_t)r * W + (i % W) + (int64_t)(i / W) * G * W;
+}
+__device__ __forceinline__ int claim_block(int *ctr, int lane) {
+    int v = 0;
+    if (lane == 0) v = atomicAdd(ctr, 1);
+    return __shfl_sync(0xFFFFFFFFu, v, 0);
+}
+// Number of blocks of CTA r.
+__device__ __forceinline__ int cta_blocks(int64_t b0, int64_t b1, int r, int G, int W) {
+    const int64_t rel = b1 - b0 - (int64_t)r * W;
+    if (rel < 0) return 0;
+    const int64_t GW = (int64_t)G * W;
+    const int64_t rem = rel % GW;
+    return (int)((rel / GW) * W + (rem + 1 < W ? rem + 1 : W));
+}
+
 // One step's sweep of this CTA's share (rank r of G) of [lo, lo + n).
 template <typename T, int DC, int NT>
 __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__restrict__ mind,
                                           int64_t lo, int64_t n, int d, const T *cs, bool first_step,
-                                          int r, int G) {
+                                          int r, int G, int *ctr) {
     constexpr int W = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t hi = lo + n;
-    const int64_t b1 = (hi - 1) / BLK;
+    const int64_t b0 = lo / BLK, b1 = (hi - 1) / BLK;
     uint64_t best = 0;
-    for (int64_t b = lo / BLK + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) {
+    int nxt = ctr ? claim_block(ctr, lane) : warp;
+    for (;;) {
+        const int64_t b = cta_block(b0, r, G, W, nxt);
+        if (b > b1) break;
+        nxt = ctr ? claim_block(ctr, lane) : nxt + W;
         const int64_t g0 = b * BLK + lane * 4;
         const bool full = g0 >= lo && g0 + 3 < hi;
         uint4 *mp = reinterpret_cast<uint4 *>(mind + b * BLK) + lane;
@@ -208,6 +237,7 @@ struct Shared {
     uint64_t red[32];
     uint64_t key;
     int abort;
+    int ctr[2];   // block counters of even and odd steps
 };
 
 // All k steps of one instance by this CTA (rank r of a group of G).
@@ -220,7 +250,10 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
     const T *pk = (const T *)I.pk;
     if (warp == 0) {
         for (int j = lane; j < d; j += 32) cs[j] = pk[pk_index(I.lo + I.first, j, d)];
-        if (lane == 0) sh.abort = 0;
+        if (lane == 0) {
+            sh.abort = 0;
+            sh.ctr[0] = sh.ctr[1] = 0;
+        }
     }
     if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
     __syncthreads();
@@ -228,10 +261,11 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
     int it;
     uint64_t K = 0;
     for (it = 0; it < I.k; ++it) {
-        uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G);
+        uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G, &sh.ctr[it & 1]);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
+        if (tid == 0) sh.ctr[(it + 1) & 1] = 0;   // the next step's counter (last used a step ago)
         if (warp == 0) {
             uint64_t v = lane < W ? sh.red[lane] : 0;
             v = warp_max_u64(v);
@@ -317,7 +351,11 @@ struct Cand {
 };
 constexpr int LP_CAP = 128;   // candidates per warp
 
+constexpr int LP_OWN_MAX = 1024;   // CTA blocks whose claiming warp is recorded (dynamic claims)
+
 struct ShLP {
+    uint8_t owner[LP_OWN_MAX];   // warp that claimed each of the CTA's blocks this step
+    int ctr[2];                  // block counters of even and odd steps
     uint64_t red[32];
     uint64_t key;
     unsigned Lcta;     // largest positive lower bound L published by a warp this step (float bits)
@@ -514,6 +552,10 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
 
     for (int j = tid; j < dp; j += NT) scs[j] = (KIND == KC_SWEEP_FP8) ? I.scale[j] : 1.f;
     __syncthreads();
+    // claims are dynamic (see cta_block) when the overflow rescan can find
+    // the claiming warp of every block of the CTA
+    const int64_t b0 = lo / BLK;
+    const bool dynb = cta_blocks(b0, b1, r, G, W) <= LP_OWN_MAX;
     if (warp == 0) {
         float ec;
         lp_load_center<KIND>(I, I.first, d, ng, cl, scs, 0, lane, &ec);
@@ -521,6 +563,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             sh.ecmax = ec;
             sh.abort = 0;
             sh.Lcta = 0u;
+            sh.ctr[0] = sh.ctr[1] = 0;
         }
     }
     if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
@@ -535,7 +578,14 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
         float Lrun = -INFINITY;
         int cnt = 0;
         bool ovf = false;
-        for (int64_t b = lo / BLK + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) {
+        int *ctr = dynb ? &sh.ctr[it & 1] : nullptr;
+        int nxt = ctr ? claim_block(ctr, lane) : warp;
+        for (;;) {
+            const int bi = nxt;
+            const int64_t b = cta_block(b0, r, G, W, bi);
+            if (b > b1) break;
+            nxt = ctr ? claim_block(ctr, lane) : bi + W;
+            if (ctr && lane == 0) sh.owner[bi] = (uint8_t)warp;
             const int64_t g0 = b * BLK + lane * 4;
             const uint4 *src = reinterpret_cast<const uint4 *>(I.lp + b * ng * BLK) + lane;
             float a[4] = {0.f, 0.f, 0.f, 0.f};
@@ -655,6 +705,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             sh.cnt[warp] = cnt;
         }
         __syncthreads();
+        if (tid == 0) sh.ctr[(it + 1) & 1] = 0;   // the next step's counter (last used a step ago)
         if (clk && tid == 0) pc_mark(sh.pc, 0);
         float T = -INFINITY;
         for (int w = 0; w < W; ++w) T = fmaxf(T, sh.Lw[w]);
@@ -696,7 +747,10 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             if (lane == 0) atomicAdd(&g_counters[1], 1ull);
             int c2 = 0;
             __syncwarp();
-            for (int64_t b = lo / BLK + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) {
+            for (int bi = dynb ? 0 : warp;; bi += dynb ? 1 : W) {
+                const int64_t b = cta_block(b0, r, G, W, bi);
+                if (b > b1) break;
+                if (dynb && sh.owner[bi] != warp) continue;
                 const float delta = __fadd_ru(I.eblk[b], ecmax);
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) {
