@@ -130,14 +130,6 @@ __device__ __forceinline__ int claim_block(int *ctr, int lane) {
     if (lane == 0) v = atomicAdd(ctr, 1);
     return __shfl_sync(0xFFFFFFFFu, v, 0);
 }
-// Number of blocks of CTA r.
-__device__ __forceinline__ int cta_blocks(int64_t b0, int64_t b1, int r, int G, int W) {
-    const int64_t rel = b1 - b0 - (int64_t)r * W;
-    if (rel < 0) return 0;
-    const int64_t GW = (int64_t)G * W;
-    const int64_t rem = rel % GW;
-    return (int)((rel / GW) * W + (rem + 1 < W ? rem + 1 : W));
-}
 
 // One step's sweep of this CTA's share (rank r of G) of [lo, lo + n).
 template <typename T, int DC, int NT>
@@ -261,7 +253,12 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
     int it;
     uint64_t K = 0;
     for (it = 0; it < I.k; ++it) {
-        uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G, &sh.ctr[it & 1]);
+        // claimed blocks in the 1024-thread group CTAs (measured: GON on
+        // 8M x 64, k = 1024, 313 -> 308 ms); the fixed assignment in the
+        // 256-thread queue CTAs (MRG round 1 on 10M x 16 was 5% slower with
+        // claims)
+        uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G,
+                                         NT == GROUP_NT ? &sh.ctr[it & 1] : nullptr);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
@@ -351,11 +348,7 @@ struct Cand {
 };
 constexpr int LP_CAP = 128;   // candidates per warp
 
-constexpr int LP_OWN_MAX = 1024;   // CTA blocks whose claiming warp is recorded (dynamic claims)
-
 struct ShLP {
-    uint8_t owner[LP_OWN_MAX];   // warp that claimed each of the CTA's blocks this step
-    int ctr[2];                  // block counters of even and odd steps
     uint64_t red[32];
     uint64_t key;
     unsigned Lcta;     // largest positive lower bound L published by a warp this step (float bits)
@@ -552,10 +545,10 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
 
     for (int j = tid; j < dp; j += NT) scs[j] = (KIND == KC_SWEEP_FP8) ? I.scale[j] : 1.f;
     __syncthreads();
-    // claims are dynamic (see cta_block) when the overflow rescan can find
-    // the claiming warp of every block of the CTA
+    // fixed assignment of the CTA's blocks to its warps (claiming them from a
+    // counter, as the FP32 sweep does, measured slower here: 183 -> 188 ms
+    // per solve on 8M x 64, k = 1024)
     const int64_t b0 = lo / BLK;
-    const bool dynb = cta_blocks(b0, b1, r, G, W) <= LP_OWN_MAX;
     if (warp == 0) {
         float ec;
         lp_load_center<KIND>(I, I.first, d, ng, cl, scs, 0, lane, &ec);
@@ -563,7 +556,6 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             sh.ecmax = ec;
             sh.abort = 0;
             sh.Lcta = 0u;
-            sh.ctr[0] = sh.ctr[1] = 0;
         }
     }
     if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
@@ -578,14 +570,9 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
         float Lrun = -INFINITY;
         int cnt = 0;
         bool ovf = false;
-        int *ctr = dynb ? &sh.ctr[it & 1] : nullptr;
-        int nxt = ctr ? claim_block(ctr, lane) : warp;
-        for (;;) {
-            const int bi = nxt;
+        for (int bi = warp;; bi += W) {
             const int64_t b = cta_block(b0, r, G, W, bi);
             if (b > b1) break;
-            nxt = ctr ? claim_block(ctr, lane) : bi + W;
-            if (ctr && lane == 0) sh.owner[bi] = (uint8_t)warp;
             const int64_t g0 = b * BLK + lane * 4;
             const uint4 *src = reinterpret_cast<const uint4 *>(I.lp + b * ng * BLK) + lane;
             float a[4] = {0.f, 0.f, 0.f, 0.f};
@@ -705,7 +692,6 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             sh.cnt[warp] = cnt;
         }
         __syncthreads();
-        if (tid == 0) sh.ctr[(it + 1) & 1] = 0;   // the next step's counter (last used a step ago)
         if (clk && tid == 0) pc_mark(sh.pc, 0);
         float T = -INFINITY;
         for (int w = 0; w < W; ++w) T = fmaxf(T, sh.Lw[w]);
@@ -747,10 +733,9 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             if (lane == 0) atomicAdd(&g_counters[1], 1ull);
             int c2 = 0;
             __syncwarp();
-            for (int bi = dynb ? 0 : warp;; bi += dynb ? 1 : W) {
+            for (int bi = warp;; bi += W) {
                 const int64_t b = cta_block(b0, r, G, W, bi);
                 if (b > b1) break;
-                if (dynb && sh.owner[bi] != warp) continue;
                 const float delta = __fadd_ru(I.eblk[b], ecmax);
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) {

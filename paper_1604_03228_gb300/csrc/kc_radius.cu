@@ -290,8 +290,13 @@ cudaError_t dispatch_min(RadiusArgs &a, cudaStream_t s, int sms) {
     const int64_t groups = (nblocks(a.n) + RAD_W - 1) / RAD_W;
     const int64_t cap = (int64_t)sms * 8;
     const int grid = (int)(groups < cap ? groups : cap);
+    // the row stride DR is the smallest specialisation >= d: padded
+    // coordinates cost a subtract and a multiply-add each for every center
+    if (a.d <= 2) return run_min<T, 2>(a, s, grid);
+    if (a.d <= 3) return run_min<T, 3>(a, s, grid);
     if (a.d <= 4) return run_min<T, 4>(a, s, grid);
     if (a.d <= 8) return run_min<T, 8>(a, s, grid);
+    if (a.d <= 10) return run_min<T, 10>(a, s, grid);
     if (a.d <= 16) return run_min<T, 16>(a, s, grid);
     const int64_t g2 = (a.n + RAD_NT - 1) / RAD_NT;
     const int grid2 = (int)(g2 < cap ? g2 : cap);
