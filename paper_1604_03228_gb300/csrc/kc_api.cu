@@ -569,6 +569,10 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     int res_cap = 0, res_sw = 0;
     const int res_grid = (!lp && !pin_pts) ? gon_resident_plan(c.o.dtype, d, n, &res_cap, &res_sw) : 0;
     const int grid = res_grid ? res_grid : choose_gon_grid(c.o.dtype, d, n, lp);
+    // the FP32 streaming group shares the last blocks of every step between its
+    // CTAs (KC_GON_TAIL=0 keeps every block with its CTA)
+    bool use_tail = !lp && !res_grid && grid > 1;
+    if (const char *env = getenv("KC_GON_TAIL")) use_tail = use_tail && atoi(env) != 0;
     const int64_t nb = nblocks(n);
     const size_t esz = 4;
     LPBufs LB;
@@ -585,6 +589,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         // CTAs' lower bounds too
         uint64_t *slots = cv.take<uint64_t>(res_grid ? (size_t)keff * grid * res_sw
                                                       : (size_t)slot_words(keff, grid, lp != 0));
+        int *tail = use_tail ? cv.take<int>((size_t)keff) : nullptr;
         *zero_bytes = cv.off;
         *staging = (dev_pts || pin_pts) ? nullptr : cv.take<char>((size_t)n * d * esz);
         void *pk = res_grid ? nullptr : cv.take<char>((size_t)nb * BLK * d * esz);
@@ -599,6 +604,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         ecmax = lp ? cv.take<float>(1) : nullptr;
         gon_single(g, pk, c.o.dtype, n, d, keff, first, mind, slots, *cen_dev, *kout_dev,
                    (uint64_t *)key32, range2, grid);
+        g.single.tail = tail;
         if (lp) {
             attach_lp(g.single, LB, lp, cenT, keff, ecmax);
             g.lp_kind = lp;

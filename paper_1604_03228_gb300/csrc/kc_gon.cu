@@ -131,28 +131,57 @@ __device__ __forceinline__ int claim_block(int *ctr, int lane) {
     return __shfl_sync(0xFFFFFFFFu, v, 0);
 }
 
+// First block of the group's shared tail: with a tail counter, the CTAs own
+// the blocks below it (7/8 of the range, whole rounds of G W blocks) and any
+// warp of the group claims the rest, two blocks at a time, from a per-step
+// counter in global memory, so the group's step ends when its blocks are done
+// rather than when the CTA that got the least bandwidth is.  Blocks of the
+// tail change CTA from step to step: their minima are read past L1 and every
+// step's writes are fenced before the step's slot is published (gon_solve).
+__device__ __forceinline__ int64_t tail_start(int64_t b0, int64_t b1, int G, int W, bool tail) {
+    if (!tail) return b1 + 1;
+    const int64_t GW = (int64_t)G * W;
+    const int64_t rounds = (b1 - b0 + 1) * 7 / 8 / GW;
+    return rounds >= 2 ? b0 + rounds * GW : b1 + 1;
+}
+
 // One step's sweep of this CTA's share (rank r of G) of [lo, lo + n).
 template <typename T, int DC, int NT>
 __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__restrict__ mind,
                                           int64_t lo, int64_t n, int d, const T *cs, bool first_step,
-                                          int r, int G, int *ctr) {
+                                          int r, int G, int *ctr, int *gtail) {
     constexpr int W = NT / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t hi = lo + n;
     const int64_t b0 = lo / BLK, b1 = (hi - 1) / BLK;
+    const int64_t ts = tail_start(b0, b1, G, W, gtail != nullptr);
     uint64_t best = 0;
     int nxt = ctr ? claim_block(ctr, lane) : warp;
+    int64_t pend = -1;   // second block of a claimed tail pair
     for (;;) {
-        const int64_t b = cta_block(b0, r, G, W, nxt);
-        if (b > b1) break;
-        nxt = ctr ? claim_block(ctr, lane) : nxt + W;
+        int64_t b = cta_block(b0, r, G, W, nxt);
+        if (b < ts) {
+            nxt = ctr ? claim_block(ctr, lane) : nxt + W;
+        } else if (ts > b1) {
+            break;
+        } else if (pend >= 0) {
+            b = pend;
+            pend = -1;
+        } else {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(gtail, 2);
+            t = __shfl_sync(0xFFFFFFFFu, t, 0);
+            b = ts + t;
+            if (b > b1) break;
+            if (b + 1 <= b1) pend = b + 1;
+        }
         const int64_t g0 = b * BLK + lane * 4;
         const bool full = g0 >= lo && g0 + 3 < hi;
         uint4 *mp = reinterpret_cast<uint4 *>(mind + b * BLK) + lane;
         uint32_t o[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
         if (!first_step) {
             if (full) {
-                const uint4 ov = *mp;
+                const uint4 ov = __ldcg(mp);   // L2: tail blocks move between CTAs
                 o[0] = ov.x;
                 o[1] = ov.y;
                 o[2] = ov.z;
@@ -160,7 +189,7 @@ __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (g0 + q >= lo && g0 + q < hi) o[q] = mind[g0 + q];
+                    if (g0 + q >= lo && g0 + q < hi) o[q] = __ldcg(mind + g0 + q);
             }
         }
         typename AccOf<T>::type acc[4];
@@ -258,7 +287,8 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
         // 256-thread queue CTAs (MRG round 1 on 10M x 16 was 5% slower with
         // claims)
         uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G,
-                                         NT == GROUP_NT ? &sh.ctr[it & 1] : nullptr);
+                                         NT == GROUP_NT ? &sh.ctr[it & 1] : nullptr,
+                                         (G > 1 && I.tail) ? I.tail + it : nullptr);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
@@ -271,8 +301,14 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
             if (G > 1) {
                 const int64_t row = (int64_t)it * slot_stride(G);
                 const bool held = withhold == it + 1 && r == G - 1;
+                // with a shared tail, the step's minima (written by this
+                // CTA's threads before the barrier) are made visible to the
+                // group before the slot is, and the other CTAs' after it is
+                // seen (the release / acquire pattern of a grid barrier)
+                if (I.tail) __threadfence();
                 if (lane == 0 && !held) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
                 g = poll_slots(I.slots + row, G, timeout, st, it, &ab);
+                if (I.tail) __threadfence();
             }
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {
                 const int64_t c = key_idx(g);

@@ -182,6 +182,9 @@ cudaError_t launch_range_check(const int32_t *range2, int d, DevStatus *st, cuda
 // centers written out are base + local index (or map[local] when map is set).
 struct GonInst {
     const void *pk;          // packed points of this instance (block aligned)
+    // per-step counters of the group's shared tail of blocks ([k], zeroed),
+    // or nullptr: every block stays with its CTA (FP32 group kernels only)
+    int *tail;
     // FP32 rows of the instance's points, row of local index 0 (row-major,
     // d floats per row), or nullptr: the exact rechecks of the mixed-precision
     // sweep then read the packed copy (one point's coordinates 512 bytes
@@ -279,6 +282,7 @@ inline void gon_single(GonArgs &g, const void *pk, int dtype, int64_t n, int d, 
                        uint64_t *final_key, const int32_t *range2, int grid) {
     GonInst &I = g.single;
     I.pk = pk;
+    I.tail = nullptr;
     I.rm = nullptr;
     I.mind = mind;
     I.slots = slots;

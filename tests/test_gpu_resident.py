@@ -2,7 +2,8 @@
 k steps, running minima in registers, candidate coordinates carried in the
 exchange slots) against the oracle and against the streaming kernel
 (KC_GON_RESIDENT=0), on sizes that use registers only, registers plus shared
-memory, and the 1M x 10 workload that fills shared memory.
+memory, and the 1M x 10 workload that fills shared memory; and the streaming
+kernel's shared tail of blocks (KC_GON_TAIL=0 turns it off) on 3M points.
 """
 import numpy as np
 import pytest
@@ -67,3 +68,17 @@ def test_resident_input_checks(kc):
     assert e.value.status == kc.KC_ERR_RANGE
     ok = kc.kc_gonzalez(_dev(pts), 10)   # the status was cleared
     assert ok.k_out == 10
+
+
+@pytest.mark.parametrize("d", [8, 17])
+def test_streaming_shared_tail_equals_oracle(kc, d, monkeypatch):
+    # 3M points: too many to stay on chip, and enough blocks per warp that the
+    # group shares the last blocks of every step between its CTAs
+    pts = I.gauss_mixture(3_000_000, d, 910 + d, 30, 0.7, -10.0, 10.0)
+    x = _dev(pts)
+    a = kc.kc_gonzalez(x, 64)
+    monkeypatch.setenv("KC_GON_TAIL", "0")
+    b = kc.kc_gonzalez(x, 64)
+    assert a.centers.cpu().tolist() == b.centers.cpu().tolist() and a.radius == b.radius
+    ref = O.gonzalez(pts, 64, mode="f32")
+    assert a.centers.cpu().numpy().tolist() == ref.centers.tolist() and a.radius == ref.radius
