@@ -32,8 +32,18 @@ namespace kc {
 
 namespace {
 
-// Largest |x_j| per column j: one warp covers 32 points of one (block, j).
+// Largest |x_j| per column j: one warp covers 32 points of one (block, j);
+// the CTA gathers its warps' maxima per column in shared memory (up to
+// CM_SMEM columns, else straight in global memory) and adds them to the
+// global maxima once, so the global words see one atomic per CTA and column
+// instead of one per 32 values.
+constexpr int CM_SMEM = 1024;
 __global__ void colmax_kernel(const float *__restrict__ pk, int64_t n, int d, unsigned *__restrict__ colmax) {
+    __shared__ unsigned cm[CM_SMEM];
+    const bool local = d <= CM_SMEM;
+    if (local)
+        for (int j = threadIdx.x; j < d; j += blockDim.x) cm[j] = 0u;
+    __syncthreads();
     const int64_t total = nblocks(n) * (int64_t)d * BLK;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = e / ((int64_t)d * BLK);
@@ -42,8 +52,12 @@ __global__ void colmax_kernel(const float *__restrict__ pk, int64_t n, int d, un
         float v = (b * BLK + i < n) ? fabsf(pk[e]) : 0.f;
 #pragma unroll
         for (int o = 16; o; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xFFFFFFFFu, v, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(&colmax[j], __float_as_uint(v));
+        if ((threadIdx.x & 31) == 0) atomicMax(local ? &cm[j] : &colmax[j], __float_as_uint(v));
     }
+    __syncthreads();
+    if (local)
+        for (int j = threadIdx.x; j < d; j += blockDim.x)
+            if (cm[j]) atomicMax(&colmax[j], cm[j]);
 }
 
 __device__ __forceinline__ float fp8_scale(const unsigned *colmax, int j) {
