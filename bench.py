@@ -381,6 +381,10 @@ def run_gpu(args):
     assert kc.kc_sync(s) == kc.KC_OK
     ref_centers, ref_rad = cen.cpu().tolist(), float(rad.item())
     assert int(kout.item()) == k
+    # the result's FP32 evaluation against FP64: the canonical FP32 covering
+    # radius beside the returned FP64 one (the same for every sweep precision)
+    r32 = kc.kc_last_fp32_radius(s)
+    fp64_error = {"radius_fp64": ref_rad, "radius_fp32": r32, "rel_err": abs(r32 - ref_rad) / ref_rad}
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -476,7 +480,8 @@ def run_gpu(args):
                              "frac": achieved / peak, "traffic": traffic, "kernel": "gon_group_kernel",
                              "peak_kind": peak_kind, "avg_ms": gon_avg, "alg_bytes_per_launch": alg_bytes,
                              "alg_bytes_rule": "k n (4 d + 4): each step reads every point and its running minimum"},
-                "mixed": mixed, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "mixed": mixed, "fp64_error": fp64_error, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks,
                 "step_share_ms": {k_: v / args.steps for k_, v in shares.items()}}
         print(json.dumps(line), flush=True)
     if world > 1:

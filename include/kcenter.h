@@ -320,6 +320,18 @@ kc_status kc_gonzalez_noalloc(const void *pts, int64_t n, int32_t d, int32_t k, 
  */
 kc_status kc_sync(void *stream);
 
+/*
+ * kc_last_fp32_radius -- the error of a result against FP64, for the last
+ * kc_gonzalez, kc_mrg, kc_eim or kc_radius call on `stream`: *radius32 is the
+ * square root of the largest canonical FP32 squared distance from a point to
+ * its nearest chosen center (the values every selection was decided on; exact
+ * for int32 points), in double.  Beside the call's returned radius (the same
+ * quantity in FP64) it gives the FP32 evaluation's error at that result.
+ * Waits for the stream.  KC_ERR_ARG if no such call ran on the stream since
+ * kc_release; the value is undefined if that call failed.
+ */
+kc_status kc_last_fp32_radius(void *stream, double *radius32);
+
 /* kc_last_error -- text describing the last failure on this thread. */
 const char *kc_last_error(void);
 

@@ -92,10 +92,30 @@ def load(path: str | None = None):
     L.kc_launch_count.restype = i64
     L.kc_counters.restype = i32
     L.kc_counters.argtypes = [vp, i32]
+    L.kc_last_fp32_radius.restype = ct.c_int
+    L.kc_last_fp32_radius.argtypes = [vp, ct.POINTER(ct.c_double)]
     L.kc_read_sweep.restype = ct.c_int
     L.kc_read_sweep.argtypes = [vp, ct.c_size_t, i32, vp, vp]
     _LIB = L
     return L
+
+
+def kc_last_fp32_radius(stream=None) -> float:
+    """The canonical FP32 covering radius of the last solve or radius call
+    on `stream` (default: torch's current stream): with the FP64 radius that
+    call returned, the result's FP32 error against FP64."""
+    L = load()
+    h = None
+    if stream is not None:
+        h = int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+    else:
+        try:
+            h = int(_torch().cuda.current_stream().cuda_stream)
+        except Exception:
+            h = None
+    out = ct.c_double()
+    _check(L, L.kc_last_fp32_radius(h, ct.byref(out)))
+    return out.value
 
 
 def kc_read_sweep(buf, reps: int, sink, *, stream=None) -> None:

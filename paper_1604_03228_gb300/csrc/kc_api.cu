@@ -111,6 +111,10 @@ struct Arena {
     size_t pinned_bytes = 0;
     cudaEvent_t pinned_ev = nullptr;
     bool pinned_busy = false;
+    // the argmax key (value bits: the largest canonical FP32 minimum) of the
+    // last solve or radius on this stream, for kc_last_fp32_radius
+    const unsigned long long *last_key32 = nullptr;
+    int last_dtype = KC_F32;
 };
 
 // Copy `bytes` of host data to device memory `dst` in stream order through
@@ -523,6 +527,7 @@ void kc_release(void) {
     for (auto &kv : g_arenas) {
         cudaSetDevice(kv.first.first);
         Arena *a = kv.second;
+        a->last_key32 = nullptr;
         if (a->dev) cudaFree(a->dev);
         if (a->status) cudaFree(a->status);
         if (a->host_status) cudaFreeHost(a->host_status);
@@ -533,6 +538,28 @@ void kc_release(void) {
     }
     g_arenas.clear();
     cudaSetDevice(cur);
+}
+
+kc_status kc_last_fp32_radius(void *stream, double *radius32) {
+    g_err.clear();
+    if (!radius32) return fail(KC_ERR_ARG, "null pointer argument");
+    Arena *a = nullptr;
+    kc_status r = arena_for((cudaStream_t)stream, &a);
+    if (r != KC_OK) return r;
+    if (!a->last_key32) return fail(KC_ERR_ARG, "no solve or radius has run on this stream");
+    unsigned long long key = 0;
+    KC_CUDA(cudaMemcpyAsync(&key, a->last_key32, sizeof key, cudaMemcpyDeviceToHost, (cudaStream_t)stream),
+            "key read-back");
+    KC_CUDA(cudaStreamSynchronize((cudaStream_t)stream), "cudaStreamSynchronize");
+    const uint32_t v = (uint32_t)(key >> 32);
+    if (a->last_dtype == KC_I32) {
+        *radius32 = std::sqrt((double)v);
+    } else {
+        float f;
+        memcpy(&f, &v, sizeof f);
+        *radius32 = std::sqrt((double)f);
+    }
+    return KC_OK;
 }
 
 kc_status kc_sync(void *stream) {
@@ -650,6 +677,8 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     ra.st = c.arena->status;
     g.timeout_cycles = timeout_cycles(c.o);
     g.withhold = (c.o.flags & KC_TEST_WITHHOLD) ? 1 : 0;
+    c.arena->last_key32 = ra.key32;
+    c.arena->last_dtype = c.o.dtype;
 
     KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
     const void *src;
@@ -767,6 +796,8 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
     ra.argmax_out = arg_dev;
     ra.st = c.arena->status;
     ra.have_mind = false;
+    c.arena->last_key32 = ra.key32;
+    c.arena->last_dtype = c.o.dtype;
 
     KC_CUDA(cudaMemsetAsync(c.arena->dev, 0, zero_bytes, c.s), "scratch clear");
     const void *src;
@@ -988,6 +1019,8 @@ kc_status mrg_run(const void *pts, int64_t n, int32_t d, int32_t k, int32_t m, c
     Carve cv(c.arena->dev);
     layout(cv);
     DevStatus *st = c.arena->status;
+    c.arena->last_key32 = Lo.key32;
+    c.arena->last_dtype = c.o.dtype;
 
     // Round-1 descriptors (host-built, uploaded once).
     std::vector<GonInst> h1((size_t)m);
@@ -1358,6 +1391,8 @@ kc_status kc_eim(const void *pts, int64_t n, int32_t d, int32_t k, double eps, i
     Carve cv(c.arena->dev);
     layout(cv);
     DevStatus *st = c.arena->status;
+    c.arena->last_key32 = Lo.key32;
+    c.arena->last_dtype = c.o.dtype;
     auto read_u64 = [&](const unsigned long long *p, unsigned long long *out) -> kc_status {
         KC_CUDA(cudaMemcpyAsync(out, p, sizeof *out, cudaMemcpyDeviceToHost, c.s), "count read-back");
         KC_CUDA(cudaStreamSynchronize(c.s), "cudaStreamSynchronize");

@@ -339,3 +339,26 @@ def test_zz_fp64_divergence_is_rare():
         pytest.skip("too few float GON checks ran in this session")
     print(f"FP64 selection parted from FP32 in {_TALLY['diverged']} of {_TALLY['calls']} checks")
     assert _TALLY["diverged"] <= 0.1 * _TALLY["calls"]
+
+
+def test_fp32_radius_against_fp64_per_result(kc):
+    """kc_last_fp32_radius: the canonical FP32 covering radius of the last
+    result, equal to the oracle's FP32 value; its gap to the returned FP64
+    radius is within the FP32 evaluation's error bound."""
+    pts = I.gauss_mixture(60_000, 12, 71, 20, 1.0, -30, 30)
+    x = _dev(pts)
+    g = kc.kc_gonzalez(x, 50)
+    r32 = kc.kc_last_fp32_radius()
+    ref = O.gonzalez(pts, 50, mode="f32")
+    assert r32 == math.sqrt(ref.radius2)
+    gamma = 14 * 2.0 ** -24 / (1 - 14 * 2.0 ** -24)
+    assert abs(r32 - g.radius) <= gamma * g.radius
+    m = kc.kc_mrg(x, 30, 8)
+    mref = O.mrg(pts, 30, I.even_offsets(60_000, 8), mode="f32")
+    assert kc.kc_last_fp32_radius() == math.sqrt(mref.radius2) and m.radius == mref.radius
+    C = g.centers[:17]
+    rr = kc.kc_radius(x, C)
+    assert kc.kc_last_fp32_radius() == math.sqrt(O.radius(pts, C.cpu().numpy(), mode="f32")[2])
+    ipts = I.gon_int_10k().points
+    gi = kc.kc_gonzalez(_dev(ipts), 10)
+    assert kc.kc_last_fp32_radius() == gi.radius
