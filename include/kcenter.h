@@ -80,7 +80,10 @@ typedef enum {
     KC_ERR_OOM = 3,        /* device scratch allocation failed */
     KC_ERR_TIMEOUT = 4,    /* a device spin-wait ran out of its time budget */
     KC_ERR_RANGE = 5,      /* int32 squared distances would not fit 32 bits */
-    KC_ERR_NONFINITE = 6   /* a float coordinate is NaN or infinite */
+    KC_ERR_NONFINITE = 6,  /* a float coordinate is NaN or infinite */
+    KC_ERR_BOUNDS = 7      /* checked build only (libkcenter_checks.so, compiled with
+                              -DKC_CHECKS): a kernel found an index outside the
+                              buffer it was about to address and skipped the access */
 } kc_status;
 
 typedef enum { KC_F32 = 0, KC_I32 = 1 } kc_dtype;
@@ -109,6 +112,11 @@ typedef enum { KC_SWEEP_F32 = 0, KC_SWEEP_BF16 = 1, KC_SWEEP_FP8 = 2, KC_SWEEP_F
  * without faulting or hanging the GPU; has no effect when the launch has a
  * single CTA (no exchange). */
 #define KC_TEST_WITHHOLD 0x80000000u
+/* Testing only, checked build only (kc_gonzalez; the regular build rejects
+ * it with KC_ERR_ARG): the first winner's index is replaced by one past the
+ * last point, so that the kernel's own check records KC_ERR_BOUNDS instead
+ * of reading past the points.  Selects the streaming kernel. */
+#define KC_TEST_BAD_INDEX 0x40000000u
 
 typedef struct {
     int32_t dtype;          /* kc_dtype of the points */

@@ -17,13 +17,14 @@ import numpy as np
 
 from . import build as _build
 
-KC_OK, KC_ERR_ARG, KC_ERR_CUDA, KC_ERR_OOM, KC_ERR_TIMEOUT, KC_ERR_RANGE, KC_ERR_NONFINITE = range(7)
+KC_OK, KC_ERR_ARG, KC_ERR_CUDA, KC_ERR_OOM, KC_ERR_TIMEOUT, KC_ERR_RANGE, KC_ERR_NONFINITE, KC_ERR_BOUNDS = range(8)
 KC_F32, KC_I32 = 0, 1
 KC_ASYNC = 1
 KC_AUTOTUNE = 2
 KC_TEST_WITHHOLD = 0x80000000
+KC_TEST_BAD_INDEX = 0x40000000
 STATUS_NAMES = {0: "KC_OK", 1: "KC_ERR_ARG", 2: "KC_ERR_CUDA", 3: "KC_ERR_OOM", 4: "KC_ERR_TIMEOUT",
-                5: "KC_ERR_RANGE", 6: "KC_ERR_NONFINITE"}
+                5: "KC_ERR_RANGE", 6: "KC_ERR_NONFINITE", 7: "KC_ERR_BOUNDS"}
 
 
 class KCError(RuntimeError):
@@ -46,11 +47,13 @@ _LIB = None
 
 
 def load(path: str | None = None):
-    """Build (if stale) and load libkcenter.so; raises if that fails."""
+    """Build (if stale) and load libkcenter.so (or the library that the
+    KC_LIBRARY environment variable names, e.g. the checked build); raises if
+    that fails."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = path or _build.build()
+    path = path or os.environ.get("KC_LIBRARY") or _build.build()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library missing: {path}")
     L = ct.CDLL(path)

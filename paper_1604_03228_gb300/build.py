@@ -2,7 +2,9 @@
 
 Each .cu file compiles to its own object in parallel, then nvcc links the
 shared library with the static CUDA runtime.  Outputs land in
-paper_1604_03228_gb300/_build/ (git-ignored).
+paper_1604_03228_gb300/_build/ (git-ignored).  build(checks=True) makes the
+checked build instead (-DKC_CHECKS: kernels test the indices they use and
+report KC_ERR_BOUNDS), libkcenter_checks.so in _build/checks/.
 """
 from __future__ import annotations
 
@@ -17,6 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkcenter.so")
+CHECKS_DIR = os.path.join(OUT_DIR, "checks")
+CHECKS_LIB = os.path.join(CHECKS_DIR, "libkcenter_checks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"] + ARCH
@@ -38,22 +42,23 @@ def _deps():
                                                                   os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=None, checks: bool = False) -> str:
+    lib, out_dir = (CHECKS_LIB, CHECKS_DIR) if checks else (LIB, OUT_DIR)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + list(extra or [])
+    flags = NVCC_FLAGS + list(extra or []) + (["-DKC_CHECKS"] if checks else [])
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [nvcc, "-c", src, "-o", obj] + flags
         if verbose:
             print(" ".join(cmd), flush=True)
@@ -66,15 +71,15 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-lcuda"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None, checks="--checks" in sys.argv))

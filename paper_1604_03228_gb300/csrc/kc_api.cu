@@ -241,6 +241,14 @@ const char *where_name(int w) {
         case 2: return "int32 range check";
         case 3: return "GON step exchange";
         case 4: return "center index check";
+        case KC_AT_CENTER_LOAD: return "GON winner index (checked build)";
+        case KC_AT_RESIDENT_SMEM: return "resident shared-memory column (checked build)";
+        case KC_AT_CANDIDATE: return "candidate buffer (checked build)";
+        case KC_AT_RECHECK: return "exact recheck index (checked build)";
+        case KC_AT_CENTER_COPY: return "center copy slot (checked build)";
+        case KC_AT_EIM_INDEX: return "EIM point index (checked build)";
+        case KC_AT_RADIUS_LIST: return "radius recheck list (checked build)";
+        case KC_AT_SLOT: return "exchange slot (checked build)";
         default: return "device";
     }
 }
@@ -259,6 +267,8 @@ kc_status status_text(const DevStatus &d) {
                         (long long)d.info);
         case KC_ERR_ARG:
             return fail(KC_ERR_ARG, "%s failed (item %lld)", where_name(d.where), (long long)d.info);
+        case KC_ERR_BOUNDS:
+            return fail(KC_ERR_BOUNDS, "index %lld outside its buffer at %s", (long long)d.info, where_name(d.where));
         default:
             return fail((kc_status)d.code, "device error %d in %s", d.code, where_name(d.where));
     }
@@ -578,8 +588,13 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     if (k < 1) return fail(KC_ERR_ARG, "k=%d must be >= 1", k);
     if (first < 0 || first >= n) return fail(KC_ERR_ARG, "first=%lld outside [0, n)", (long long)first);
     CallCtx c;
+#ifdef KC_CHECKS
+    kc_status r = begin(opts, c, KC_ASYNC | KC_TEST_WITHHOLD | KC_TEST_BAD_INDEX);
+#else
     kc_status r = begin(opts, c, KC_ASYNC | KC_TEST_WITHHOLD);
+#endif
     if (r != KC_OK) return r;
+    const bool bad_index = (c.o.flags & KC_TEST_BAD_INDEX) != 0;
 
     const bool dev_pts = is_device_ptr(pts, c.dev);
     const void *pin_pts = dev_pts ? nullptr : pinned_device_ptr(pts);   // read in place by the pack
@@ -594,7 +609,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     // points that fit on chip: the resident kernel reads the rows in place
     // (device memory or the staging copy) and keeps them for all k steps
     int res_cap = 0, res_sw = 0;
-    const int res_grid = (!lp && !pin_pts) ? gon_resident_plan(c.o.dtype, d, n, &res_cap, &res_sw) : 0;
+    const int res_grid = (!lp && !pin_pts && !bad_index) ? gon_resident_plan(c.o.dtype, d, n, &res_cap, &res_sw) : 0;
     const int grid = res_grid ? res_grid : choose_gon_grid(c.o.dtype, d, n, lp);
     // the FP32 streaming group shares the last blocks of every step between its
     // CTAs (KC_GON_TAIL=0 keeps every block with its CTA)
@@ -677,6 +692,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     ra.st = c.arena->status;
     g.timeout_cycles = timeout_cycles(c.o);
     g.withhold = (c.o.flags & KC_TEST_WITHHOLD) ? 1 : 0;
+    g.bad_index = bad_index ? 1 : 0;
     c.arena->last_key32 = ra.key32;
     c.arena->last_dtype = c.o.dtype;
 

@@ -274,7 +274,7 @@ struct Shared {
 // All k steps of one instance by this CTA (rank r of a group of G).
 template <typename T, int DC, int NT>
 __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, DevStatus *st,
-                          long long timeout, int withhold = 0) {
+                          long long timeout, int withhold = 0, bool bad_index = false) {
     constexpr int W = NT / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = DC > 0 ? DC : I.d;
@@ -328,9 +328,19 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
                 if (I.tail) __threadfence();
             }
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {
+#ifdef KC_CHECKS
+                // testing hook of the checked build: a winner index one past
+                // the instance, which the check below must catch
+                const int64_t c = (bad_index && it == 0) ? I.n : (int64_t)key_idx(g);
+#else
                 const int64_t c = key_idx(g);
-                for (int j = lane; j < d; j += 32) cs[j] = pk[pk_index(I.lo + c, j, d)];
-                if (r == 0 && lane == 0) I.centers[it + 1] = out_index(I, c);
+#endif
+                if (KC_IN_RANGE(st, c, I.n, KC_AT_CENTER_LOAD)) {
+                    for (int j = lane; j < d; j += 32) cs[j] = pk[pk_index(I.lo + c, j, d)];
+                    if (r == 0 && lane == 0) I.centers[it + 1] = out_index(I, c);
+                } else {
+                    ab = true;
+                }
             }
             if (lane == 0) {
                 sh.key = g;
@@ -508,7 +518,9 @@ __device__ uint32_t memo_min_warp(const float *__restrict__ pk, int64_t gx, int 
 // best key and recheck count.
 template <bool VEC>
 __device__ __forceinline__ void memo_recheck(const GonInst &I, const float *__restrict__ pk, int d, int ncen,
-                                             bool want, uint32_t idx, int lane, uint64_t &best, unsigned &nre) {
+                                             bool want, uint32_t idx, int lane, uint64_t &best, unsigned &nre,
+                                             DevStatus *st) {
+    want = want && KC_IN_RANGE(st, idx, I.n, KC_AT_RECHECK);
     const int64_t gx = I.lo + idx;
     const bool small = want && ncen - (int)I.stamp[gx] <= MEMO_LANE_GAP;
     if (small) {
@@ -732,7 +744,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                             break;
                         }
                     }
-                    if (pred)
+                    if (pred && KC_IN_RANGE(st, cnt + __popc(bal & ((1u << lane) - 1u)), LP_CAP, KC_AT_CANDIDATE))
                         buf[cnt + __popc(bal & ((1u << lane) - 1u))] =
                             Cand{(uint32_t)(g0 + q - lo), lp_upper(hib, delta, opg)};
                     cnt += nq;
@@ -777,7 +789,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                 const int e = e0 + lane;
                 Cand c = {0u, -INFINITY};
                 if (e < cnt) c = buf[e];
-                memo_recheck<(DC > 0)>(I, pk, d, ncen, e < cnt && c.U >= T, c.idx, lane, best, nre);
+                memo_recheck<(DC > 0)>(I, pk, d, ncen, e < cnt && c.U >= T, c.idx, lane, best, nre, st);
             }
         } else {
             // the buffer overflowed: rescan the warp's running minima against
@@ -798,13 +810,14 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                         lp_upper(((uint32_t)reinterpret_cast<const uint16_t *>(I.mind)[g] + 1u) << 16, delta, opg) >=
                             T;
                     const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
-                    if (pred) buf[c2 + __popc(bal & ((1u << lane) - 1u))] = Cand{(uint32_t)(g - lo), 0.f};
+                    if (pred && KC_IN_RANGE(st, c2 + __popc(bal & ((1u << lane) - 1u)), LP_CAP, KC_AT_CANDIDATE))
+                        buf[c2 + __popc(bal & ((1u << lane) - 1u))] = Cand{(uint32_t)(g - lo), 0.f};
                     c2 += __popc(bal);
                     if (c2 > LP_CAP - 32) {
                         __syncwarp();
                         for (int e0 = 0; e0 < c2; e0 += 32)
                             memo_recheck<(DC > 0)>(I, pk, d, ncen, e0 + lane < c2, e0 + lane < c2 ? buf[e0 + lane].idx : 0u,
-                                         lane, best, nre);
+                                         lane, best, nre, st);
                         c2 = 0;
                         __syncwarp();
                     }
@@ -813,7 +826,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             __syncwarp();
             for (int e0 = 0; e0 < c2; e0 += 32)
                 memo_recheck<(DC > 0)>(I, pk, d, ncen, e0 + lane < c2, e0 + lane < c2 ? buf[e0 + lane].idx : 0u, lane, best,
-                             nre);
+                             nre, st);
         }
         nre = __reduce_add_sync(0xFFFFFFFFu, nre);
         if (lane == 0 && nre) atomicAdd(&g_counters[0], (unsigned long long)nre);
@@ -842,10 +855,14 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             if (lane == 0) sh.Lcta = 0u;   // next step's admission bound starts over
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {
                 const int64_t c = key_idx(g);
-                float ec;
-                lp_load_center<KIND>(I, c, d, ng, cl, scs, it + 1, lane, &ec);
-                if (lane == 0) sh.ecmax = fmaxf(sh.ecmax, ec);
-                if (r == 0 && lane == 0) I.centers[it + 1] = out_index(I, c);
+                if (KC_IN_RANGE(st, c, I.n, KC_AT_CENTER_LOAD) && KC_IN_RANGE(st, it + 1, I.kcap, KC_AT_CENTER_COPY)) {
+                    float ec;
+                    lp_load_center<KIND>(I, c, d, ng, cl, scs, it + 1, lane, &ec);
+                    if (lane == 0) sh.ecmax = fmaxf(sh.ecmax, ec);
+                    if (r == 0 && lane == 0) I.centers[it + 1] = out_index(I, c);
+                } else {
+                    ab = true;
+                }
             }
             if (lane == 0) {
                 sh.key = g;
@@ -907,7 +924,7 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_kernel(GonArgs a) {
     if (r < 0 || r >= I.G) return;
     if (ld_volatile_i32(&a.st->code) != 0) return;
     if (!instance_ok<T>(I, a.st)) return;
-    gon_solve<T, DC, GROUP_NT>(I, r, I.G, cs, sh, a.st, a.timeout_cycles, a.withhold);
+    gon_solve<T, DC, GROUP_NT>(I, r, I.G, cs, sh, a.st, a.timeout_cycles, a.withhold, a.bad_index != 0);
 }
 
 // Queue mode, optionally with heavy instances in front: insts[0, nheavy)
@@ -1122,8 +1139,10 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_resident_kernel(GonArgs a) {
         const unsigned own = __ballot_sync(0xFFFFFFFFu, wb != 0 && best == wb);
         if (own && lane == __ffs(own) - 1) {
             const int i = (int)((int64_t)key_idx(wb) - lo_r);
+            if (i < NT || KC_IN_RANGE(a.st, i - NT, cap, KC_AT_RESIDENT_SMEM)) {
 #pragma unroll
-            for (int c = 0; c < DC; ++c) sh.cand[warp][c] = val_bits(i < NT ? xr[c] : sp[c * cap + (i - NT)]);
+                for (int c = 0; c < DC; ++c) sh.cand[warp][c] = val_bits(i < NT ? xr[c] : sp[c * cap + (i - NT)]);
+            }
         }
         if (lane == 0) sh.red[warp] = wb;
         __syncthreads();
@@ -1174,6 +1193,7 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_resident_kernel(GonArgs a) {
                 const unsigned wl = __ballot_sync(0xFFFFFFFFu, gg != 0 && lk == gg);
                 const int win = __shfl_sync(0xFFFFFFFFu, ls, wl ? __ffs(wl) - 1 : 0);
                 // the winner's coordinates from its slot (each tag set once written)
+                if (!ab && !KC_IN_RANGE(a.st, win, G, KC_AT_SLOT)) ab = true;
                 if (!ab && lane < DC) {
                     const uint64_t *wp = row + (int64_t)win * SW + 1 + lane;
                     uint64_t w = ld_relaxed_u64(wp);
@@ -1205,7 +1225,8 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_resident_kernel(GonArgs a) {
             ++it;
             break;
         }
-        if (r == 0 && tid == 0 && it + 1 < I.k) I.centers[it + 1] = out_index(I, key_idx(g));
+        if (r == 0 && tid == 0 && it + 1 < I.k && KC_IN_RANGE(a.st, key_idx(g), I.n, KC_AT_CENTER_LOAD))
+            I.centers[it + 1] = out_index(I, key_idx(g));
     }
     // the running minima, for the radius recheck
 #pragma unroll

@@ -53,6 +53,35 @@ __device__ __forceinline__ void set_status(DevStatus *st, int code, int where, i
     }
 }
 
+// ------------------------------------------------------- checked build
+// Compiled with -DKC_CHECKS (a separate library, libkcenter_checks.so, built
+// by build.build(checks=True)), kernels test the indices they are about to
+// use against the extent of the buffer they address and, on a miss, record
+// KC_ERR_BOUNDS (where = the site, info = the index) and skip the access
+// instead of making it.  This stands in for compute-sanitizer where that tool
+// is not available.  In the regular build the test is the constant true.
+#ifdef KC_CHECKS
+__device__ __forceinline__ bool kc_in_range(DevStatus *st, int64_t i, int64_t extent, int where) {
+    if (i >= 0 && i < extent) return true;
+    set_status(st, KC_ERR_BOUNDS, where, i);
+    return false;
+}
+#define KC_IN_RANGE(st, i, extent, where) kc::kc_in_range((st), (int64_t)(i), (int64_t)(extent), (where))
+#else
+#define KC_IN_RANGE(st, i, extent, where) true
+#endif
+// Sites of the checked build (DevStatus.where).
+enum {
+    KC_AT_CENTER_LOAD = 11,   // a GON winner's index, before its coordinates are read
+    KC_AT_RESIDENT_SMEM = 12, // a resident kernel's shared-memory column
+    KC_AT_CANDIDATE = 13,     // a mixed-precision candidate buffer entry
+    KC_AT_RECHECK = 14,       // a point index of an exact recheck
+    KC_AT_CENTER_COPY = 15,   // a center slot of the transposed FP32 center copy
+    KC_AT_EIM_INDEX = 16,     // an index into the points in EIM's kernels
+    KC_AT_RADIUS_LIST = 17,   // an entry of the radius recheck's point list
+    KC_AT_SLOT = 18           // a GON exchange slot
+};
+
 // ---------------------------------------------------------------- keys
 // A 64-bit argmax key: the 32-bit value (float bits of a non-negative float,
 // which order like unsigned integers, or an unsigned integer) in the high
@@ -249,6 +278,9 @@ struct GonArgs {
     // a group does not publish its exchange slot, so that the group's waits
     // run out of their budget; 0 = never
     int withhold;
+    // testing hook of the checked build (KC_TEST_BAD_INDEX): the first
+    // winner index is replaced by one past the instance; 0 = never
+    int bad_index;
     // resident form (single instance, gon_resident_kernel): points per
     // coordinate held in each CTA's shared memory; 0 = the streaming kernels
     int res_cap;

@@ -218,8 +218,9 @@ __global__ void recheck_max_kernel(const float *__restrict__ pk, const float *__
     for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < cnt;
          base += warps * 32) {
         const int64_t i = base + lane;
-        const int64_t x = i < cnt ? (list ? (int64_t)list[i] : i) : 0;
-        const bool flag = i < cnt && can_reach(mind, x, thr, eblk, ecmax, opg, sc);
+        int64_t x = i < cnt ? (list ? (int64_t)list[i] : i) : 0;
+        if (i < cnt && !KC_IN_RANGE((DevStatus *)st, x, n, KC_AT_RADIUS_LIST)) x = -1;
+        const bool flag = i < cnt && x >= 0 && can_reach(mind, x, thr, eblk, ecmax, opg, sc);
         unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);
         while (todo) {
             const int src = __ffs(todo) - 1;
