@@ -122,16 +122,6 @@ __device__ __forceinline__ void dist4(const T *__restrict__ blk, int d, const T 
 // when its blocks are, not when its slowest warp's fixed list is.  A block's
 // minima stay with the CTA, which orders every step's accesses with its
 // barriers.  ctr null: the fixed assignment i = warp + j W.
-// Ask L2 for `bytes` at p (one 128-byte line per lane and round); nothing
-// waits for it.  Warps call it for their first block of the next step before
-// the step's exchange, so that the next sweep starts on L2 hits while the
-// memory pipeline would otherwise be empty.
-__device__ __forceinline__ void prefetch_l2(const void *p, size_t bytes, int lane) {
-    const char *c = static_cast<const char *>(p);
-    for (size_t off = (size_t)lane * 128; off < bytes; off += 32 * 128)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + off));
-}
-
 __device__ __forceinline__ int64_t cta_block(int64_t b0, int r, int G, int W, int i) {
     return b0 + (int64_t)r * W + (i % W) + (int64_t)(i / W) * G * W;
 }
@@ -301,13 +291,6 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
                                          (G > 1 && I.tail) ? I.tail + it : nullptr);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
-        if (G > 1 && it + 1 < I.k) {   // this warp's share of the CTA's first round of the next step
-            const int64_t b = cta_block(I.lo / BLK, r, G, W, warp);
-            if (b <= (I.lo + I.n - 1) / BLK) {
-                prefetch_l2(pk + b * d * BLK, (size_t)d * BLK * sizeof(T), lane);
-                prefetch_l2(I.mind + b * BLK, BLK * sizeof(uint32_t), lane);
-            }
-        }
         __syncthreads();
         if (tid == 0) sh.ctr[(it + 1) & 1] = 0;   // the next step's counter (last used a step ago)
         if (warp == 0) {
@@ -832,13 +815,6 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
         if (lane == 0 && nre) atomicAdd(&g_counters[0], (unsigned long long)nre);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
-        if (G > 1 && it + 1 < I.k) {   // this warp's first block of the next step
-            const int64_t b = cta_block(b0, r, G, W, warp);
-            if (b <= b1) {
-                prefetch_l2(I.lp + b * ng * BLK, (size_t)ng * BLK * sizeof(uint32_t), lane);
-                prefetch_l2(reinterpret_cast<const uint16_t *>(I.mind) + b * BLK, BLK * sizeof(uint16_t), lane);
-            }
-        }
         __syncthreads();
         if (clk && tid == 0) pc_mark(sh.pc, 1);
         if (warp == 0) {
