@@ -268,7 +268,7 @@ kc_status kc_gonzalez_batch(int32_t count, const void *const *pts, const int64_t
  * kc_batch_plan_create takes the arguments of kc_gonzalez_batch, all of them
  * device memory of the current device (KC_ERR_ARG otherwise), checks them,
  * picks the launch shape (KC_AUTOTUNE: builds and times a plan per candidate
- * theta, three replays each, and keeps the fastest), allocates the plan's
+ * theta: a warm-up replay, then the fastest of five, and keeps the fastest), allocates the plan's
  * own scratch (freed by kc_batch_plan_destroy), uploads the instance
  * descriptors and captures pack + GON + radius into a CUDA graph.  The
  * pointers are bound at creation: each run reads the current contents of

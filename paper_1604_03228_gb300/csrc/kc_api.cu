@@ -2093,8 +2093,9 @@ kc_status kc_batch_plan_create(int32_t count, const void *const *pts, const int6
     double theta = kThetaDefault;
     const bool known = pick_theta(sig, &theta);
     if ((c.o.flags & KC_AUTOTUNE) && !known) {
-        // Time each candidate's graph (one warm-up, then the mean of three
-        // replays) and keep the fastest plan.
+        // Time each candidate's graph (one warm-up replay, then the fastest of
+        // five replays timed one by one: a mean of a few replays let one slow
+        // replay pick a slower split) and keep the fastest plan.
         kc_batch_plan *best = nullptr;
         float best_ms = 0.f;
         cudaEvent_t e0, e1;
@@ -2105,11 +2106,15 @@ kc_status kc_batch_plan_create(int32_t count, const void *const *pts, const int6
             if ((r = plan_build(b, th, count, pts, n, d, k, centers, k_out, radii, c.o, &p)) != KC_OK) break;
             float ms = 0.f;
             cudaError_t e = cudaGraphLaunch(p->exec, c.s);
-            if (e == cudaSuccess) e = cudaEventRecord(e0, c.s);
-            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = cudaGraphLaunch(p->exec, c.s);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, c.s);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            for (int rep = 0; rep < 5 && e == cudaSuccess; ++rep) {
+                float one = 0.f;
+                e = cudaEventRecord(e0, c.s);
+                if (e == cudaSuccess) e = cudaGraphLaunch(p->exec, c.s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c.s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&one, e0, e1);
+                if (e == cudaSuccess && (rep == 0 || one < ms)) ms = one;
+            }
             if (e != cudaSuccess) {
                 r = cuda_fail(e, "plan timing");
                 plan_free(p);
