@@ -394,10 +394,7 @@ struct Cand {
 };
 constexpr int LP_CAP = 128;   // candidates per warp
 
-constexpr int LP_TAIL_MAX = 16;   // shared-tail blocks a warp may take per step (its rescan list)
-
 struct ShLP {
-    int tailb[32][LP_TAIL_MAX];   // each warp's shared-tail blocks this step (offsets from the tail's start)
     uint64_t red[32];
     uint64_t key;
     unsigned Lcta;     // largest positive lower bound L published by a warp this step (float bits)
@@ -471,8 +468,8 @@ __device__ __forceinline__ uint32_t memo_min_lane(const float *__restrict__ pk, 
                                                   const float *__restrict__ cenT, int kcap, int ncen,
                                                   uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp,
                                                   const float *__restrict__ row) {
-    const int s0 = (int)__ldcg(stamp + gx);   // L2: a shared-tail block's memo may come from another CTA
-    uint32_t m = s0 ? __ldcg(m32 + gx) : 0xFFFFFFFFu;
+    const int s0 = (int)stamp[gx];
+    uint32_t m = s0 ? m32[gx] : 0xFFFFFFFFu;
     for (int i = s0; i < ncen; ++i) m = min(m, __float_as_uint(memo_dist<VEC>(pk, gx, d, cenT, kcap, i, row)));
     m32[gx] = m;
     stamp[gx] = (uint32_t)ncen;
@@ -484,8 +481,8 @@ template <bool VEC>
 __device__ uint32_t memo_min_warp(const float *__restrict__ pk, int64_t gx, int d, const float *__restrict__ cenT,
                                   int kcap, int ncen, uint32_t *__restrict__ m32, uint32_t *__restrict__ stamp,
                                   int lane, const float *__restrict__ row) {
-    const int s0 = (int)__ldcg(stamp + gx);   // L2: a shared-tail block's memo may come from another CTA
-    uint32_t m = s0 ? __ldcg(m32 + gx) : 0xFFFFFFFFu;
+    const int s0 = (int)stamp[gx];
+    uint32_t m = s0 ? m32[gx] : 0xFFFFFFFFu;
     for (int i = s0 + lane; i < ncen; i += 32)
         m = min(m, __float_as_uint(memo_dist<VEC>(pk, gx, d, cenT, kcap, i, row)));
 #pragma unroll
@@ -508,7 +505,7 @@ __device__ __forceinline__ void memo_recheck(const GonInst &I, const float *__re
                                              DevStatus *st) {
     want = want && KC_IN_RANGE(st, idx, I.n, KC_AT_RECHECK);
     const int64_t gx = I.lo + idx;
-    const bool small = want && ncen - (int)__ldcg(I.stamp + gx) <= MEMO_LANE_GAP;
+    const bool small = want && ncen - (int)I.stamp[gx] <= MEMO_LANE_GAP;
     if (small) {
         const uint32_t mm = memo_min_lane<VEC>(pk, gx, d, I.cenT, I.kcap, ncen, I.m32, I.stamp,
                                           I.rm ? I.rm + (int64_t)idx * d : nullptr);
@@ -598,12 +595,8 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
     __syncthreads();
     // fixed assignment of the CTA's blocks to its warps (claiming them from a
     // counter, as the FP32 sweep does, measured slower here: 183 -> 188 ms
-    // per solve on 8M x 64, k = 1024); with a tail counter the group shares
-    // its last blocks (tail_start), at most LP_TAIL_MAX per warp and step, so
-    // the pool is capped at what the warps' lists hold
+    // per solve on 8M x 64, k = 1024)
     const int64_t b0 = lo / BLK;
-    int64_t ts = tail_start(b0, b1, G, W, G > 1 && I.tail != nullptr);
-    if (ts <= b1 && b1 + 1 - ts > (int64_t)G * W * LP_TAIL_MAX / 2) ts = b1 + 1 - (int64_t)G * W * LP_TAIL_MAX / 2;
     if (warp == 0) {
         float ec;
         lp_load_center<KIND>(I, I.first, d, ng, cl, scs, 0, lane, &ec);
@@ -625,30 +618,9 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
         float Lrun = -INFINITY;
         int cnt = 0;
         bool ovf = false;
-        int bi = warp, ntail = 0;
-        int64_t pend = -1;   // second block of a claimed tail pair
-        for (;;) {
-            int64_t b = cta_block(b0, r, G, W, bi);
-            if (b < ts) {
-                bi += W;
-            } else if (ts > b1) {
-                break;
-            } else if (pend >= 0) {
-                b = pend;
-                pend = -1;
-            } else {
-                if (ntail + 2 > LP_TAIL_MAX) break;   // list full: the other warps take the rest
-                int t = 0;
-                if (lane == 0) t = atomicAdd(I.tail + it, 2);
-                t = __shfl_sync(0xFFFFFFFFu, t, 0);
-                b = ts + t;
-                if (b > b1) break;
-                if (b + 1 <= b1) pend = b + 1;
-            }
-            if (b >= ts) {
-                if (lane == 0) sh.tailb[warp][ntail] = (int)(b - ts);
-                ++ntail;
-            }
+        for (int bi = warp;; bi += W) {
+            const int64_t b = cta_block(b0, r, G, W, bi);
+            if (b > b1) break;
             const int64_t g0 = b * BLK + lane * 4;
             const uint4 *src = reinterpret_cast<const uint4 *>(I.lp + b * ng * BLK) + lane;
             float a[4] = {0.f, 0.f, 0.f, 0.f};
@@ -694,7 +666,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             uint2 *mp = reinterpret_cast<uint2 *>(m16 + b * BLK) + lane;
             if (it > 0) {
                 if (full) {
-                    const uint2 ov = __ldcg(mp);   // L2: shared-tail blocks move between CTAs
+                    const uint2 ov = *mp;
                     o[0] = ov.x & 0xFFFFu;
                     o[1] = ov.x >> 16;
                     o[2] = ov.y & 0xFFFFu;
@@ -702,7 +674,7 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (g0 + q >= lo && g0 + q < hi) o[q] = __ldcg(m16 + g0 + q);
+                        if (g0 + q >= lo && g0 + q < hi) o[q] = m16[g0 + q];
                 }
             }
             uint32_t m[4];
@@ -809,23 +781,16 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             if (lane == 0) atomicAdd(&g_counters[1], 1ull);
             int c2 = 0;
             __syncwarp();
-            // this warp's blocks of the step: its own, then its shared-tail ones
-            for (int bi = warp, ti = 0;;) {
-                int64_t b = cta_block(b0, r, G, W, bi);
-                if (b < ts) {
-                    bi += W;
-                } else {
-                    if (ti >= ntail) break;
-                    b = ts + sh.tailb[warp][ti++];
-                }
+            for (int bi = warp;; bi += W) {
+                const int64_t b = cta_block(b0, r, G, W, bi);
+                if (b > b1) break;
                 const float delta = __fadd_ru(I.eblk[b], ecmax);
 #pragma unroll 1
                 for (int q = 0; q < 4; ++q) {
                     const int64_t g = b * BLK + lane * 4 + q;
                     const bool pred =
                         g >= lo && g < hi &&
-                        lp_upper(((uint32_t)__ldcg(reinterpret_cast<const uint16_t *>(I.mind) + g) + 1u) << 16, delta,
-                                 opg) >=
+                        lp_upper(((uint32_t)reinterpret_cast<const uint16_t *>(I.mind)[g] + 1u) << 16, delta, opg) >=
                             T;
                     const unsigned bal = __ballot_sync(0xFFFFFFFFu, pred);
                     if (pred && KC_IN_RANGE(st, c2 + __popc(bal & ((1u << lane) - 1u)), LP_CAP, KC_AT_CANDIDATE))
@@ -860,13 +825,8 @@ __device__ void gon_solve_lp(const GonInst &I, int r, int G, float *smem, ShLP &
             if (G > 1) {
                 const int64_t row = (int64_t)it * slot_stride(G);
                 const bool held = withhold == it + 1 && r == G - 1;
-                // with a shared tail, the step's minima and memo entries are
-                // made visible to the group before the slot is, and the other
-                // CTAs' after it is seen (as in the FP32 sweep)
-                if (I.tail) __threadfence();
                 if (lane == 0 && !held) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
                 g = poll_slots(I.slots + row, G, timeout, st, it, &ab);
-                if (I.tail) __threadfence();
             }
             if (lane == 0) sh.Lcta = 0u;   // next step's admission bound starts over
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {

@@ -212,7 +212,7 @@ cudaError_t launch_range_check(const int32_t *range2, int d, DevStatus *st, cuda
 struct GonInst {
     const void *pk;          // packed points of this instance (block aligned)
     // per-step counters of the group's shared tail of blocks ([k], zeroed),
-    // or nullptr: every block stays with its CTA (group kernels only)
+    // or nullptr: every block stays with its CTA (FP32 group kernels only)
     int *tail;
     // FP32 rows of the instance's points, row of local index 0 (row-major,
     // d floats per row), or nullptr: the exact rechecks of the mixed-precision
