@@ -74,3 +74,23 @@ def test_batch_plan_host_argument_errors():
     assert L.kc_batch_plan_run(None, None) == kc.KC_ERR_ARG
     assert L.kc_batch_plan_wait(None) == kc.KC_ERR_ARG
     assert L.kc_batch_plan_destroy(None) == kc.KC_OK
+
+
+def test_measurement_and_diagnostic_entry_points_check_arguments():
+    import paper_1604_03228_gb300 as kc
+    L = kc.load()
+    sink = np.zeros(1, dtype=np.uint64)
+    buf = np.zeros(64, dtype=np.float32)
+    # rejected before any CUDA call: no buffer, no sink, no repetition, size not a multiple of 16
+    assert L.kc_read_sweep(None, 256, 1, sink.ctypes.data, None) == kc.KC_ERR_ARG
+    assert L.kc_read_sweep(buf.ctypes.data, 256, 1, None, None) == kc.KC_ERR_ARG
+    assert L.kc_read_sweep(buf.ctypes.data, 256, 0, sink.ctypes.data, None) == kc.KC_ERR_ARG
+    assert L.kc_read_sweep(buf.ctypes.data, 250, 1, sink.ctypes.data, None) == kc.KC_ERR_ARG
+    assert L.kc_last_fp32_radius(None, None) == kc.KC_ERR_ARG
+
+
+def test_checked_build_flags_are_declared():
+    import paper_1604_03228_gb300 as kc
+    src = open(os.path.join(ROOT, "include", "kcenter.h")).read()
+    assert "KC_ERR_BOUNDS = 7" in src and "KC_TEST_BAD_INDEX 0x40000000u" in src
+    assert kc.binding.KC_ERR_BOUNDS == 7 and kc.binding.KC_TEST_BAD_INDEX == 0x40000000
