@@ -181,7 +181,9 @@ __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__
         uint32_t o[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
         if (!first_step) {
             if (full) {
-                const uint4 ov = __ldcg(mp);   // L2: tail blocks move between CTAs
+                // past L1 only when tail blocks move between CTAs; a small
+                // instance's minima otherwise stay in L1 from step to step
+                const uint4 ov = gtail ? __ldcg(mp) : *mp;
                 o[0] = ov.x;
                 o[1] = ov.y;
                 o[2] = ov.z;
@@ -189,7 +191,7 @@ __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__
             } else {
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (g0 + q >= lo && g0 + q < hi) o[q] = __ldcg(mind + g0 + q);
+                    if (g0 + q >= lo && g0 + q < hi) o[q] = gtail ? __ldcg(mind + g0 + q) : mind[g0 + q];
             }
         }
         typename AccOf<T>::type acc[4];
@@ -278,16 +280,18 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
     }
     if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
     __syncthreads();
+    const bool claim =
+        NT == GROUP_NT && (I.lo + I.n - 1) / BLK - I.lo / BLK + 1 >= 4 * (int64_t)G * W;
 
     int it;
     uint64_t K = 0;
     for (it = 0; it < I.k; ++it) {
-        // claimed blocks in the 1024-thread group CTAs (measured: GON on
-        // 8M x 64, k = 1024, 313 -> 308 ms); the fixed assignment in the
-        // 256-thread queue CTAs (MRG round 1 on 10M x 16 was 5% slower with
-        // claims)
+        // claimed blocks in the 1024-thread group CTAs when every warp has
+        // several (measured: GON on 8M x 64, k = 1024, 313 -> 308 ms); the
+        // fixed assignment in the 256-thread queue CTAs (MRG round 1 on
+        // 10M x 16 was 5% slower with claims) and for small instances
         uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G,
-                                         NT == GROUP_NT ? &sh.ctr[it & 1] : nullptr,
+                                         claim ? &sh.ctr[it & 1] : nullptr,
                                          (G > 1 && I.tail) ? I.tail + it : nullptr);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
