@@ -612,8 +612,10 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     const int res_grid = (!lp && !pin_pts && !bad_index) ? gon_resident_plan(c.o.dtype, d, n, &res_cap, &res_sw) : 0;
     const int grid = res_grid ? res_grid : choose_gon_grid(c.o.dtype, d, n, lp);
     // the FP32 streaming group shares the last blocks of every step between its
-    // CTAs (KC_GON_TAIL=0 keeps every block with its CTA)
-    bool use_tail = !lp && !res_grid && grid > 1;
+    // CTAs when every warp has at least two whole rounds of its own before the
+    // tail (tail_start; KC_GON_TAIL=0 keeps every block with its CTA)
+    bool use_tail = !lp && !res_grid && grid > 1 &&
+                    nblocks(n) * 7 / 8 / ((int64_t)grid * gon_warps_per_cta()) >= 2;
     if (const char *env = getenv("KC_GON_TAIL")) use_tail = use_tail && atoi(env) != 0;
     const int64_t nb = nblocks(n);
     const size_t esz = 4;

@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <cstdlib>
 #include <type_traits>
 
@@ -154,27 +155,9 @@ __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t hi = lo + n;
     const int64_t b0 = lo / BLK, b1 = (hi - 1) / BLK;
-    const int64_t ts = tail_start(b0, b1, G, W, gtail != nullptr);
     uint64_t best = 0;
-    int nxt = ctr ? claim_block(ctr, lane) : warp;
-    int64_t pend = -1;   // second block of a claimed tail pair
-    for (;;) {
-        int64_t b = cta_block(b0, r, G, W, nxt);
-        if (b < ts) {
-            nxt = ctr ? claim_block(ctr, lane) : nxt + W;
-        } else if (ts > b1) {
-            break;
-        } else if (pend >= 0) {
-            b = pend;
-            pend = -1;
-        } else {
-            int t = 0;
-            if (lane == 0) t = atomicAdd(gtail, 2);
-            t = __shfl_sync(0xFFFFFFFFu, t, 0);
-            b = ts + t;
-            if (b > b1) break;
-            if (b + 1 <= b1) pend = b + 1;
-        }
+    // one block: distances to the newest center, the running minima, the key
+    auto block = [&](int64_t b) {
         const int64_t g0 = b * BLK + lane * 4;
         const bool full = g0 >= lo && g0 + 3 < hi;
         uint4 *mp = reinterpret_cast<uint4 *>(mind + b * BLK) + lane;
@@ -214,6 +197,33 @@ __device__ __forceinline__ uint64_t sweep(const T *__restrict__ pk, uint32_t *__
                 }
             }
         }
+    };
+    if (!ctr && !gtail) {
+        // the fixed assignment: warp w of CTA r takes blocks b0 + r W + w + j G W
+        for (int64_t b = b0 + (int64_t)r * W + warp; b <= b1; b += (int64_t)G * W) block(b);
+        return best;
+    }
+    const int64_t ts = tail_start(b0, b1, G, W, gtail != nullptr);
+    int nxt = ctr ? claim_block(ctr, lane) : warp;
+    int64_t pend = -1;   // second block of a claimed tail pair
+    for (;;) {
+        int64_t b = cta_block(b0, r, G, W, nxt);
+        if (b < ts) {
+            nxt = ctr ? claim_block(ctr, lane) : nxt + W;
+        } else if (ts > b1) {
+            break;
+        } else if (pend >= 0) {
+            b = pend;
+            pend = -1;
+        } else {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(gtail, 2);
+            t = __shfl_sync(0xFFFFFFFFu, t, 0);
+            b = ts + t;
+            if (b > b1) break;
+            if (b + 1 <= b1) pend = b + 1;
+        }
+        block(b);
     }
     return best;
 }
@@ -1376,11 +1386,19 @@ int gon_resident_plan(int dtype, int d, int64_t n, int *cap, int *slot_words) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int64_t want = (n + GROUP_NT - 1) / GROUP_NT;
-    int G = (int)(want < sms ? want : sms);
-    if (G > 160) G = 160;   // warp 0 polls five slots per lane
+    // The fewest CTAs whose shares fit (at most RES_PPT points per thread, the
+    // rest of a share within the shared memory one CTA may take), but at
+    // least one CTA per 8192 points (about two 128-point blocks per warp, as
+    // the streaming kernel aims for) and at most one per SM.
+    const int64_t cap_pts = (int64_t)((size_t)optin - sizeof(ShRes) - 1024) / (4 * d) + GROUP_NT;
+    const int64_t per = std::min<int64_t>((int64_t)RES_PPT * GROUP_NT, cap_pts);
+    int64_t target = 8192;
+    if (const char *env = getenv("KC_GON_RESIDENT_PTS")) target = std::max<int64_t>(atoll(env), 1);
+    int64_t G64 = std::max<int64_t>((n + per - 1) / per, (n + target - 1) / target);
+    if (G64 > sms || G64 > 160) return 0;   // warp 0 polls at most five slots per lane
+    const int G = (int)std::max<int64_t>(G64, 1);
     const int64_t npmax = (n + G - 1) / G;
-    if (npmax > (int64_t)RES_PPT * GROUP_NT) return 0;
+    if (npmax > per) return 0;
     const int64_t c = npmax > GROUP_NT ? npmax - GROUP_NT : 1;
     const size_t smem = (size_t)c * d * 4;
     if (smem + sizeof(ShRes) + 1024 > (size_t)optin) return 0;
