@@ -614,8 +614,9 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     // the FP32 streaming group shares the last blocks of every step between its
     // CTAs when every warp has at least two whole rounds of its own before the
     // tail (tail_start; KC_GON_TAIL=0 keeps every block with its CTA)
-    bool use_tail = !lp && !res_grid && grid > 1 &&
-                    nblocks(n) * 7 / 8 / ((int64_t)grid * gon_warps_per_cta()) >= 2;
+    const bool dyn = !lp && !res_grid && c.o.dtype == KC_F32 &&
+                     nblocks(n) >= 4 * (int64_t)grid * gon_warps_per_cta();   // claimed blocks pay off
+    bool use_tail = dyn && grid > 1 && nblocks(n) * 7 / 8 / ((int64_t)grid * gon_warps_per_cta()) >= 2;
     if (const char *env = getenv("KC_GON_TAIL")) use_tail = use_tail && atoi(env) != 0;
     const int64_t nb = nblocks(n);
     const size_t esz = 4;
@@ -695,6 +696,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
     g.timeout_cycles = timeout_cycles(c.o);
     g.withhold = (c.o.flags & KC_TEST_WITHHOLD) ? 1 : 0;
     g.bad_index = bad_index ? 1 : 0;
+    g.dyn = dyn ? 1 : 0;
     c.arena->last_key32 = ra.key32;
     c.arena->last_dtype = c.o.dtype;
 

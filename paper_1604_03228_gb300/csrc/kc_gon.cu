@@ -273,8 +273,10 @@ struct Shared {
     int ctr[2];   // block counters of even and odd steps
 };
 
-// All k steps of one instance by this CTA (rank r of a group of G).
-template <typename T, int DC, int NT>
+// All k steps of one instance by this CTA (rank r of a group of G).  DYN:
+// the instance is large enough for claimed blocks and the shared tail (a
+// separate instantiation, so that small instances run the plain loop).
+template <typename T, int DC, int NT, bool DYN = false>
 __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, DevStatus *st,
                           long long timeout, int withhold = 0, bool bad_index = false) {
     constexpr int W = NT / 32;
@@ -290,8 +292,8 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
     }
     if (r == 0 && tid == 0) I.centers[0] = out_index(I, I.first);
     __syncthreads();
-    const bool claim =
-        NT == GROUP_NT && (I.lo + I.n - 1) / BLK - I.lo / BLK + 1 >= 4 * (int64_t)G * W;
+    const bool claim = DYN && NT == GROUP_NT && (I.lo + I.n - 1) / BLK - I.lo / BLK + 1 >= 4 * (int64_t)G * W;
+    const bool tail = DYN && G > 1 && I.tail != nullptr;
 
     int it;
     uint64_t K = 0;
@@ -301,12 +303,11 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
         // fixed assignment in the 256-thread queue CTAs (MRG round 1 on
         // 10M x 16 was 5% slower with claims) and for small instances
         uint64_t best = sweep<T, DC, NT>(pk, I.mind, I.lo, I.n, d, cs, it == 0, r, G,
-                                         claim ? &sh.ctr[it & 1] : nullptr,
-                                         (G > 1 && I.tail) ? I.tail + it : nullptr);
+                                         claim ? &sh.ctr[it & 1] : nullptr, tail ? I.tail + it : nullptr);
         best = warp_max_u64(best);
         if (lane == 0) sh.red[warp] = best;
         __syncthreads();
-        if (tid == 0) sh.ctr[(it + 1) & 1] = 0;   // the next step's counter (last used a step ago)
+        if (DYN && tid == 0) sh.ctr[(it + 1) & 1] = 0;   // the next step's counter (last used a step ago)
         if (warp == 0) {
             uint64_t v = lane < W ? sh.red[lane] : 0;
             v = warp_max_u64(v);
@@ -319,10 +320,10 @@ __device__ void gon_solve(const GonInst &I, int r, int G, T *cs, Shared &sh, Dev
                 // CTA's threads before the barrier) are made visible to the
                 // group before the slot is, and the other CTAs' after it is
                 // seen (the release / acquire pattern of a grid barrier)
-                if (I.tail) __threadfence();
+                if (tail) __threadfence();
                 if (lane == 0 && !held) st_relaxed_u64(&I.slots[row + r], v ? v : 1);
                 g = poll_slots(I.slots + row, G, timeout, st, it, &ab);
-                if (I.tail) __threadfence();
+                if (tail) __threadfence();
             }
             if (!ab && key_val(g) != 0 && it + 1 < I.k) {
 #ifdef KC_CHECKS
@@ -899,7 +900,7 @@ __device__ __forceinline__ void find_group(const GonInst *insts, int m, GonInst 
     I = insts[lo];
 }
 
-template <typename T, int DC>
+template <typename T, int DC, bool DYN>
 __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_kernel(GonArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *cs = reinterpret_cast<T *>(smem_raw);
@@ -914,7 +915,7 @@ __global__ void __launch_bounds__(GROUP_NT, 1) gon_group_kernel(GonArgs a) {
     if (r < 0 || r >= I.G) return;
     if (ld_volatile_i32(&a.st->code) != 0) return;
     if (!instance_ok<T>(I, a.st)) return;
-    gon_solve<T, DC, GROUP_NT>(I, r, I.G, cs, sh, a.st, a.timeout_cycles, a.withhold, a.bad_index != 0);
+    gon_solve<T, DC, GROUP_NT, DYN>(I, r, I.G, cs, sh, a.st, a.timeout_cycles, a.withhold, a.bad_index != 0);
 }
 
 // Queue mode, optionally with heavy instances in front: insts[0, nheavy)
@@ -1249,7 +1250,7 @@ void *pick_resident(int dtype, int d) {
     }
 }
 
-template <typename T, int DC> void *group_fn() { return (void *)gon_group_kernel<T, DC>; }
+template <typename T, int DC, bool DYN = false> void *group_fn() { return (void *)gon_group_kernel<T, DC, DYN>; }
 template <typename T, int DC> void *queue_fn() { return (void *)gon_queue_kernel<T, DC>; }
 template <int KIND, int DC> void *group_lp_fn() { return (void *)gon_group_lp_kernel<KIND, DC>; }
 template <int KIND, int DC> void *queue_lp_fn() { return (void *)gon_queue_lp_kernel<KIND, DC>; }
@@ -1293,7 +1294,19 @@ size_t lp_smem_bytes(int kind, int dmax, int nt) {
     return (size_t)2 * ((dp + 1) & ~1) * sizeof(float) + (size_t)(nt / 32) * LP_CAP * sizeof(Cand);
 }
 
-void *pick_group(int dtype, int dc) {
+void *pick_group(int dtype, int dc, bool dyn = false) {
+    if (dtype == KC_F32 && dyn) {
+        switch (dc) {
+            case 2: return group_fn<float, 2, true>();
+            case 3: return group_fn<float, 3, true>();
+            case 8: return group_fn<float, 8, true>();
+            case 10: return group_fn<float, 10, true>();
+            case 16: return group_fn<float, 16, true>();
+            case 32: return group_fn<float, 32, true>();
+            case 64: return group_fn<float, 64, true>();
+            default: return group_fn<float, 0, true>();
+        }
+    }
     if (dtype == KC_F32) {
         switch (dc) {
             case 2: return group_fn<float, 2>();
@@ -1341,9 +1354,9 @@ int gon_threads() { return GROUP_NT; }
 int gon_queue_warps() { return QUEUE_NT / 32; }
 int gon_warps_per_cta() { return GROUP_NT / 32; }
 
-static void *pick_fn(int dtype, int lp, int dc, bool queue) {
+static void *pick_fn(int dtype, int lp, int dc, bool queue, bool dyn = false) {
     if (dtype == KC_F32 && lp) return queue ? pick_queue_lp(lp, dc) : pick_group_lp(lp, dc);
-    return queue ? pick_queue(dtype, dc) : pick_group(dtype, dc);
+    return queue ? pick_queue(dtype, dc) : pick_group(dtype, dc, dyn);
 }
 
 static size_t smem_for(int dtype, int lp, int dmax, bool queue) {
@@ -1386,17 +1399,19 @@ int gon_resident_plan(int dtype, int d, int64_t n, int *cap, int *slot_words) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    // The fewest CTAs whose shares fit (at most RES_PPT points per thread, the
-    // rest of a share within the shared memory one CTA may take), but at
-    // least one CTA per 8192 points (about two 128-point blocks per warp, as
-    // the streaming kernel aims for) and at most one per SM.
+    // One CTA per 4096 points (four per thread; measured best of 1024, 4096
+    // and 8192 on sets of 10k to 1M points in d = 2..10), at most one per SM,
+    // and at least as many as the shares need to fit (at most RES_PPT points
+    // per thread, the rest of a share within the shared memory one CTA may
+    // take).  KC_GON_RESIDENT_PTS sets the points per CTA.
     const int64_t cap_pts = (int64_t)((size_t)optin - sizeof(ShRes) - 1024) / (4 * d) + GROUP_NT;
     const int64_t per = std::min<int64_t>((int64_t)RES_PPT * GROUP_NT, cap_pts);
-    int64_t target = 8192;
+    int64_t target = 4096;
     if (const char *env = getenv("KC_GON_RESIDENT_PTS")) target = std::max<int64_t>(atoll(env), 1);
-    int64_t G64 = std::max<int64_t>((n + per - 1) / per, (n + target - 1) / target);
-    if (G64 > sms || G64 > 160) return 0;   // warp 0 polls at most five slots per lane
-    const int G = (int)std::max<int64_t>(G64, 1);
+    const int64_t gmin = (n + per - 1) / per;
+    if (gmin > sms || gmin > 160) return 0;   // warp 0 polls at most five slots per lane
+    const int G = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(gmin, (n + target - 1) / target),
+                                                             std::min(sms, 160)));
     const int64_t npmax = (n + G - 1) / G;
     if (npmax > per) return 0;
     const int64_t c = npmax > GROUP_NT ? npmax - GROUP_NT : 1;
@@ -1441,7 +1456,7 @@ cudaError_t launch_gon(GonArgs &a, cudaStream_t s) {
         return cudaLaunchKernelExC(&cfg, fn, args);
     }
     const size_t smem = smem_for(a.dtype, a.lp_kind, a.dmax, a.queue != 0);
-    void *fn = pick_fn(a.dtype, a.lp_kind, a.dc, a.queue != 0);
+    void *fn = pick_fn(a.dtype, a.lp_kind, a.dc, a.queue != 0, a.dyn != 0);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -281,6 +281,9 @@ struct GonArgs {
     // testing hook of the checked build (KC_TEST_BAD_INDEX): the first
     // winner index is replaced by one past the instance; 0 = never
     int bad_index;
+    // FP32 group kernels of large instances: the instantiation that claims
+    // blocks and shares the tail (gon_solve's DYN); 0 = the plain loop
+    int dyn;
     // resident form (single instance, gon_resident_kernel): points per
     // coordinate held in each CTA's shared memory; 0 = the streaming kernels
     int res_cap;
