@@ -2,8 +2,9 @@
 k steps, running minima in registers, candidate coordinates carried in the
 exchange slots) against the oracle and against the streaming kernel
 (KC_GON_RESIDENT=0), on sizes that use registers only, registers plus shared
-memory, and the 1M x 10 workload that fills shared memory; and the streaming
-kernel's shared tail of blocks (KC_GON_TAIL=0 turns it off) on 3M points.
+memory, and the 1M x 10 workload that fills shared memory; the dimensions
+below 8 that stay on the streaming kernel; and the streaming kernel's shared
+tail of blocks (KC_GON_TAIL=0 turns it off) on 3M points.
 """
 import numpy as np
 import pytest
@@ -22,6 +23,7 @@ def _dev(x):
 @pytest.mark.parametrize("n", [1, 1025, 4097, 150_001, 600_000])
 @pytest.mark.parametrize("d", [2, 3, 8, 10])
 def test_resident_equals_oracle(kc, n, d):
+    # d = 2 and 3 run the streaming kernel (no resident specialisation)
     pts = I.gauss_mixture(n, d, 900 + d, 12, 1.0, -30.0, 30.0)
     k = min(n, 64)
     r = kc.kc_gonzalez(_dev(pts), k, first=n // 3)
@@ -42,8 +44,10 @@ def test_resident_equals_streaming_on_the_1m_x_10_workload(kc, monkeypatch):
 
 
 def test_resident_int_ties_and_early_stop(kc):
-    # small integer grid: many exact ties (lowest index wins) and early stop
-    pts = I.int_points(300_000, 2, 901, 0, 6)
+    # a 7 x 7 integer grid in the first two of ten coordinates: many exact
+    # ties (lowest index wins) and an early stop after the 49 distinct points
+    pts = np.zeros((300_000, 10), np.int32)
+    pts[:, :2] = I.int_points(300_000, 2, 901, 0, 6)
     r = kc.kc_gonzalez(_dev(pts), 80)
     ref = O.gonzalez(pts, 80)
     assert r.centers.cpu().numpy().tolist() == ref.centers.tolist()
