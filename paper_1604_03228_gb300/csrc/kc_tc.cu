@@ -124,6 +124,11 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
+// An L2 prefetch of bytes (a multiple of 16) at a 16-byte aligned address.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
@@ -487,6 +492,7 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
 struct TcArgs {
     int d, kp, kc, ntiles;      // centers: kc real of ntiles * TC_N rows
     int resident;               // all center tiles stay in shared memory (loaded once)
+    int pf;                     // point tiles prefetched into L2 this many of the CTA's tiles ahead (0: none)
     int64_t npts;               // points (rows of the A tiles)
     const __half *at;           // point tiles [ceil(npts/128)][128 x kp]
     const float *an, *ae;       // point norms and bounds
@@ -579,6 +585,13 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
                 mbar_expect_tx(&a_full[sa], a_bytes);
                 bulk_g2s(sAb + sa * a_bytes, a.at + pt * (int64_t)TC_M * kp, a_bytes, &a_full[sa]);
                 afill ^= 1u << sa;
+                if (a.pf > 0) {
+                    // the first call also covers the tiles between, later calls one new tile each
+                    for (int q = (p == 0 ? 1 : a.pf); q <= a.pf; ++q) {
+                        const int64_t pq = pt + (int64_t)q * gridDim.x;
+                        if (pq < ntile_pts) bulk_prefetch_l2(a.at + pq * (int64_t)TC_M * kp, a_bytes);
+                    }
+                }
                 if (a.resident) {
                     if (p == 0) {   // every center tile, once, behind the first point tile
                         mbar_expect_tx(&b_full[0], (uint32_t)a.ntiles * b_bytes);
@@ -1147,6 +1160,7 @@ cudaError_t launch_tc_radius(const float *pk, const float *rm, int64_t n, int d,
     a.mhi = B.mhi;
     a.mlo_max = B.mlomax;
     a.st = st;
+    if (const char *env = getenv("KC_TC_PF")) a.pf = std::max(0, std::min(atoi(env), 16));
     const size_t smem = tc_smem_for(a);
     if ((e = cudaFuncSetAttribute(tc_dmin_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
