@@ -55,11 +55,22 @@
  *  KC_TC_STREAM_CENTERS=1    tensor-core blocks stream the center tiles through
  *                            a two-stage ring even when all of them fit in
  *                            shared memory
+ *  KC_TC_PAIR=0              streamed center tiles feed one point tile each
+ *                            (default: two, for d <= 93)
  *  KC_PRUNE_PAIR_CAP=N       capacity of the tensor-core prune's buffer of
  *                            undecided pairs (rows past it get a full exact
  *                            scan)
  *  KC_GON_GRID=G             CTAs of a single Gonzalez launch (clamped to the
  *                            co-resident maximum)
+ *  KC_GON_RESIDENT=0         single FP32 / int32 Gonzalez instances always
+ *                            stream their points (default: held on chip when
+ *                            they fit, d = 8 or 10)
+ *  KC_GON_RESIDENT_PTS=P     points per CTA the resident form aims for
+ *                            (default 4096)
+ *  KC_GON_TAIL=0             no shared tail of blocks in large streaming FP32
+ *                            Gonzalez launches
+ *  KC_LP_LOCAL_T=1           mixed-precision sweeps recheck against each CTA's
+ *                            own bound instead of the group's
  *  KC_BATCH_THETA=x|inf      the batch split of kc_gonzalez_batch and batch
  *                            plans (see there); overrides the tuned value
  */

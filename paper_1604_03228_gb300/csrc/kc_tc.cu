@@ -32,6 +32,9 @@
 //        while those are used, releases the accumulator, and folds v into a
 //        running maximum three values at a time (radius) or compares it with
 //        the point's two decision limits (prune).
+// With streamed centers (the prune; the radius when the centers do not fit)
+// tc_dmin2_kernel takes two point tiles per center tile instead, so that a
+// center tile read from L2 feeds two MMAs (see there).
 // Shared-memory operand layout: no swizzle, K-major, 8 x 16-byte core
 // matrices; core matrix (row block mi, column block ki) of an R-row tile at
 // byte ((ki * R/8) + mi) * 128: the descriptor's leading (K) byte offset is
@@ -122,11 +125,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                      smem_u32(dst)),
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
-}
-
-// An L2 prefetch of bytes (a multiple of 16) at a 16-byte aligned address.
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
@@ -492,7 +490,6 @@ __global__ void tc_rows_kernel(const float *__restrict__ pk, const float *__rest
 struct TcArgs {
     int d, kp, kc, ntiles;      // centers: kc real of ntiles * TC_N rows
     int resident;               // all center tiles stay in shared memory (loaded once)
-    int pf;                     // point tiles prefetched into L2 this many of the CTA's tiles ahead (0: none)
     int64_t npts;               // points (rows of the A tiles)
     const __half *at;           // point tiles [ceil(npts/128)][128 x kp]
     const float *an, *ae;       // point norms and bounds
@@ -585,13 +582,6 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
                 mbar_expect_tx(&a_full[sa], a_bytes);
                 bulk_g2s(sAb + sa * a_bytes, a.at + pt * (int64_t)TC_M * kp, a_bytes, &a_full[sa]);
                 afill ^= 1u << sa;
-                if (a.pf > 0) {
-                    // the first call also covers the tiles between, later calls one new tile each
-                    for (int q = (p == 0 ? 1 : a.pf); q <= a.pf; ++q) {
-                        const int64_t pq = pt + (int64_t)q * gridDim.x;
-                        if (pq < ntile_pts) bulk_prefetch_l2(a.at + pq * (int64_t)TC_M * kp, a_bytes);
-                    }
-                }
                 if (a.resident) {
                     if (p == 0) {   // every center tile, once, behind the first point tile
                         mbar_expect_tx(&b_full[0], (uint32_t)a.ntiles * b_bytes);
@@ -867,6 +857,307 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
     }
 }
 
+// Two point tiles per center tile, for streamed centers (the prune; the
+// radius when the centers do not fit in shared memory).  tc_dmin_kernel
+// reads every center tile from L2 once per point tile; at the MMA's rate that
+// is most of the L2 bandwidth (40 KB per 128 x 256 x 80 block, d = 64).  Here
+// a center tile feeds two MMAs, one per point tile of a pair, each into its
+// own TMEM accumulator (columns 0-255 and 256-511), so every center byte
+// serves twice the flops.  While the epilogue drains one accumulator the
+// other is being computed: the two accumulators give the overlap of the
+// double buffer they replace.  Warps 0-3 own point tile 0's rows, 4-7 tile
+// 1's (TMEM lanes 32 (w % 4) ..); each thread holds one row and all 256
+// columns of every center tile, so a row's decision needs no exchange
+// between warps.  Shared memory: two stages of a tile pair and a two-stage
+// center ring (4 A + 2 B bytes).
+template <int MODE>
+__global__ void __launch_bounds__(384, 1) tc_dmin2_kernel(TcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int kp = a.kp;
+    const uint32_t a_bytes = (uint32_t)TC_M * kp * 2, b_bytes = (uint32_t)TC_N * kp * 2;
+    // tile j of pair stage s at smem + (2 s + j) a_bytes, center stage s after them
+    unsigned char *const sAb = smem, *const sBb = smem + 4 * a_bytes;
+    __shared__ __align__(8) uint64_t a_full[2], a_empty[2], b_full[2], b_empty[2], t_full[2], t_empty[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t ntile_pts = (a.npts + TC_M - 1) / TC_M;
+    const int64_t npairs = (ntile_pts + 1) / 2;
+    volatile int *abort = &s_abort;
+
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&a_full[s], 1);
+            mbar_init(&a_empty[s], 1);
+            mbar_init(&b_full[s], 1);
+            mbar_init(&b_empty[s], 1);
+            mbar_init(&t_full[s], 1);        // accumulator j = s
+            mbar_init(&t_empty[s], TC_M);    // its four epilogue warps
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(2 * TC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+
+    if (warp == TC_PROD) {
+        // ------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t afill = 0, bfill = 0;   // bit s: parity of stage s's fills so far
+            int64_t u = 0, p = 0;
+            for (int64_t pp = blockIdx.x; pp < npairs && !*abort; pp += gridDim.x, ++p) {
+                const int sa = (int)(p & 1);
+                const int64_t t0 = 2 * pp;
+                const bool has2 = t0 + 1 < ntile_pts;
+                if (!mbar_wait(&a_empty[sa], ((afill >> sa) & 1u) ^ 1u, abort)) {
+                    *abort = 1;
+                    set_status(a.st, KC_ERR_TIMEOUT, 6, 0);
+                    break;
+                }
+                mbar_expect_tx(&a_full[sa], (has2 ? 2u : 1u) * a_bytes);
+                bulk_g2s(sAb + (2 * sa) * a_bytes, a.at + t0 * (int64_t)TC_M * kp, a_bytes, &a_full[sa]);
+                if (has2)
+                    bulk_g2s(sAb + (2 * sa + 1) * a_bytes, a.at + (t0 + 1) * (int64_t)TC_M * kp, a_bytes, &a_full[sa]);
+                afill ^= 1u << sa;
+                for (int t = 0; t < a.ntiles; ++t, ++u) {
+                    const int s = (int)(u & 1);
+                    if (!mbar_wait(&b_empty[s], ((bfill >> s) & 1u) ^ 1u, abort)) {
+                        *abort = 1;
+                        set_status(a.st, KC_ERR_TIMEOUT, 6, t);
+                        break;
+                    }
+                    mbar_expect_tx(&b_full[s], b_bytes);
+                    bulk_g2s(sBb + s * b_bytes, a.bt + (int64_t)t * TC_N * kp, b_bytes, &b_full[s]);
+                    bfill ^= 1u << s;
+                }
+            }
+        }
+    } else if (warp == TC_MMA) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = umma_idesc_f16(TC_M, TC_N);
+            const uint32_t a_lbo = (TC_M / 8) * 128, b_lbo = (TC_N / 8) * 128;
+            uint32_t ause = 0, buse = 0, tuse = 0;   // bit s: parity of stage (accumulator) s's uses so far
+            int64_t u = 0, p = 0;
+            for (int64_t pp = blockIdx.x; pp < npairs && !*abort; pp += gridDim.x, ++p) {
+                const int sa = (int)(p & 1);
+                const int nj = 2 * pp + 1 < ntile_pts ? 2 : 1;
+                if (!mbar_wait(&a_full[sa], (ause >> sa) & 1u, abort)) {
+                    *abort = 1;
+                    set_status(a.st, KC_ERR_TIMEOUT, 7, 0);
+                    break;
+                }
+                for (int t = 0; t < a.ntiles && !*abort; ++t, ++u) {
+                    const int s = (int)(u & 1);
+                    if (!mbar_wait(&b_full[s], (buse >> s) & 1u, abort)) {
+                        *abort = 1;
+                        set_status(a.st, KC_ERR_TIMEOUT, 8, t);
+                        break;
+                    }
+                    const uint32_t bbase = smem_u32(sBb + s * b_bytes);
+                    for (int j = 0; j < nj; ++j) {
+                        if (!mbar_wait(&t_empty[j], ((tuse >> j) & 1u) ^ 1u, abort)) {
+                            *abort = 1;
+                            set_status(a.st, KC_ERR_TIMEOUT, 8, t);
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t abase = smem_u32(sAb + (2 * sa + j) * a_bytes);
+                        for (int kk = 0; kk < kp / 16; ++kk) {
+                            const uint64_t ad = umma_desc(abase + kk * 2 * a_lbo, a_lbo, 128);
+                            const uint64_t bd = umma_desc(bbase + kk * 2 * b_lbo, b_lbo, 128);
+                            umma_f16(tmem + (uint32_t)(j * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        }
+                        umma_commit(&t_full[j]);
+                        tuse ^= 1u << j;
+                    }
+                    umma_commit(&b_empty[s]);
+                    buse ^= 1u << s;
+                }
+                umma_commit(&a_empty[sa]);
+                ause ^= 1u << sa;
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue warps
+        const int j = warp >> 2;                  // the point tile of the pair
+        const int row = (warp & 3) * 32 + lane;   // and its row (TMEM lane)
+        const float sc = tc_scale(a.absmax, a.d);
+        const float sc2 = sc * sc;                // exact power of two
+        const float isc2 = 1.f / sc2;             // exact power of two
+        const float eta = tc_eta(a.d, kp);
+        const float g = lp_slack(a.d);
+        const float E = __uint_as_float(a.maxes[0]);
+        const float cnmax2 = __fmul_ru(2.f, __uint_as_float(a.maxes[1]));
+        const float rmax = __uint_as_float(a.maxes[2]);
+        const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(j * TC_N);
+        uint32_t tuse = 0;   // parity of this accumulator's uses so far
+        float lomax = 0.f;              // radius: largest lower bound of this thread's rows
+        unsigned long long nrows = 0;   // prune: rows processed (diagnostics)
+        for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x) {
+            const int64_t pt = 2 * pp + j;
+            if (pt >= ntile_pts) continue;   // the last pair has one tile (uniform over the warp)
+            const int64_t pi = pt * TC_M + row;
+            const bool valid = pi < a.npts;
+            const float xn = valid ? a.an[pi] : 0.f;
+            const float sl = __fadd_ru(valid ? a.ae[pi] : 0.f, E);
+            const float eps = __fadd_ru(__fmul_ru(eta, __fadd_ru(xn, cnmax2)), rmax);
+            int64_t gx = 0;
+            bool removed = !valid;
+            if (MODE == 1 && valid) {
+                gx = (int64_t)a.R[pi];
+                removed = a.rin[pi] != 0;
+            }
+            float vlo = INFINITY, vhi = INFINITY;
+            if (MODE == 1 && valid) {
+                // as in tc_dmin_kernel: v >= vlo surely within the threshold,
+                // v < vhi surely beyond it, between: the exact pair check
+                const float thr = __fmul_rn(__uint_as_float(*a.thr), sc2);   // scaled, exact
+                const float ra = __fsub_rd(__fsqrt_rd(__fdiv_rd(thr, __fadd_ru(1.f, g))), sl);
+                const float lo_lim = ra > 0.f ? __fsub_rd(__fmul_rd(ra, ra), eps) : -1.f;
+                const float rb = __fadd_ru(__fsqrt_ru(__fdiv_ru(thr, __fsub_rd(1.f, g))), sl);
+                const float hi_lim = __fadd_ru(__fmul_ru(rb, rb), eps);
+                vlo = lo_lim >= 0.f ? __fsub_ru(xn, lo_lim) : INFINITY;
+                vhi = __fsub_rd(xn, hi_lim);
+            }
+            float v0 = -INFINITY, v1 = -INFINITY, v2 = -INFINITY, v3 = -INFINITY;
+            unsigned long long namb = 0;
+            bool emitted = false, ovf = false;
+            int cbase = 0;
+            auto chunk = [&](const uint32_t(&r)[32], int c0) {
+                if (MODE == 0) {
+#pragma unroll
+                    for (int q = 0; q < 32; q += 8) {
+                        v0 = max3f(v0, __uint_as_float(r[q]), __uint_as_float(r[q + 1]));
+                        v1 = max3f(v1, __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
+                        v2 = max3f(v2, __uint_as_float(r[q + 4]), __uint_as_float(r[q + 5]));
+                        v3 = max3f(v3, __uint_as_float(r[q + 6]), __uint_as_float(r[q + 7]));
+                    }
+                } else if (!removed) {
+                    float m0 = -INFINITY, m1 = -INFINITY;
+#pragma unroll
+                    for (int q = 0; q < 32; q += 4) {
+                        m0 = max3f(m0, __uint_as_float(r[q]), __uint_as_float(r[q + 1]));
+                        m1 = max3f(m1, __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
+                    }
+                    if (fmaxf(m0, m1) >= vhi) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const float v = __uint_as_float(r[q]);
+                            if (v >= vhi && !removed) {
+                                if (v >= vlo) {
+                                    removed = true;
+                                } else if (!ovf) {
+                                    const int64_t ci = (int64_t)cbase + c0 + q;
+                                    if (ci < a.kc) {
+                                        const unsigned long long slot = atomicAdd(a.npairs, 1ull);
+                                        if (slot < (unsigned long long)a.pcap)
+                                            a.pairs[slot] = make_uint2((uint32_t)pi, (uint32_t)ci);
+                                        else
+                                            ovf = true;
+                                        emitted = true;
+                                        ++namb;
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            };
+            for (int t = 0; t < a.ntiles; ++t) {
+                if (!__all_sync(0xFFFFFFFFu, mbar_wait(&t_full[j], tuse & 1u, abort))) {
+                    set_status(a.st, KC_ERR_TIMEOUT, 10, t);
+                    *abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                cbase = t * TC_N;
+                bool released = false;
+                if (MODE == 0 || !__all_sync(0xFFFFFFFFu, removed)) {
+                    // 256 columns as two halves of three 32-column loads behind
+                    // one wait and a fourth in flight; the accumulator is
+                    // released once the last load has landed
+                    uint32_t ra[32], rb[32], rc[32];
+#pragma unroll 1
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t ta = taddr + (uint32_t)(h * 128);
+                        tmem_ld32(ta, ra);
+                        tmem_ld32(ta + 32, rb);
+                        tmem_ld32(ta + 64, rc);
+                        tmem_wait_ld(ra);
+                        tmem_pin(rb);
+                        tmem_pin(rc);
+                        chunk(ra, h * 128);
+                        tmem_ld32(ta + 96, ra);
+                        chunk(rb, h * 128 + 32);
+                        chunk(rc, h * 128 + 64);
+                        tmem_wait_ld(ra);
+                        if (h == 1) {
+                            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                            mbar_arrive(&t_empty[j]);
+                            released = true;
+                        }
+                        chunk(ra, h * 128 + 96);
+                    }
+                }
+                if (!released) {
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(&t_empty[j]);
+                }
+                tuse ^= 1u;
+            }
+            if (!valid) continue;
+            if (MODE == 0) {
+                // min over centers of s~ = xn - max v, then bounds on the
+                // canonical FP32 minimum (scaled units), then unscaled
+                const float vm = fmaxf(fmaxf(v0, v1), fmaxf(v2, v3));
+                const float mm_hi = __fsub_ru(xn, vm), mm_lo = __fsub_rd(xn, vm);
+                const float lo_r = __fsub_rd(__fsqrt_rd(fmaxf(__fsub_rd(mm_lo, eps), 0.f)), sl);
+                const float lo = lo_r > 0.f ? __fmul_rd(__fmul_rd(lo_r, lo_r), __fsub_rd(1.f, g)) : 0.f;
+                const float hi_r = __fadd_ru(__fsqrt_ru(__fadd_ru(fmaxf(mm_hi, 0.f), eps)), sl);
+                const float hi = __fmul_ru(__fmul_ru(hi_r, hi_r), __fadd_ru(1.f, g));
+                const float lo_u = __fmul_rd(lo, isc2), hi_u = __fmul_ru(hi, isc2);
+                a.mlo[pi] = lo_u;
+                a.mhi[pi] = hi_u;
+                lomax = fmaxf(lomax, lo_u);
+            } else {
+                if (!removed) {
+                    const int pf = (emitted ? 1 : 0) | (ovf ? 2 : 0);
+                    if (pf) {
+                        // decided by the pair check (and a full scan on overflow)
+                        a.pflag[pi] = (uint8_t)pf;
+                        a.pend[atomicAdd(a.npend, 1ull)] = (uint32_t)pi;
+                    } else {
+                        a.Rn[atomicAdd(a.rnn, 1ull)] = (uint32_t)gx;
+                    }
+                }
+                if (namb) atomicAdd(&g_tc_counters[0], namb);
+                ++nrows;
+            }
+        }
+        if (MODE == 0) {
+            const unsigned m = __reduce_max_sync(0xFFFFFFFFu, __float_as_uint(lomax));
+            if (lane == 0) atomicMax(a.mlo_max, m);
+        } else {
+            const unsigned long long r = __reduce_add_sync(0xFFFFFFFFu, (unsigned)nrows);
+            if (lane == 0 && r) atomicAdd(&g_tc_counters[1], r);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_N));
+    }
+}
+
 // Radius, exact part.  T = (largest lower bound) (1 - 3 gamma): a point whose
 // upper bound reaches T can hold the maximum (the FP32-to-FP64 margin of the
 // CUDA-core path).  Flag pass: those points go to a list (in no particular
@@ -1060,6 +1351,29 @@ size_t tc_smem_for(TcArgs &a) {
     return need > floor1 ? need : floor1;
 }
 
+// tc_dmin2_kernel's shared memory (two stages of a point-tile pair, a
+// two-stage center ring), or 0 when it does not fit (d above 93) or
+// KC_TC_PAIR=0 in the environment.
+size_t tc_pair_smem(int kp) {
+    const size_t A = (size_t)TC_M * kp * 2, B = (size_t)TC_N * kp * 2;
+    if (const char *env = getenv("KC_TC_PAIR"))
+        if (atoi(env) == 0) return 0;
+    const size_t need = 4 * A + 2 * B;
+    return need <= TC_SMEM_MAX ? (need > 120 * 1024 ? need : 120 * 1024) : 0;
+}
+
+template <int MODE>
+cudaError_t launch_dmin2(const TcArgs &a, size_t smem, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(tc_dmin2_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    const int64_t pairs = ((a.npts + TC_M - 1) / TC_M + 1) / 2;
+    const int grid = (int)std::min<int64_t>(pairs, (int64_t)sms());
+    if (grid > 0) tc_dmin2_kernel<MODE><<<grid, TC_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int R>
 cudaError_t rows(const float *pk, const float *rm, const uint32_t *idx, const int32_t *cnt_dev, int64_t cnt, int d,
                  const unsigned *absmax, void *tiles, float *norm, float *err, unsigned *maxes, cudaStream_t s,
@@ -1160,15 +1474,20 @@ cudaError_t launch_tc_radius(const float *pk, const float *rm, int64_t n, int d,
     a.mhi = B.mhi;
     a.mlo_max = B.mlomax;
     a.st = st;
-    if (const char *env = getenv("KC_TC_PF")) a.pf = std::max(0, std::min(atoi(env), 16));
     const size_t smem = tc_smem_for(a);
     if ((e = cudaFuncSetAttribute(tc_dmin_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
     cudaMemsetAsync(B.mlomax, 0, sizeof(unsigned), s);
-    const int64_t tiles = (n + TC_M - 1) / TC_M;
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms());
-    tc_dmin_kernel<0><<<grid, TC_THREADS, smem, s>>>(a);
+    const size_t smem2 = a.resident ? 0 : tc_pair_smem(a.kp);
+    if (smem2) {
+        // streamed centers: two point tiles per center tile
+        if ((e = launch_dmin2<0>(a, smem2, s)) != cudaSuccess) return e;
+    } else {
+        const int64_t tiles = (n + TC_M - 1) / TC_M;
+        const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms());
+        tc_dmin_kernel<0><<<grid, TC_THREADS, smem, s>>>(a);
+    }
     const int g2 = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sms() * 8);
     cudaMemsetAsync(B.fcount, 0, sizeof(unsigned long long), s);
     tc_flag_kernel<<<g2, 256, 0, s>>>(n, d, B.mhi, B.mlomax, mind, B.flist, B.fcount, st);
@@ -1223,13 +1542,19 @@ cudaError_t launch_tc_prune(const float *src, int d, const uint32_t *R, int64_t 
     a.npend = P.npend;
     a.st = st;
     const size_t smem = tc_smem_for(a);
-    if ((e = cudaFuncSetAttribute(tc_dmin_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-        return e;
     const int64_t tiles = (rn + TC_M - 1) / TC_M;
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms());
-    if (grid == 0) return cudaGetLastError();
-    tc_dmin_kernel<1><<<grid, TC_THREADS, smem, s>>>(a);
+    if (tiles == 0) return cudaGetLastError();
+    const size_t smem2 = a.resident ? 0 : tc_pair_smem(a.kp);
+    if (smem2) {
+        // streamed centers: two point tiles per center tile
+        if ((e = launch_dmin2<1>(a, smem2, s)) != cudaSuccess) return e;
+    } else {
+        if ((e = cudaFuncSetAttribute(tc_dmin_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms());
+        tc_dmin_kernel<1><<<grid, TC_THREADS, smem, s>>>(a);
+    }
     const bool v4 = (d & 3) == 0 && ((uintptr_t)src & 15) == 0 && ((uintptr_t)Scen & 15) == 0;
     const int g2 = sms() * 8;
     tc_pair_kernel<<<g2, 256, 0, s>>>(src, d, v4, R, Scen, P.pairs, P.npairs, P.pcap, thr, P.hit);

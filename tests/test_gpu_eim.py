@@ -82,14 +82,18 @@ def test_eim_bad_eps(kc):
         kc.kc_eim(_dev(I.gauss_mixture(100, 2, 1, 2, 1.0, 0, 1)), 2, eps=1.5)
 
 
+@pytest.mark.parametrize("route", ["default", "pair", "single"])
 @pytest.mark.parametrize("cap", [None, "1"])
-def test_eim_tc_prune_deferred_pairs(kc, monkeypatch, cap):
+def test_eim_tc_prune_deferred_pairs(kc, monkeypatch, cap, route):
     # Integer-valued FP32 coordinates on a small grid: many pair distances
     # equal the threshold exactly, so the tensor-core bounds leave pairs
     # undecided and the deferred exact check decides them.  cap=1 overflows
     # the pair buffer at once, so the full-scan route decides those rows.
     pts = I.int_points(40000, 8, 19, 0, 20).astype(np.float32)
     monkeypatch.setenv("KC_PRUNE_TC", "1")   # d = 8 takes the CUDA cores by default
+    if route != "default":   # streamed centers, two point tiles per center tile or one
+        monkeypatch.setenv("KC_TC_STREAM_CENTERS", "1")
+        monkeypatch.setenv("KC_TC_PAIR", "1" if route == "pair" else "0")
     if cap is not None:
         monkeypatch.setenv("KC_PRUNE_PAIR_CAP", cap)
     kc.kc_counters()
@@ -104,6 +108,19 @@ def test_eim_tc_prune_center_ring(kc, monkeypatch, stream):
         monkeypatch.setenv("KC_TC_STREAM_CENTERS", stream)
     pts = I.gauss_mixture(40000, 24, 77, 60, 0.5, -10, 10)
     check_eim(kc, pts, 5, expect_loop=True)
+
+
+@pytest.mark.parametrize("n", [90_001, 39_100])
+def test_eim_tc_prune_two_point_tiles_per_center_tile(kc, monkeypatch, n):
+    # streamed centers: the kernel that feeds each center tile to two point
+    # tiles against the one-tile kernel and the oracle, with several pairs
+    # per CTA and pairs whose second tile is missing
+    pts = I.gauss_mixture(n, 32, 78, 80, 0.5, -10, 10)
+    monkeypatch.setenv("KC_TC_STREAM_CENTERS", "1")
+    a, _ = check_eim(kc, pts, 6, seed=42, expect_loop=True)
+    monkeypatch.setenv("KC_TC_PAIR", "0")
+    b = kc.kc_eim(_dev(pts), 6, eps=0.1, phi=6.0, seed=42)
+    assert a.centers.cpu().tolist() == b.centers.cpu().tolist() and a.radius == b.radius
 
 
 def test_eim_tc_prune_matches_cuda_cores(kc, monkeypatch):

@@ -221,13 +221,18 @@ def test_radius_tensor_core_matches_cuda_cores(kc, n, d, kc_, monkeypatch):
     assert a.radius == b.radius == r64 and a.argmax == b.argmax == am
 
 
-@pytest.mark.parametrize("n,d,kc_", [(30000, 64, 1000), (9000, 17, 513), (6000, 1, 300)])
-def test_radius_tensor_core_streamed_centers(kc, n, d, kc_, monkeypatch):
-    # the two-stage center ring (the default keeps these center sets resident)
+@pytest.mark.parametrize("pair", [None, "0"])
+@pytest.mark.parametrize("n,d,kc_", [(30000, 64, 1000), (9000, 17, 513), (6000, 1, 300), (41_000, 90, 600),
+                                      (20_000, 100, 300)])
+def test_radius_tensor_core_streamed_centers(kc, n, d, kc_, monkeypatch, pair):
+    # the two-stage center ring (the default keeps these center sets
+    # resident), with two point tiles per center tile (up to d = 93) or one
     pts = I.gauss_mixture(n, d, 300 + d, 11, 0.7, -15, 15)
     C = I.uniform_int(58, d, kc_, 0, n - 1)
     monkeypatch.setenv("KC_RADIUS_TC", "1")
     monkeypatch.setenv("KC_TC_STREAM_CENTERS", "1")
+    if pair is not None:
+        monkeypatch.setenv("KC_TC_PAIR", pair)
     rr = kc.kc_radius(_dev(pts), _dev(C))
     r64, am, _ = O.radius(pts, C, mode="f64")
     assert rr.radius == r64 and rr.argmax == am
@@ -295,6 +300,38 @@ def test_radius_tensor_core_outlier_outside_scale_sample(kc, monkeypatch, row):
     rr = kc.kc_radius(_dev(pts), _dev(C))
     r64, am, _ = O.radius(pts, C, mode="f64")
     assert rr.radius == r64 and rr.argmax == am
+
+
+@pytest.mark.parametrize("n,d,kc_", [(60_003, 64, 1000), (60_000, 3, 4000), (50_001, 16, 700), (45_000, 60, 300),
+                                      (40_000, 100, 257), (39_000, 128, 512), (700, 64, 1024)])
+def test_radius_tensor_core_tiles_per_cta(kc, monkeypatch, n, d, kc_):
+    # row-major points through the tile pass and the tensor-core kernel with
+    # several point tiles per CTA, ragged last tiles, d with 16-byte loads,
+    # partial and scalar rows, fewer tiles than SMs
+    pts = I.gauss_mixture(n, d, 700 + d, 13, 0.8, -6, 6)
+    C = I.uniform_int(71 + d, 3, kc_, 0, n - 1)
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    rr = kc.kc_radius(_dev(pts), _dev(C))
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    assert rr.radius == r64 and rr.argmax == am
+
+
+@pytest.mark.parametrize("row", [1, 70_001])
+def test_radius_tensor_core_scale_fix_up_and_unaligned_rows(kc, monkeypatch, row):
+    # an outlier on a row the scale sample skips makes the tile pass redo the
+    # tiles with the true scale; the unaligned view takes the scalar loads
+    import torch
+    n, d = 80_000, 32
+    pts = I.gauss_mixture(n, d, 72, 7, 0.5, -1, 1)
+    pts[row, 9] = -3.0e3
+    C = I.uniform_int(73, 3, 700, 0, n - 1)
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    flat = torch.from_numpy(np.concatenate([np.zeros(1, np.float32), pts.ravel()])).cuda()
+    view = flat[1:].view(n, d)
+    for src in (_dev(pts), view):
+        rr = kc.kc_radius(src, _dev(C))
+        assert rr.radius == r64 and rr.argmax == am
 
 
 @pytest.mark.parametrize("bad,status", [(np.nan, "KC_ERR_NONFINITE"), (np.inf, "KC_ERR_NONFINITE"),
