@@ -132,6 +132,35 @@ __device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t ad, uint64_t 
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
+// One accumulation chain of KS MMAs (K = 16 each) into d: A and B start at
+// descriptors ad and bd and advance by ainc / binc (the next K step's start
+// address, in the descriptor's 16-byte units; the start field cannot carry:
+// shared-memory addresses stay below 2^18 bytes).  The single issuing thread
+// does almost nothing between MMAs: rebuilding both 64-bit descriptors per
+// MMA in a runtime loop took as long as the MMA itself (a 128 x 256 x 16
+// block is about 135 SM clocks) and held the tensor pipe near half its rate.
+template <int KS>
+__device__ __forceinline__ void umma_chain(uint32_t d, uint64_t ad, uint64_t bd, uint64_t ainc, uint64_t binc,
+                                           uint32_t idesc) {
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) umma_f16(d, ad + kk * ainc, bd + kk * binc, idesc, kk > 0 ? 1u : 0u);
+}
+// The chain for Kp / 16 = ks K steps (1..9: Kp = d + 3 rounded up to 16, d <= 128).
+__device__ __forceinline__ void umma_chain_k(int ks, uint32_t d, uint64_t ad, uint64_t bd, uint64_t ainc,
+                                             uint64_t binc, uint32_t idesc) {
+    switch (ks) {
+        case 1: umma_chain<1>(d, ad, bd, ainc, binc, idesc); break;
+        case 2: umma_chain<2>(d, ad, bd, ainc, binc, idesc); break;
+        case 3: umma_chain<3>(d, ad, bd, ainc, binc, idesc); break;
+        case 4: umma_chain<4>(d, ad, bd, ainc, binc, idesc); break;
+        case 5: umma_chain<5>(d, ad, bd, ainc, binc, idesc); break;
+        case 6: umma_chain<6>(d, ad, bd, ainc, binc, idesc); break;
+        case 7: umma_chain<7>(d, ad, bd, ainc, binc, idesc); break;
+        case 8: umma_chain<8>(d, ad, bd, ainc, binc, idesc); break;
+        default: umma_chain<9>(d, ad, bd, ainc, binc, idesc); break;
+    }
+}
+
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
@@ -608,6 +637,8 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
         if (lane == 0) {
             const uint32_t idesc = umma_idesc_f16(TC_M, TC_N);
             const uint32_t a_lbo = (TC_M / 8) * 128, b_lbo = (TC_N / 8) * 128;
+            // one K step = two core-matrix columns, in 16-byte descriptor units
+            const uint64_t ainc = (2 * a_lbo) >> 4, binc = (2 * b_lbo) >> 4;
             uint32_t ause = 0, buse = 0, tuse = 0;   // bit s: parity of stage s's uses so far
             int64_t u = 0, p = 0;
             for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x, ++p) {
@@ -628,13 +659,9 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t abase = smem_u32(sAb + sa * a_bytes);
-                    const uint32_t bbase = smem_u32(sBb + (a.resident ? t : s) * b_bytes);
-                    for (int kk = 0; kk < kp / 16; ++kk) {
-                        const uint64_t ad = umma_desc(abase + kk * 2 * a_lbo, a_lbo, 128);
-                        const uint64_t bd = umma_desc(bbase + kk * 2 * b_lbo, b_lbo, 128);
-                        umma_f16(tmem + (uint32_t)(s * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
-                    }
+                    const uint64_t ad = umma_desc(smem_u32(sAb + sa * a_bytes), a_lbo, 128);
+                    const uint64_t bd = umma_desc(smem_u32(sBb + (a.resident ? t : s) * b_bytes), b_lbo, 128);
+                    umma_chain_k(kp / 16, tmem + (uint32_t)(s * TC_N), ad, bd, ainc, binc, idesc);
                     if (!a.resident) umma_commit(&b_empty[s]);
                     umma_commit(&t_full[s]);
                     buse ^= 1u << s;
@@ -944,6 +971,8 @@ __global__ void __launch_bounds__(384, 1) tc_dmin2_kernel(TcArgs a) {
         if (lane == 0) {
             const uint32_t idesc = umma_idesc_f16(TC_M, TC_N);
             const uint32_t a_lbo = (TC_M / 8) * 128, b_lbo = (TC_N / 8) * 128;
+            // one K step = two core-matrix columns, in 16-byte descriptor units
+            const uint64_t ainc = (2 * a_lbo) >> 4, binc = (2 * b_lbo) >> 4;
             uint32_t ause = 0, buse = 0, tuse = 0;   // bit s: parity of stage (accumulator) s's uses so far
             int64_t u = 0, p = 0;
             for (int64_t pp = blockIdx.x; pp < npairs && !*abort; pp += gridDim.x, ++p) {
@@ -961,7 +990,7 @@ __global__ void __launch_bounds__(384, 1) tc_dmin2_kernel(TcArgs a) {
                         set_status(a.st, KC_ERR_TIMEOUT, 8, t);
                         break;
                     }
-                    const uint32_t bbase = smem_u32(sBb + s * b_bytes);
+                    const uint64_t bd = umma_desc(smem_u32(sBb + s * b_bytes), b_lbo, 128);
                     for (int j = 0; j < nj; ++j) {
                         if (!mbar_wait(&t_empty[j], ((tuse >> j) & 1u) ^ 1u, abort)) {
                             *abort = 1;
@@ -969,12 +998,8 @@ __global__ void __launch_bounds__(384, 1) tc_dmin2_kernel(TcArgs a) {
                             break;
                         }
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const uint32_t abase = smem_u32(sAb + (2 * sa + j) * a_bytes);
-                        for (int kk = 0; kk < kp / 16; ++kk) {
-                            const uint64_t ad = umma_desc(abase + kk * 2 * a_lbo, a_lbo, 128);
-                            const uint64_t bd = umma_desc(bbase + kk * 2 * b_lbo, b_lbo, 128);
-                            umma_f16(tmem + (uint32_t)(j * TC_N), ad, bd, idesc, kk > 0 ? 1u : 0u);
-                        }
+                        const uint64_t ad = umma_desc(smem_u32(sAb + (2 * sa + j) * a_bytes), a_lbo, 128);
+                        umma_chain_k(kp / 16, tmem + (uint32_t)(j * TC_N), ad, bd, ainc, binc, idesc);
                         umma_commit(&t_full[j]);
                         tuse ^= 1u << j;
                     }
