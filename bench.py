@@ -669,7 +669,9 @@ def run_extra(args):
                          "prune_undecided_pairs": counters[2], "prune_points": counters[3],
                          "sweep_big_rechecks": counters[5], "gon_cycles_sweep": counters[6],
                          "gon_cycles_recheck": counters[7], "gon_cycles_exchange": counters[8],
-                         "gon_cycles_sweep_max_cta": counters[9], "gon_cycles_sweep_recheck_max_cta": counters[10]}}
+                         "gon_cycles_sweep_max_cta": counters[9], "gon_cycles_sweep_recheck_max_cta": counters[10],
+                         "tc_mma_cycles_wait_centers": counters[11], "tc_mma_cycles_wait_accumulator": counters[12],
+                         "tc_mma_cycles_wait_points": counters[13], "tc_mma_cycles": counters[14]}}
     print(json.dumps(line), flush=True)
 
 

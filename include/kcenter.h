@@ -393,8 +393,10 @@ int64_t kc_launch_count(void);
  * a whole warp); out[6..8] = clock cycles of the persistent GON kernels,
  * summed over CTAs, spent in the sweep, the exact rechecks and the group
  * exchange; out[9], out[10] = the largest per-CTA sweep total and sweep +
- * recheck total.  Synchronises the device.  Returns the number of values
- * (11), or -1 on a CUDA error.
+ * recheck total; out[11..14] = clock cycles of the tensor-core blocks' MMA-
+ * issuing thread, summed over CTAs, spent waiting for a center tile, for a
+ * free accumulator, for a point tile, and in all.  Synchronises the device.
+ * Returns the number of values (15), or -1 on a CUDA error.
  */
 int32_t kc_counters(int64_t *out, int32_t cap);
 

@@ -136,9 +136,10 @@ def kc_counters():
     overflows, prune undecided pairs, prune points, prune |R| x |S| pairs,
     sweep rechecks with a lagging memo, GON kernel cycles in sweep / recheck /
     exchange summed over CTAs, largest per-CTA sweep and sweep + recheck
-    totals)."""
-    out = np.zeros(11, dtype=np.int64)
-    if load().kc_counters(out.ctypes.data, 11) < 0:
+    totals, tensor-core MMA issuer cycles waiting for a center tile / a free
+    accumulator / a point tile and in all, summed over CTAs)."""
+    out = np.zeros(15, dtype=np.int64)
+    if load().kc_counters(out.ctypes.data, 15) < 0:
         raise KCError(KC_ERR_CUDA, "kc_counters failed")
     return tuple(int(v) for v in out)
 

@@ -480,12 +480,15 @@ const char *kc_version(void) { return "kcenter-gb300 0.1 (sm_103a)"; }
 void kc_trace_enable(int32_t on) { g_trace_on = on ? 1 : 0; }
 
 int32_t kc_counters(int64_t *out, int32_t cap) {
-    unsigned long long v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0}, g[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    unsigned long long v[15] = {0}, g[8] = {0, 0, 0, 0, 0, 0, 0, 0}, tc[6] = {0, 0, 0, 0, 0, 0};
     if (cudaDeviceSynchronize() != cudaSuccess || read_counters(g, true) != cudaSuccess ||
-        read_tc_counters(v + 2, true) != cudaSuccess) {
+        read_tc_counters(tc, true) != cudaSuccess) {
         cudaGetLastError();
         return -1;
     }
+    v[2] = tc[0];
+    v[3] = tc[1];
+    for (int i = 0; i < 4; ++i) v[11 + i] = tc[2 + i];
     v[0] = g[0];
     v[1] = g[1];
     v[4] = g_prune_pairs.exchange(0);
@@ -495,8 +498,8 @@ int32_t kc_counters(int64_t *out, int32_t cap) {
     v[8] = g[5];
     v[9] = g[6];
     v[10] = g[7];
-    for (int i = 0; i < cap && i < 11; ++i) out[i] = (int64_t)v[i];
-    return 11;
+    for (int i = 0; i < cap && i < 15; ++i) out[i] = (int64_t)v[i];
+    return 15;
 }
 
 int64_t kc_launch_count(void) { return g_launches.load(); }

@@ -497,7 +497,7 @@ inline TcBufs tc_bufs(const RadiusArgs &a) {
                   a.tc_mlomax, a.tc_rin, a.tc_flist, a.tc_fcount};
 }
 bool tc_supported(int d);
-cudaError_t read_tc_counters(unsigned long long out[2], bool reset);
+cudaError_t read_tc_counters(unsigned long long out[6], bool reset);
 int tc_center_tiles(int64_t kc);
 size_t tc_center_bytes(int64_t kc, int d);
 size_t tc_point_bytes(int64_t n, int d);

@@ -56,9 +56,27 @@
 
 namespace kc {
 
-// Diagnostics of the tensor-core prune (since the last read): [0] exact pair
-// checks of undecided pairs, [1] points processed.
-__device__ unsigned long long g_tc_counters[2];
+// Diagnostics of the tensor-core blocks (since the last read): [0] exact pair
+// checks of undecided pairs, [1] points processed (prune); clock cycles of
+// the MMA-issuing thread, summed over CTAs (radius and prune): [2] waiting
+// for a center tile, [3] for a free accumulator, [4] for a point tile, [5] in
+// all.
+__device__ unsigned long long g_tc_counters[6];
+
+// Cycle counts of an MMA issuer's waits, added to g_tc_counters[2..5] once.
+struct MmaClock {
+    long long t0, wb, wt, wa;
+    __device__ __forceinline__ void start() {
+        t0 = clock64();
+        wb = wt = wa = 0;
+    }
+    __device__ __forceinline__ void publish() {
+        atomicAdd(&g_tc_counters[2], (unsigned long long)wb);
+        atomicAdd(&g_tc_counters[3], (unsigned long long)wt);
+        atomicAdd(&g_tc_counters[4], (unsigned long long)wa);
+        atomicAdd(&g_tc_counters[5], (unsigned long long)(clock64() - t0));
+    }
+};
 
 namespace {
 
@@ -641,19 +659,28 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
             const uint64_t ainc = (2 * a_lbo) >> 4, binc = (2 * b_lbo) >> 4;
             uint32_t ause = 0, buse = 0, tuse = 0;   // bit s: parity of stage s's uses so far
             int64_t u = 0, p = 0;
+            MmaClock clk;
+            clk.start();
             for (int64_t pt = blockIdx.x; pt < ntile_pts && !*abort; pt += gridDim.x, ++p) {
                 const int sa = (int)(p & 1);
+                long long c0 = clock64();
                 if (!mbar_wait(&a_full[sa], (ause >> sa) & 1u, abort)) {
                     *abort = 1;
                     set_status(a.st, KC_ERR_TIMEOUT, 7, 0);
                     break;
                 }
+                clk.wa += clock64() - c0;
                 for (int t = 0; t < a.ntiles; ++t, ++u) {
                     const int s = (int)(u & 1);
                     // resident center tiles: one barrier phase, completed once
+                    c0 = clock64();
                     const bool bok = a.resident ? (p > 0 || t > 0 || mbar_wait(&b_full[0], 0u, abort))
                                                 : mbar_wait(&b_full[s], (buse >> s) & 1u, abort);
-                    if (!mbar_wait(&t_empty[s], ((tuse >> s) & 1u) ^ 1u, abort) || !bok) {
+                    const long long c1 = clock64();
+                    clk.wb += c1 - c0;
+                    const bool tok = mbar_wait(&t_empty[s], ((tuse >> s) & 1u) ^ 1u, abort);
+                    clk.wt += clock64() - c1;
+                    if (!tok || !bok) {
                         *abort = 1;
                         set_status(a.st, KC_ERR_TIMEOUT, 8, t);
                         break;
@@ -670,6 +697,7 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
                 umma_commit(&a_empty[sa]);
                 ause ^= 1u << sa;
             }
+            clk.publish();
         }
     } else {
         // ------------------------------------------------ epilogue warps
@@ -975,24 +1003,33 @@ __global__ void __launch_bounds__(384, 1) tc_dmin2_kernel(TcArgs a) {
             const uint64_t ainc = (2 * a_lbo) >> 4, binc = (2 * b_lbo) >> 4;
             uint32_t ause = 0, buse = 0, tuse = 0;   // bit s: parity of stage (accumulator) s's uses so far
             int64_t u = 0, p = 0;
+            MmaClock clk;
+            clk.start();
             for (int64_t pp = blockIdx.x; pp < npairs && !*abort; pp += gridDim.x, ++p) {
                 const int sa = (int)(p & 1);
                 const int nj = 2 * pp + 1 < ntile_pts ? 2 : 1;
+                long long c0 = clock64();
                 if (!mbar_wait(&a_full[sa], (ause >> sa) & 1u, abort)) {
                     *abort = 1;
                     set_status(a.st, KC_ERR_TIMEOUT, 7, 0);
                     break;
                 }
+                clk.wa += clock64() - c0;
                 for (int t = 0; t < a.ntiles && !*abort; ++t, ++u) {
                     const int s = (int)(u & 1);
+                    c0 = clock64();
                     if (!mbar_wait(&b_full[s], (buse >> s) & 1u, abort)) {
                         *abort = 1;
                         set_status(a.st, KC_ERR_TIMEOUT, 8, t);
                         break;
                     }
+                    clk.wb += clock64() - c0;
                     const uint64_t bd = umma_desc(smem_u32(sBb + s * b_bytes), b_lbo, 128);
                     for (int j = 0; j < nj; ++j) {
-                        if (!mbar_wait(&t_empty[j], ((tuse >> j) & 1u) ^ 1u, abort)) {
+                        c0 = clock64();
+                        const bool tok = mbar_wait(&t_empty[j], ((tuse >> j) & 1u) ^ 1u, abort);
+                        clk.wt += clock64() - c0;
+                        if (!tok) {
                             *abort = 1;
                             set_status(a.st, KC_ERR_TIMEOUT, 8, t);
                             break;
@@ -1009,6 +1046,7 @@ __global__ void __launch_bounds__(384, 1) tc_dmin2_kernel(TcArgs a) {
                 umma_commit(&a_empty[sa]);
                 ause ^= 1u << sa;
             }
+            clk.publish();
         }
     } else {
         // ------------------------------------------------ epilogue warps
@@ -1417,10 +1455,10 @@ cudaError_t rows(const float *pk, const float *rm, const uint32_t *idx, const in
 
 bool tc_supported(int d) { return d >= 1 && d <= TC_KMAX; }
 
-cudaError_t read_tc_counters(unsigned long long out[2], bool reset) {
-    cudaError_t e = cudaMemcpyFromSymbol(out, g_tc_counters, 2 * sizeof(unsigned long long));
+cudaError_t read_tc_counters(unsigned long long out[6], bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_tc_counters, 6 * sizeof(unsigned long long));
     if (e == cudaSuccess && reset) {
-        const unsigned long long z[2] = {0, 0};
+        const unsigned long long z[6] = {0, 0, 0, 0, 0, 0};
         e = cudaMemcpyToSymbol(g_tc_counters, z, sizeof z);
     }
     return e;
