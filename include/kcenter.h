@@ -171,7 +171,9 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
  * the tensor cores (fp16 products with per-point bounds; every point that can
  * reach the maximum is recomputed in canonical FP32, then FP64), reading the
  * row-major points where they lie; the result is the same as the CUDA-core
- * path's (KC_RADIUS_TC selects either).
+ * path's (KC_RADIUS_TC selects either).  On the CUDA cores float points with
+ * d <= 16 are read row-major too (no packed copy); host points are copied to
+ * the device first on both row-major paths.
  * Errors: KC_ERR_ARG if kc < 1 or an index is out of range; others as above.
  */
 kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *centers, int32_t kc,

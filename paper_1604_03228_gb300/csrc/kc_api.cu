@@ -638,6 +638,7 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         uint64_t *slots = cv.take<uint64_t>(res_grid ? (size_t)keff * grid * res_sw
                                                       : (size_t)slot_words(keff, grid, lp != 0));
         int *tail = use_tail ? cv.take<int>((size_t)keff) : nullptr;
+        unsigned *flag_words = c.o.dtype == KC_F32 ? cv.take<unsigned>(2) : nullptr;   // flagged count, done
         *zero_bytes = cv.off;
         *staging = (dev_pts || pin_pts) ? nullptr : cv.take<char>((size_t)n * d * esz);
         void *pk = res_grid ? nullptr : cv.take<char>((size_t)nb * BLK * d * esz);
@@ -677,6 +678,11 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
         ra.radius_out = *rad_dev;
         ra.argmax_out = nullptr;
         ra.have_mind = true;
+        if (flag_words) {
+            ra.flagged = cv.take<uint32_t>((size_t)n);
+            ra.flagged_n = flag_words;
+            ra.done = flag_words + 1;
+        }
     };
 
     GonArgs g{};
@@ -758,10 +764,11 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
     kc_status r = begin(opts, c);
     if (r != KC_OK) return r;
 
-    // On the tensor-core path the row-major points are read where they are
-    // (device memory, else a device copy): no pack.  Otherwise the pack reads
-    // pinned host memory in place.
-    const bool rowmajor = tc_radius_wanted(c.o.dtype, d, kc);
+    // On the tensor-core path, and for float points with d <= 16 on the CUDA
+    // cores, the row-major points are read where they are (device memory,
+    // else a device copy): no pack.  Otherwise the pack reads pinned host
+    // memory in place.
+    const bool rowmajor = tc_radius_wanted(c.o.dtype, d, kc) || (c.o.dtype == KC_F32 && d <= 16);
     const bool dev_pts = is_device_ptr(pts, c.dev);
     const void *pin_pts = (dev_pts || rowmajor) ? nullptr : pinned_device_ptr(pts);
     const bool dev_cin = is_device_ptr(centers, c.dev);
@@ -789,7 +796,13 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
         ra.key32 = cv.take<unsigned long long>(1);
         ra.max64 = cv.take<unsigned long long>(1);
         ra.arg64 = cv.take<unsigned long long>(1);
+        unsigned *flag_words = c.o.dtype == KC_F32 ? cv.take<unsigned>(2) : nullptr;   // flagged count, done
         zero_bytes = cv.off;
+        if (flag_words) {
+            ra.flagged_n = flag_words;
+            ra.done = flag_words + 1;
+            ra.flagged = cv.take<uint32_t>((size_t)n);
+        }
         staging = (dev_pts || pin_pts) ? nullptr : cv.take<char>((size_t)n * d * esz);
         ra.pk = rowmajor ? nullptr : cv.take<char>((size_t)nb * BLK * d * esz);
         ra.mind = cv.take<uint32_t>((size_t)nb * BLK);
@@ -830,7 +843,7 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
         KC_CUDA(cudaMemcpyAsync((void *)cin_dev, centers, (size_t)kc * sizeof(int64_t), cudaMemcpyHostToDevice, c.s),
                 "copy centers in");
     if (rowmajor) {
-        ra.rm = (const float *)src;   // checked by the tensor-core prep
+        ra.rm = (const float *)src;   // checked by the tensor-core prep or the minimum kernel
     } else {
         TraceStep t("pack", c.s);
         KC_CUDA(launch_pack(src, c.o.dtype, n, d, (void *)ra.pk, range2, c.arena->status, c.s), "pack launch");

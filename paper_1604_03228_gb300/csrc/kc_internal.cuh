@@ -441,8 +441,9 @@ cudaError_t launch_compact(const uint8_t *mask, int64_t n, int *counts, int64_t 
 
 struct RadiusArgs {
     const void *pk;
-    // float points on the tensor-core path may come row-major instead
-    // ([n][d], pk null): nothing is packed, the coordinates are read in place
+    // float points may come row-major instead ([n][d], pk null): on the
+    // tensor-core path, the CUDA-core minimum for d <= 16, and the rechecks;
+    // nothing is packed, the coordinates are read in place
     const float *rm;
     int dtype;
     int64_t n;
@@ -476,6 +477,11 @@ struct RadiusArgs {
     // count); the FP64 recheck then visits only these
     uint32_t *tc_flist;
     unsigned long long *tc_fcount;
+    // float points: with these set (flagged: [n] slots; flagged_n and done
+    // zeroed before the launch) the FP64 recheck, the argmax and the result
+    // are one launch (recheck_kernel); null: three launches
+    uint32_t *flagged;
+    unsigned *flagged_n, *done;
 };
 
 // ------------------------------------------------- tensor-core blocks

@@ -50,11 +50,15 @@ __global__ void gather_kernel(const T *__restrict__ pk, const T *__restrict__ rm
 // Minimum over all centers for the 4 points of each lane.  Centers are staged
 // through shared memory in tiles with a row stride of DR >= d coordinates,
 // zero-padded (a zero term leaves the canonical sum unchanged), and the
-// lane's points are held in registers when d <= DR.
+// lane's points are held in registers when d <= DR.  The points come from the
+// packed array pk, or (pk null, float) straight from the row-major array rm:
+// a lane's 4 points are 4d consecutive floats, 16-byte aligned when rm is,
+// and every coordinate is checked as the pack would check it (NaN/Inf, then
+// magnitude above 2^54), so no packed copy is made.
 template <typename T, int DR>
 __global__ void __launch_bounds__(RAD_NT) radius_min_kernel(
-    const T *__restrict__ pk, int64_t n, int d, const T *__restrict__ cen, const int32_t *kc_dev,
-    int kc_max, uint32_t *__restrict__ mind, unsigned long long *key32, const DevStatus *st) {
+    const T *__restrict__ pk, const T *__restrict__ rm, int64_t n, int d, const T *__restrict__ cen,
+    const int32_t *kc_dev, int kc_max, uint32_t *__restrict__ mind, unsigned long long *key32, DevStatus *st) {
     using A = typename AccOf<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *cs = reinterpret_cast<T *>(smem_raw);
@@ -68,16 +72,53 @@ __global__ void __launch_bounds__(RAD_NT) radius_min_kernel(
         const int64_t b = g * RAD_W + warp;
         const bool active = b < nb;
         T x[DR][4];
+        if (pk || !std::is_same<T, float>::value) {
 #pragma unroll
-        for (int j = 0; j < DR; ++j) {
-            x[j][0] = x[j][1] = x[j][2] = x[j][3] = T(0);
-            if (active && j < d) {
-                const T *p = pk + (b * d + j) * BLK + lane * 4;
-                x[j][0] = p[0];
-                x[j][1] = p[1];
-                x[j][2] = p[2];
-                x[j][3] = p[3];
+            for (int j = 0; j < DR; ++j) {
+                x[j][0] = x[j][1] = x[j][2] = x[j][3] = T(0);
+                if (active && j < d) {
+                    const T *p = pk + (b * d + j) * BLK + lane * 4;
+                    x[j][0] = p[0];
+                    x[j][1] = p[1];
+                    x[j][2] = p[2];
+                    x[j][3] = p[3];
+                }
             }
+        } else if constexpr (std::is_same<T, float>::value) {
+            const int64_t i0 = b * BLK + lane * 4;
+            bool bad = false, nonfin = false;
+            if (active && d == DR && i0 + 3 < n && ((uintptr_t)rm & 15) == 0) {
+                // 4 rows of DR floats: DR 16-byte loads
+                T v[4 * DR];
+#pragma unroll
+                for (int t = 0; t < DR; ++t) {
+                    const float4 w = __ldg(reinterpret_cast<const float4 *>(rm + i0 * DR) + t);
+                    v[4 * t] = w.x;
+                    v[4 * t + 1] = w.y;
+                    v[4 * t + 2] = w.z;
+                    v[4 * t + 3] = w.w;
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int j = 0; j < DR; ++j) x[j][q] = v[q * DR + j];
+            } else {
+#pragma unroll
+                for (int j = 0; j < DR; ++j)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        x[j][q] = (active && j < d && i0 + q < n) ? __ldg(rm + (i0 + q) * d + j) : T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < DR; ++j)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float av = fabsf((float)x[j][q]);
+                    if (!(av <= 0x1p54f)) bad = true;   // NaN fails the comparison
+                    if (!isfinite((float)x[j][q])) nonfin = true;
+                }
+            if (nonfin) set_status(st, KC_ERR_NONFINITE, 1, 0);
+            else if (bad) set_status(st, KC_ERR_RANGE, 1, 0);
         }
         uint32_t m[4] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
         for (int t0 = 0; t0 < kc; t0 += tile) {
@@ -257,6 +298,87 @@ __global__ void recheck_arg_kernel(int64_t n, int d, const uint32_t *__restrict_
     }
 }
 
+// Float points, one launch for the FP64 recheck and the result: every CTA
+// scans its share of the points (the list, or all n) as recheck_max_kernel
+// does and also appends each flagged point to a list; the last CTA to finish
+// (a completion counter, after a fence) takes the lowest flagged index whose
+// FP64 value equals the maximum and writes radius and argmax, as
+// recheck_arg_kernel and finalize_kernel do.  Only this call's flagged points
+// are visited, so m64 entries left by earlier calls are never read.
+__global__ void __launch_bounds__(256) recheck_kernel(
+    const float *__restrict__ pk, const float *__restrict__ rm, int64_t n, int d, const float *__restrict__ cen,
+    const int32_t *kc_dev, int kc_max, const uint32_t *__restrict__ mind, const unsigned long long *key32,
+    unsigned long long *max64, double *m64, DevStatus *st, const float *eblk, const float *ecmax,
+    const float *lpscale, const uint32_t *__restrict__ list, const unsigned long long *lcount, uint32_t *flagged,
+    unsigned *flagged_n, unsigned *done, double *radius_out, int64_t *argmax_out) {
+    __shared__ int s_last;
+    __shared__ unsigned long long s_arg[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool run = ld_volatile_i32(&st->code) == 0 && key_val(*key32) != 0;
+    if (run) {
+        const double sc = lpscale ? (double)*lpscale : 1.0;
+        const int kc = (int)dev_count(kc_dev, kc_max);
+        const double thr = flag_threshold(key32, d);
+        const float opg = __fadd_ru(1.f, lp_slack(d));
+        const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+        const int64_t cnt = list ? (int64_t)*lcount : n;
+        for (int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + warp) * 32; base < cnt; base += warps * 32) {
+            const int64_t i = base + lane;
+            int64_t x = i < cnt ? (list ? (int64_t)list[i] : i) : 0;
+            if (i < cnt && !KC_IN_RANGE(st, x, n, KC_AT_RADIUS_LIST)) x = -1;
+            const bool flag = i < cnt && x >= 0 && can_reach(mind, x, thr, eblk, ecmax, opg, sc);
+            unsigned todo = __ballot_sync(0xFFFFFFFFu, flag);
+            while (todo) {
+                const int src = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int64_t xs = __shfl_sync(0xFFFFFFFFu, x, src);
+                const double v = min64_warp(pk, rm, xs, d, cen, kc, lane, eblk ? 0xFFFFFFFFu : mind[xs]);
+                if (lane == src) {
+                    m64[xs] = v;
+                    atomicMax(max64, (unsigned long long)__double_as_longlong(v));
+                    const unsigned slot = atomicAdd(flagged_n, 1u);
+                    if (KC_IN_RANGE(st, slot, n, KC_AT_RADIUS_LIST)) flagged[slot] = (uint32_t)xs;
+                }
+            }
+        }
+    }
+    // the last CTA to finish sees every other CTA's writes (fence, counter)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (ld_volatile_i32(&st->code) != 0) return;
+    const uint64_t K = __ldcg(key32);
+    if (key_val(K) == 0) {
+        // every minimum is exactly 0
+        if (threadIdx.x == 0) {
+            *radius_out = 0.0;
+            if (argmax_out) *argmax_out = key_idx(K);
+        }
+        return;
+    }
+    const unsigned long long mb = __ldcg(max64);
+    const unsigned nf = __ldcg(flagged_n);
+    unsigned long long best = 0;
+    for (unsigned f = threadIdx.x; f < nf && f < (unsigned)n; f += blockDim.x) {
+        const uint32_t x = __ldcg(flagged + f);
+        if ((unsigned long long)__double_as_longlong(__ldcg(m64 + x)) == mb)
+            best = umax64(best, 0xFFFFFFFFFFFFFFFFull - (unsigned long long)x);
+    }
+    best = warp_max_u64(best);
+    if (lane == 0) s_arg[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) best = umax64(best, s_arg[w]);
+        *radius_out = __dsqrt_rn(__longlong_as_double((long long)mb));
+        if (argmax_out) *argmax_out = (int64_t)(0xFFFFFFFFFFFFFFFFull - best);
+    }
+}
+
 // One thread: radius and argmax from the FP64 recheck (float) or directly
 // from the exact key (int32).
 __global__ void finalize_kernel(int dtype, const unsigned long long *key32,
@@ -282,7 +404,7 @@ cudaError_t run_min(RadiusArgs &a, cudaStream_t s, int grid) {
     const int tile = RAD_TILE_BYTES / (DR * (int)sizeof(T));
     const size_t smem = (size_t)tile * DR * sizeof(T);
     radius_min_kernel<T, DR><<<grid, RAD_NT, smem, s>>>(
-        (const T *)a.pk, a.n, a.d, (const T *)a.cen, a.kc_dev, a.kc_max, a.mind, a.key32, a.st);
+        (const T *)a.pk, (const T *)a.rm, a.n, a.d, (const T *)a.cen, a.kc_dev, a.kc_max, a.mind, a.key32, a.st);
     return cudaGetLastError();
 }
 
@@ -326,9 +448,10 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
                                                         a.centers, a.kc_dev, a.kc_max, (int32_t *)a.cen, a.st);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    // row-major points (pk null) are read by the tensor-core path, and by
-    // the rechecks after a Gonzalez kernel that held the minima (have_mind)
-    if (a.rm && (a.pk || (!a.have_mind && (a.dtype != KC_F32 || !a.tc_at || !tc_supported(a.d)))))
+    // row-major points (pk null) are read by the tensor-core path, by the
+    // CUDA-core minimum for float points with d <= 16, and by the rechecks
+    // after a Gonzalez kernel that held the minima (have_mind)
+    if (a.rm && (a.pk || (!a.have_mind && (a.dtype != KC_F32 || (!(a.tc_at && tc_supported(a.d)) && a.d > 16)))))
         return cudaErrorInvalidValue;
     if (!a.rm && !a.pk) return cudaErrorInvalidValue;
     if (!a.have_mind) {
@@ -342,6 +465,18 @@ cudaError_t launch_radius(RadiusArgs &a, cudaStream_t s) {
             e = a.dtype == KC_F32 ? dispatch_min<float>(a, s, sms) : dispatch_min<int32_t>(a, s, sms);
         }
         if (e != cudaSuccess) return e;
+    }
+    if (a.dtype == KC_F32 && a.flagged) {
+        const bool tcl = !a.have_mind && a.tc_at && tc_supported(a.d);
+        const int64_t g = (a.n + 255) / 256;
+        const int grid = (int)(g > sms * 8 ? sms * 8 : g);
+        recheck_kernel<<<grid, 256, 0, s>>>((const float *)a.pk, a.rm, a.n, a.d, (const float *)a.cen, a.kc_dev,
+                                            a.kc_max, a.mind, a.key32, a.max64, a.m64, a.st, a.eblk, a.ecmax,
+                                            a.lpscale, tcl ? a.tc_flist : nullptr, tcl ? a.tc_fcount : nullptr,
+                                            a.flagged, a.flagged_n, a.done, a.radius_out, a.argmax_out);
+        const bool tc = tcl;
+        note_launches(2 + (a.have_mind || tc ? 0 : 1));
+        return cudaGetLastError();
     }
     if (a.dtype == KC_F32) {
         // after the tensor-core filter only its listed points have a non-zero minimum

@@ -178,6 +178,47 @@ def test_radius_int(kc, n, d, kc_):
     assert rr.radius == math.sqrt(r2) and rr.argmax == am
 
 
+@pytest.mark.parametrize("d", [1, 3, 7, 10, 16])
+def test_radius_row_major_cuda_cores(kc, monkeypatch, d):
+    # float points with d <= 16 on the CUDA cores are read row-major (no
+    # packed copy): an unaligned device view (scalar loads), host memory
+    # (pageable and pinned), ragged last blocks; the minimum kernel performs
+    # the pack's input checks
+    import torch
+    monkeypatch.setenv("KC_RADIUS_TC", "0")
+    n = 5 * 512 + 77
+    pts = I.gauss_mixture(n, d, 520 + d, 9, 1.0, -4, 4)
+    C = I.uniform_int(65, d, 90, 0, n - 1)
+    r64, am, _ = O.radius(pts, C, mode="f64")
+    flat = torch.from_numpy(np.concatenate([np.zeros(1, np.float32), pts.ravel()])).cuda()
+    view = flat[1:].view(n, d)
+    for src in (_dev(pts), view, pts, torch.from_numpy(pts).pin_memory()):
+        rr = kc.kc_radius(src, _dev(C))
+        assert rr.radius == r64 and rr.argmax == am
+    for bad, status in ((np.nan, kc.KC_ERR_NONFINITE), (-np.inf, kc.KC_ERR_NONFINITE), (3.0e17, kc.KC_ERR_RANGE)):
+        b = pts.copy()
+        b[n - 2, d - 1] = bad
+        with pytest.raises(kc.KCError) as e:
+            kc.kc_radius(_dev(b), _dev(C))
+        assert e.value.status == status
+    assert kc.kc_radius(_dev(pts), _dev(C)).radius == r64
+
+
+def test_radius_fp64_ties_lowest_index(kc):
+    # two copies of the farthest point: equal FP64 minima, the lower index wins
+    pts = I.gauss_mixture(4000, 5, 66, 4, 0.5, -1, 1)
+    far = np.full((1, 5), 9.5, np.float32)
+    pts = np.concatenate([pts[:1000], far, pts[1000:3000], far, pts[3000:]]).astype(np.float32)
+    C = np.arange(0, 4002, 97)
+    C = C[(C != 1000) & (C != 3001)]
+    for src in (_dev(pts),):
+        rr = kc.kc_radius(src, _dev(C))
+        r64, am, _ = O.radius(pts, C, mode="f64")
+        assert rr.radius == r64 and rr.argmax == am == 1000
+    g = kc.kc_gonzalez(_dev(pts), 1, first=0)
+    assert g.radius == O.radius(pts, np.array([0]), mode="f64")[0]
+
+
 def test_radius_all_points_are_centers(kc):
     pts = I.gauss_mixture(300, 3, 5, 3, 1.0, 0, 1)
     rr = kc.kc_radius(_dev(pts), _dev(np.arange(300)))
