@@ -48,7 +48,8 @@
  * ----------------------------------------------------------------
  *  KC_RADIUS_TC=0|1          covering radius on CUDA cores / on the tensor-core
  *                            blocks (default: tensor cores for float points
- *                            when k * d >= 8192 and d <= 128)
+ *                            with d <= 128 when k * d >= 8192, or when
+ *                            k * d >= 1536 and n >= 262144)
  *  KC_PRUNE_TC=0|1           EIM prune on CUDA cores / tensor cores (default:
  *                            tensor cores for float points, 16 <= d <= 128,
  *                            |S| >= 256)
@@ -167,8 +168,8 @@ kc_status kc_gonzalez(const void *pts, int64_t n, int32_t d, int32_t k, int64_t 
  *   radius        double out: the covering radius.
  *   argmax_point  int64 out (may be NULL): the farthest point, lowest index on
  *                 ties.
- * For float points with kc * d >= 8192 and d <= 128 the n x kc block runs on
- * the tensor cores (fp16 products with per-point bounds; every point that can
+ * For float points with d <= 128 and kc * d >= 8192 (kc * d >= 1536 from
+ * n = 262144 on) the n x kc block runs on the tensor cores (fp16 products with per-point bounds; every point that can
  * reach the maximum is recomputed in canonical FP32, then FP64), reading the
  * row-major points where they lie; the result is the same as the CUDA-core
  * path's (KC_RADIUS_TC selects either).  On the CUDA cores float points with

@@ -364,16 +364,24 @@ void take_lp(Carve &cv, LPBufs &L, int lp, int64_t n, int d) {
 }
 
 // Tensor-core radius filter scratch for kc centers over n float points
-// (left null, i.e. CUDA cores, for int32 points, d > 128, tiny center sets,
-// or KC_RADIUS_TC=0 in the environment).
-bool tc_radius_wanted(int dtype, int d, int kc) {
-    bool use = dtype == KC_F32 && tc_supported(d) && (int64_t)kc * d >= 8192;
+// (left null, i.e. CUDA cores, for int32 points, d > 128, little work per
+// point, or KC_RADIUS_TC=0 in the environment).  The CUDA cores' time grows
+// with k d per point, the tensor-core path's with ceil(k / 256) (Kp = d + 3
+// rounded up to 16) plus a dozen launches; measured on uniform points
+// (ms per call, CUDA cores against tensor cores): 10M x 16, k = 200: 2.35
+// against 1.00; 10M x 8, k = 200: 1.28 against 0.86; 2M x 32, k = 100: 1.92
+// against 0.39; 1M x 16, k = 200: 0.37 against 0.27; but 1M x 10, k = 100:
+// 0.22 against 0.26; 10M x 16, k = 64: 0.94 against 1.00; 10M x 4, k = 200:
+// 0.75 against 0.88.  So: k d >= 1536 from 256k points, k d >= 8192 below.
+bool tc_radius_wanted(int dtype, int64_t n, int d, int kc) {
+    const int64_t kd = (int64_t)kc * d;
+    bool use = dtype == KC_F32 && tc_supported(d) && (kd >= 8192 || (kd >= 1536 && n >= 262144));
     if (const char *env = getenv("KC_RADIUS_TC")) use = dtype == KC_F32 && tc_supported(d) && atoi(env) != 0;
     return use;
 }
 
 void take_tc(Carve &cv, RadiusArgs &ra, int dtype, int64_t n, int d, int kc) {
-    if (!tc_radius_wanted(dtype, d, kc)) {
+    if (!tc_radius_wanted(dtype, n, d, kc)) {
         ra.tc_at = nullptr;
         return;
     }
@@ -768,7 +776,7 @@ kc_status kc_radius(const void *pts, int64_t n, int32_t d, const int64_t *center
     // cores, the row-major points are read where they are (device memory,
     // else a device copy): no pack.  Otherwise the pack reads pinned host
     // memory in place.
-    const bool rowmajor = tc_radius_wanted(c.o.dtype, d, kc) || (c.o.dtype == KC_F32 && d <= 16);
+    const bool rowmajor = tc_radius_wanted(c.o.dtype, n, d, kc) || (c.o.dtype == KC_F32 && d <= 16);
     const bool dev_pts = is_device_ptr(pts, c.dev);
     const void *pin_pts = (dev_pts || rowmajor) ? nullptr : pinned_device_ptr(pts);
     const bool dev_cin = is_device_ptr(centers, c.dev);
