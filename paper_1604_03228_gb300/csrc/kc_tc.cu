@@ -28,10 +28,10 @@
 //        in TMEM (2 x 256 columns)
 //   0-7  epilogue: warps w and w+4 own point rows 32(w%4).. (their TMEM
 //        lanes) and split the 256 columns; each thread loads its 128 columns
-//        as three 32-column loads behind one wait and a fourth in flight
-//        while those are used, releases the accumulator, and folds v into a
-//        running maximum three values at a time (radius) or compares it with
-//        the point's two decision limits (prune).
+//        as four 32-column loads behind one wait, releases the accumulator
+//        after that single round trip, and folds v into a running maximum
+//        three values at a time (radius) or compares it with the point's two
+//        decision limits (prune).
 // With streamed centers (the prune; the radius when the centers do not fit)
 // tc_dmin2_kernel takes two point tiles per center tile instead, so that a
 // center tile read from L2 feeds two MMAs (see there).
@@ -822,27 +822,28 @@ __global__ void __launch_bounds__(384, 1) tc_dmin_kernel(TcArgs a) {
                 if (MODE == 1 && !removed && s_gone_v[row]) removed = true;   // another group decided
                 bool released = false;
                 if (MODE == 0 || !__all_sync(0xFFFFFFFFu, removed)) {
-                    // three 32-column loads behind one wait, the fourth in
-                    // flight while they are used; the accumulator buffer is
-                    // released as soon as the last load has landed
+                    // all four 32-column loads behind one wait: the
+                    // accumulator is released after a single TMEM round trip,
+                    // then folded (three loads behind one wait and a fourth in
+                    // flight took two round trips)
                     static_assert(TC_COLS == 128, "four 32-column chunks per thread");
                     const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(s * TC_N + grp * TC_COLS);
-                    uint32_t ra[32], rb[32], rc[32];
+                    uint32_t ra[32], rb[32], rc[32], rd[32];
                     tmem_ld32(taddr, ra);
                     tmem_ld32(taddr + 32, rb);
                     tmem_ld32(taddr + 64, rc);
+                    tmem_ld32(taddr + 96, rd);
                     tmem_wait_ld(ra);
                     tmem_pin(rb);
                     tmem_pin(rc);
-                    chunk(ra, 0);
-                    tmem_ld32(taddr + 96, ra);
-                    chunk(rb, 32);
-                    chunk(rc, 64);
-                    tmem_wait_ld(ra);
+                    tmem_pin(rd);
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     mbar_arrive(&t_empty[s]);
                     released = true;
-                    chunk(ra, 96);
+                    chunk(ra, 0);
+                    chunk(rb, 32);
+                    chunk(rc, 64);
+                    chunk(rd, 96);
                 }
                 if (!released) {
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1144,30 +1145,30 @@ __global__ void __launch_bounds__(384, 1) tc_dmin2_kernel(TcArgs a) {
                 cbase = t * TC_N;
                 bool released = false;
                 if (MODE == 0 || !__all_sync(0xFFFFFFFFu, removed)) {
-                    // 256 columns as two halves of three 32-column loads behind
-                    // one wait and a fourth in flight; the accumulator is
-                    // released once the last load has landed
-                    uint32_t ra[32], rb[32], rc[32];
+                    // 256 columns as two batches of four 32-column loads
+                    // behind one wait each; the accumulator is released as
+                    // soon as the second batch has landed
+                    uint32_t ra[32], rb[32], rc[32], rd[32];
 #pragma unroll 1
                     for (int h = 0; h < 2; ++h) {
                         const uint32_t ta = taddr + (uint32_t)(h * 128);
                         tmem_ld32(ta, ra);
                         tmem_ld32(ta + 32, rb);
                         tmem_ld32(ta + 64, rc);
+                        tmem_ld32(ta + 96, rd);
                         tmem_wait_ld(ra);
                         tmem_pin(rb);
                         tmem_pin(rc);
-                        chunk(ra, h * 128);
-                        tmem_ld32(ta + 96, ra);
-                        chunk(rb, h * 128 + 32);
-                        chunk(rc, h * 128 + 64);
-                        tmem_wait_ld(ra);
+                        tmem_pin(rd);
                         if (h == 1) {
                             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                             mbar_arrive(&t_empty[j]);
                             released = true;
                         }
-                        chunk(ra, h * 128 + 96);
+                        chunk(ra, h * 128);
+                        chunk(rb, h * 128 + 32);
+                        chunk(rc, h * 128 + 64);
+                        chunk(rd, h * 128 + 96);
                     }
                 }
                 if (!released) {
