@@ -50,3 +50,19 @@ def test_eim_prune_with_cancelling_terms(kc, monkeypatch):
     assert a.centers.cpu().tolist() == b.centers.cpu().tolist() and a.radius == b.radius
     ref = O.eim(pts, 4, 0.1, 6.0, 5, mode="f32")
     assert a.centers.cpu().numpy().tolist() == ref.centers.tolist()
+
+
+def test_mma_issuer_counters(kc, monkeypatch):
+    # the tensor-core MMA issuer's cycle counters: present after a tensor-core
+    # radius, each wait within the issuer's total
+    pts = cancelling_points(50_000, 64, 970)
+    C = np.sort(I.uniform_int(971, 3, 1024, 0, 49_999)).astype(np.int64)
+    monkeypatch.setenv("KC_RADIUS_TC", "1")
+    kc.kc_counters()
+    kc.kc_radius(_dev(pts), _dev(C))
+    c = kc.kc_counters()
+    assert len(c) == 15
+    wait_centers, wait_acc, wait_points, total = c[11:15]
+    assert total > 0
+    assert 0 <= wait_centers <= total and 0 <= wait_acc <= total and 0 <= wait_points <= total
+    assert wait_centers + wait_acc + wait_points <= total
