@@ -575,17 +575,48 @@ template <int KIND>
 __device__ __forceinline__ void lp_load_center(const GonInst &I, int64_t c, int d, int ng, float *cl, const float *scs,
                                                int slot, int lane, float *ec) {
     constexpr int LG = lp_group(KIND);
-    const float *pk = (const float *)I.pk;
+    const float *__restrict__ pk = (const float *)I.pk;
     const int64_t g = I.lo + c;
-    for (int jg = lane; jg < ng; jg += 32) {
-        const uint32_t w = I.lp[((g / BLK) * ng + jg) * BLK + g % BLK];
+    // every load first (one memory round trip for all of them), then the
+    // stores: the winner's words, FP32 coordinates (d <= 32 * 8 per lane
+    // here, the rest in a second pass) and bound
+    constexpr int NW = 4, NX = 8;
+    uint32_t w[NW];
+    float xv[NX];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int jg = lane + 32 * q;
+        w[q] = jg < ng ? __ldg(I.lp + ((g / BLK) * ng + jg) * BLK + g % BLK) : 0u;
+    }
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+        const int j = lane + 32 * q;
+        xv[q] = j < d ? __ldg(pk + pk_index(g, j, d)) : 0.f;
+    }
+    const float e = __ldg(I.ept + g);
+#pragma unroll
+    for (int q = 0; q < NW; ++q) {
+        const int jg = lane + 32 * q;
+        if (jg < ng) {
+            float v[LG];
+            LPDec<KIND>::dec(w[q], scs + jg * LG, v);
+#pragma unroll
+            for (int t = 0; t < LG; ++t) cl[jg * LG + t] = v[t];
+        }
+    }
+    for (int jg = lane + 32 * NW; jg < ng; jg += 32) {
         float v[LG];
-        LPDec<KIND>::dec(w, scs + jg * LG, v);
+        LPDec<KIND>::dec(I.lp[((g / BLK) * ng + jg) * BLK + g % BLK], scs + jg * LG, v);
 #pragma unroll
         for (int t = 0; t < LG; ++t) cl[jg * LG + t] = v[t];
     }
-    for (int j = lane; j < d; j += 32) I.cenT[(int64_t)j * I.kcap + slot] = pk[pk_index(g, j, d)];
-    *ec = I.ept[g];
+#pragma unroll
+    for (int q = 0; q < NX; ++q) {
+        const int j = lane + 32 * q;
+        if (j < d) I.cenT[(int64_t)j * I.kcap + slot] = xv[q];
+    }
+    for (int j = lane + 32 * NX; j < d; j += 32) I.cenT[(int64_t)j * I.kcap + slot] = pk[pk_index(g, j, d)];
+    *ec = e;
 }
 
 template <int KIND, int DC, int NT>
