@@ -71,8 +71,8 @@ EXTRA = (CFG2, "gon_int_n10000_d2_k10", "gon_unif_n10000000_d16_k200", "mrg_unif
 # full workload (a smaller capture scaled by the units processed).
 NCU_TRAFFIC = {
     # gon_group_kernel<float, 64, 1> at k = 16 on the 8M x 64 set (mean of two launches):
-    # 33,415,506,304 B read + 275,535,232 B written; x 64 for k = 1024
-    "0409681608b1589804de8468a267bbc846e160500536bd3ba8cbf64b8107c900": 2_156_226_658_304,
+    # 33,414,887,680 B read + 275,456,128 B written; x 64 for k = 1024
+    "3f019a95cd88c2d2cbef16eee6b28214751a0de558481537031966052fe939c9": 2_156_182_003_712,
 }
 
 
